@@ -1,0 +1,306 @@
+"""Pins for the CPU oracle against facts that do not come from the oracle itself:
+closed forms, brute force on tiny inputs, and independent library routines."""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import FP8, FP16, FP32, FP64
+from paper_2410_09819_gb300 import inputs
+
+
+# ---------------------------------------------------------------- FP64 Cholesky
+def test_pascal_factor_is_lower_binomial():
+    # P_ij = C(i+j, i) = L L^T with L_ij = C(i, j) (exact in FP64 for small n)
+    n = 12
+    P = np.array([[math.comb(i + j, i) for j in range(n)] for i in range(n)], dtype=np.float64)
+    L = oracle.cholesky(P)
+    expect = np.array([[math.comb(i, j) if j <= i else 0 for j in range(n)] for i in range(n)], float)
+    assert np.array_equal(L, expect)
+    assert oracle.logdet(L) == 0.0
+
+
+def test_tridiagonal_closed_form():
+    # tridiag(-1, 2, -1): L_ii = sqrt((i+2)/(i+1)), L_{i+1,i} = -sqrt((i+1)/(i+2)), det = n + 1
+    n = 50
+    A = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    L = oracle.cholesky(A)
+    i = np.arange(n)
+    assert np.allclose(np.diag(L), np.sqrt((i + 2) / (i + 1)), rtol=1e-14, atol=0)
+    assert np.allclose(np.diag(L, -1), -np.sqrt((i[:-1] + 1) / (i[:-1] + 2)), rtol=1e-14, atol=0)
+    assert abs(oracle.logdet(L) - math.log(n + 1)) < 1e-13
+
+
+def _ar1_closed_form(x, a):
+    # exponential covariance on sorted 1-D points is an AR(1) process:
+    # rho_j = exp(-(x_j - x_{j-1})/a), c_0 = 1, c_j = sqrt(1 - rho_j^2),
+    # L_ij = (prod_{l=j+1..i} rho_l) c_j,  log det = sum_{j>=1} log(1 - rho_j^2)
+    n = len(x)
+    rho = np.exp(-np.diff(x) / a)
+    c = np.concatenate([[1.0], np.sqrt(1.0 - rho * rho)])
+    logcum = np.concatenate([[0.0], np.cumsum(np.log(rho))])
+    L = np.tril(np.exp(logcum[:, None] - logcum[None, :])) * c[None, :]
+    return L, float(np.sum(np.log1p(-rho * rho)))
+
+
+def test_exponential_covariance_on_a_line_is_ar1():
+    pts = inputs.line_points(300, seed=11)
+    a = 0.05
+    A = oracle.matern(pts, 1.0, a, 0.5)
+    L = oracle.cholesky(A)
+    Lx, ld = _ar1_closed_form(pts[:, 0], a)
+    assert np.max(np.abs(L - Lx)) < 1e-11
+    assert abs(oracle.logdet(L) - ld) < 1e-9 * abs(ld)
+
+
+def test_integer_unit_lower_factor_is_exact():
+    rng = np.random.default_rng(3)
+    n = 160
+    L = np.tril(rng.integers(-1, 2, (n, n)).astype(np.float64), -1) + np.eye(n)
+    A = L @ L.T                                  # exact integers
+    assert np.array_equal(oracle.cholesky(A), L)
+
+
+def _laplace_det(M):
+    n = len(M)
+    if n == 1:
+        return M[0][0]
+    return sum((-1) ** j * M[0][j] * _laplace_det([row[:j] + row[j + 1:] for row in M[1:]])
+               for j in range(n) if M[0][j] != 0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+def test_logdet_matches_brute_force_determinant(n):
+    rng = np.random.default_rng(n)
+    G = rng.integers(-3, 4, (n, n))
+    A = G @ G.T + n * np.eye(n, dtype=np.int64)  # integer SPD
+    det = _laplace_det([[Fraction(int(v)) for v in row] for row in A])
+    L = oracle.cholesky(A.astype(np.float64))
+    assert abs(oracle.logdet(L) - math.log(float(det))) < 1e-12 * max(1.0, math.log(float(det)))
+
+
+def test_backward_error_and_solve_on_matern():
+    pts = inputs.uniform_points(700, seed=7)
+    A = oracle.matern(pts, 1.0, 0.1, 1.5, nugget=1e-3)
+    L = oracle.cholesky(A)
+    n = A.shape[0]
+    u = 2.0 ** -53
+    assert np.linalg.norm(A - L @ L.T) / np.linalg.norm(A) < 4 * n * u
+    B = inputs.gaussian(n, 3, seed=8)
+    X = oracle.solve(L, B)
+    berr = np.linalg.norm(B - A @ X) / (np.linalg.norm(A) * np.linalg.norm(X) + np.linalg.norm(B))
+    assert berr < 4 * n * u
+
+
+def test_not_spd_reports_first_bad_column():
+    A = np.eye(6)
+    A[3, 3] = -1.0
+    _, info = oracle.cholesky(A, return_info=True)
+    assert info == 4
+
+
+# ---------------------------------------------------------------- Eq. 1 - 3
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+def test_matern_closed_forms_equal_bessel_form(nu):
+    pts = inputs.uniform_points(120, seed=5)
+    A = oracle.matern(pts, 1.7, 0.08, nu, nugget=1e-4)
+    B = oracle.matern_bessel(pts, 1.7, 0.08, nu, nugget=1e-4)
+    assert np.allclose(A, B, rtol=1e-12, atol=1e-300)
+
+
+def test_loglik_matches_scipy_gaussian_logpdf():
+    from scipy.stats import multivariate_normal
+    pts = inputs.uniform_points(150, seed=9)
+    A = oracle.matern(pts, 1.0, 0.1, 0.5, nugget=1e-2)
+    y = inputs.gaussian(150, 1, seed=10)[:, 0]
+    L = oracle.cholesky(A)
+    ref = multivariate_normal(mean=np.zeros(150), cov=A).logpdf(y)
+    assert abs(oracle.loglik(L, y) - ref) < 1e-9 * abs(ref)
+
+
+def test_loglik_whitened_identity():
+    # y = L z  =>  y^T Sigma^{-1} y = z^T z
+    pts = inputs.uniform_points(200, seed=12)
+    A = oracle.matern(pts, 1.0, 0.05, 1.5, nugget=1e-3)
+    L = oracle.cholesky(A)
+    z = inputs.gaussian(200, 1, seed=13)[:, 0]
+    ll = oracle.loglik(L, L @ z)
+    expect = -100 * math.log(2 * math.pi) - 0.5 * oracle.logdet(L) - 0.5 * float(z @ z)
+    assert abs(ll - expect) < 1e-9 * abs(expect)
+
+
+def test_kl_matches_scipy_logpdf_difference():
+    from scipy.stats import multivariate_normal
+    pts = inputs.uniform_points(80, seed=14)
+    A0 = oracle.matern(pts, 1.0, 0.1, 0.5, nugget=1e-2)
+    Aa = A0 * (1 + 1e-3) + 1e-4 * np.eye(80)
+    ref = (multivariate_normal(cov=A0).logpdf(np.zeros(80)) - multivariate_normal(cov=Aa).logpdf(np.zeros(80)))
+    d = oracle.kl_divergence(oracle.logdet(oracle.cholesky(A0)), oracle.logdet(oracle.cholesky(Aa)))
+    assert abs(d - ref) < 1e-9
+
+
+# ---------------------------------------------------------------- tile storage
+def test_pack_layout_by_hand():
+    n, b = 6, 2
+    A = np.arange(n * n, dtype=np.float64).reshape(n, n)
+    P = oracle.pack_tiles(A, b)
+    assert P.shape == (6, 4)
+    # tile (2, 1) is index 2*3/2 + 1 = 4; column-major: (r, c) at c*b + r
+    assert list(P[4]) == [A[4, 2], A[5, 2], A[4, 3], A[5, 3]]
+    assert list(P[0]) == [0.0, 6.0, 1.0, 7.0]
+    S = oracle.unpack_tiles(P, n, b, symmetric=False)
+    assert np.array_equal(S, np.tril(A) * (np.add.outer(np.arange(n) // b, -(np.arange(n) // b)) >= 0))
+
+
+# ---------------------------------------------------------------- rounding
+def _sample_values(rng, lo_exp, hi_exp, m=20000):
+    e = rng.uniform(lo_exp, hi_exp, m)
+    v = np.exp2(e) * rng.choice([-1.0, 1.0], m)
+    return v
+
+
+def test_round_fp32_matches_numpy_cast():
+    rng = np.random.default_rng(0)
+    v = _sample_values(rng, -140, 100)
+    assert np.array_equal(oracle.round_to(v, FP32), v.astype(np.float32).astype(np.float64))
+
+
+def test_round_fp16_matches_numpy_cast_including_ties_and_subnormals():
+    rng = np.random.default_rng(1)
+    v = _sample_values(rng, -26, 15.9)
+    ties = (np.arange(1, 2000) + 0.5) * 2.0 ** -24      # exact halfway points in the subnormal range
+    ties2 = (1024 + np.arange(0, 500) + 0.5) * 2.0 ** -10  # halfway points in [1, 2)
+    v = np.concatenate([v, ties, -ties2, [0.0, 65504.0, -65504.0]])
+    assert np.array_equal(oracle.round_to(v, FP16), v.astype(np.float16).astype(np.float64))
+
+
+def test_round_e4m3_matches_torch_cast():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(2)
+    v = _sample_values(rng, -11, 8.8)
+    v = v[np.abs(v) <= 448.0]
+    grid = np.array([m * 2.0 ** e for e in range(-9, 9) for m in np.arange(8, 16) / 8.0])
+    mids = (grid[:-1] + grid[1:]) / 2                 # ties
+    v = np.concatenate([v, mids[mids <= 448], -mids[mids <= 448], [0.0, 448.0, 2.0 ** -9, 2.0 ** -10 * 3]])
+    ref = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(oracle.round_to(v, FP8), ref)
+
+
+def test_scale_exponent_by_hand():
+    assert oracle.scale_exponent(448.0, FP8) == 0
+    assert oracle.scale_exponent(448.0001, FP8) == 1
+    assert oracle.scale_exponent(224.0, FP8) == -1
+    assert oracle.scale_exponent(1.0, FP8) == -8        # 448 / 256 = 1.75 >= 1 > 0.875
+    assert oracle.scale_exponent(1.0, FP16) == -15      # 65504 / 32768 = 1.999 >= 1 > 0.9995
+    assert oracle.scale_exponent(0.0, FP8) == 0
+    assert oracle.scale_exponent(3.0, FP32) == 0
+
+
+def test_storage_round_trip_error_bounds():
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal((64, 64)) * 1e-7
+    for fmt in (FP32, FP16, FP8):
+        s = oracle.to_storage(v, fmt)
+        e = oracle.scale_exponent(float(np.abs(v).max()), fmt)
+        # relative error of normal values <= u; scaled so the largest entry is normal
+        big = np.abs(v) >= 2.0 ** (oracle.FORMATS[fmt][1] + e)
+        assert np.all(np.abs(s - v)[big] <= oracle.UNIT_ROUNDOFF[fmt] * np.abs(v)[big] * (1 + 1e-12))
+        assert np.max(np.abs(s)) <= oracle.FORMATS[fmt][2] * 2.0 ** e
+    assert oracle.as_operand(oracle.to_storage(v, FP8), FP8, FP16) is not None
+    s8 = oracle.to_storage(v, FP8)
+    assert np.array_equal(oracle.as_operand(s8, FP8, FP16), s8)   # widening is exact
+    assert np.array_equal(oracle.as_operand(s8, FP8, FP64), s8)
+
+
+# ---------------------------------------------------------------- criterion
+def test_precision_map_worked_example():
+    # n = 8, b = 2 (Nt = 4); A = 10 I plus one entry c in tiles (2,0), (3,0), (3,1) and
+    # their mirror images.  ||A||_F = sqrt(800 + 2(1e-8 + 1e-14 + 1e-4)) = 28.28427...
+    # ratio = 4 c / ||A||_F = 0.1414 c.  eps_high = 1e-6: thresholds eps/u are
+    # FP8 1.6e-5, FP16 2.048e-3, FP32 16.78.
+    A = 10.0 * np.eye(8)
+    for (i, j), c in {(2, 0): 1e-4, (3, 0): 1e-7, (3, 1): 1e-2}.items():
+        A[2 * i, 2 * j] = A[2 * j, 2 * i] = c
+    pm = oracle.precision_map(A, 2, 1e-6, band=1, prec_set=4)
+    expect = np.array([[0, 0, 0, 0],
+                       [0, 0, 0, 0],
+                       [FP8, 0, 0, 0],
+                       [FP8, FP16, 0, 0]], dtype=np.uint8)
+    assert np.array_equal(pm, expect)
+    # without a band, the all-zero tiles (1,0), (2,1), (3,2) pass the FP8 test
+    pm0 = oracle.precision_map(A, 2, 1e-6, band=0, prec_set=4)
+    assert pm0[1, 0] == FP8 and pm0[2, 1] == FP8 and pm0[3, 2] == FP8
+    # three precisions: FP8 is not allowed, the tiny tiles fall back to FP16
+    pm3 = oracle.precision_map(A, 2, 1e-6, band=1, prec_set=3)
+    assert pm3[2, 0] == FP16 and pm3[3, 0] == FP16 and pm3[3, 1] == FP16
+    # two precisions: FP32 only
+    pm2 = oracle.precision_map(A, 2, 1e-6, band=1, prec_set=2)
+    assert pm2[2, 0] == FP32 and pm2[3, 1] == FP32
+    # a stricter accuracy level pushes (3,1) (ratio 1.4e-3) up: 1e-8/u16 = 2.0e-5 -> FP32
+    pm8 = oracle.precision_map(A, 2, 1e-8, band=1, prec_set=4)
+    assert pm8[3, 1] == FP32 and pm8[3, 0] == FP8 and pm8[2, 0] == FP16
+    assert np.all(np.triu(pm8) == 0)
+
+
+# ---------------------------------------------------------------- Algorithm 1, MxP
+def _matern_case(n=512, seed=21, nu=1.5, a=0.03, nugget=1e-4):
+    pts = inputs.uniform_points(n, seed, morton=True)
+    return oracle.matern(pts, 1.0, a, nu, nugget)
+
+
+def test_mxp_all_fp64_reduces_to_cholesky():
+    A = _matern_case(384)
+    pm = np.zeros((6, 6), dtype=np.uint8)
+    L, info = oracle.mxp_cholesky(A, 64, pm)
+    assert info == 0
+    Lref = oracle.cholesky(A)
+    assert np.max(np.abs(L - Lref)) < 1e-12
+
+
+def test_mxp_integer_factor_is_exact_in_every_precision():
+    # L with entries in {-1, 0, 1} and unit diagonal: every operand, product and sum is
+    # exact in FP8/FP16/FP32, so any precision map must return L exactly.
+    rng = np.random.default_rng(9)
+    n, b = 96, 16
+    L = np.tril(rng.integers(-1, 2, (n, n)).astype(np.float64), -1) + np.eye(n)
+    A = L @ L.T
+    nt = n // b
+    pm = np.zeros((nt, nt), dtype=np.uint8)
+    for i in range(nt):
+        for j in range(i):
+            pm[i, j] = [FP32, FP16, FP8][(i + 2 * j) % 3]
+    Lm, info = oracle.mxp_cholesky(A, b, pm)
+    assert info == 0
+    assert np.array_equal(Lm, L)
+
+
+def test_mxp_backward_error_tracks_accuracy_level():
+    A = _matern_case(512, nu=0.5, a=0.02, nugget=1e-4)
+    b = 32
+    errs = {}
+    for eps in (1e-4, 1e-7):
+        pm = oracle.precision_map(A, b, eps, band=1, prec_set=4)
+        assert np.any(pm > 0)
+        L, info = oracle.mxp_cholesky(A, b, pm)
+        assert info == 0
+        errs[eps] = np.linalg.norm(A - L @ L.T) / np.linalg.norm(A)
+        assert errs[eps] < 10 * eps
+    assert errs[1e-7] < errs[1e-4]
+
+
+def test_mxp_low_precision_tiles_are_stored_values():
+    A = _matern_case(256, nu=0.5, a=0.02)
+    b = 32
+    pm = oracle.precision_map(A, b, 1e-4, band=1, prec_set=4)
+    L, _ = oracle.mxp_cholesky(A, b, pm)
+    nt = 256 // b
+    for i, j in itertools.product(range(nt), range(nt)):
+        if i > j and pm[i, j] in (FP16, FP8):
+            t = L[i * b:(i + 1) * b, j * b:(j + 1) * b]
+            assert np.array_equal(oracle.to_storage(t, int(pm[i, j])), t)
+        if i > j and pm[i, j] == FP32:
+            t = L[i * b:(i + 1) * b, j * b:(j + 1) * b]
+            assert np.array_equal(t.astype(np.float32).astype(np.float64), t)
