@@ -1,0 +1,186 @@
+/*
+ * tile_chol -- mixed-precision left-looking tile Cholesky for one GB300 (sm_103a).
+ *
+ * C ABI.  Every entry point returns an int status: TC_OK (0), a negative TC_ERR_*
+ * code, or a positive value: the 1-based global column at which the factorization met
+ * a pivot that was not positive (the matrix is not numerically SPD; LAPACK's "info"
+ * convention -- the paper does not define failure).  No exception or abort crosses
+ * this boundary; after TC_ERR_CUDA the message is available from tc_last_error().
+ *
+ * Problem (arXiv 2410.09819, Section III-A): A = L L^T for a symmetric positive
+ * definite n x n matrix A, by the left-looking tile algorithm of Algorithm 1, with a
+ * per-tile precision map (Section IV-C) and out-of-core tile caching (Section IV-B,
+ * Algorithms 2 and 3) when the matrix does not fit the device.
+ *
+ * Tile layout ("lower tile-major"), used for every matrix argument named *_tiles:
+ *   b = tile size (a multiple of 64, 64 <= b <= 4096), Nt = ceil(n / b),
+ *   T = Nt (Nt + 1) / 2 tiles;
+ *   tile (i, j), i >= j, starts at element (i (i + 1) / 2 + j) * b * b;
+ *   inside a tile, element (r, c) is at c * b + r (column-major, leading dimension b).
+ *   Only lower tiles are stored.  Diagonal tiles hold the full b x b symmetric block.
+ *   When n is not a multiple of b, the rows and columns of the last tile row/column
+ *   beyond n are padding: the library ignores what the caller stores there and treats
+ *   the padded matrix as diag(A, I), which leaves L and log|A| unchanged.
+ *
+ * Memory: a pointer argument may be host or device memory unless stated otherwise;
+ * the library asks the CUDA runtime which it is.  Host buffers are best page-locked
+ * (cudaHostAlloc); pageable memory works but copies slower.  The caller keeps
+ * ownership of every buffer it passes.  The handle owns its device workspace (the
+ * factor, the per-precision operand copies, the out-of-core tile cache) and its
+ * streams; it is released by tc_destroy().
+ *
+ * Streams and threads: all device work of a handle runs on the stream given in
+ * tc_config.stream (or one the handle creates), plus internal copy streams that
+ * synchronise with it through events.  Calls return after the work they start has
+ * completed unless stated otherwise.  A handle must not be used by two host threads
+ * at once.
+ */
+#ifndef TILE_CHOL_H
+#define TILE_CHOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Tile precision codes used in precision maps (Section IV-C, Fig. 4). */
+enum { TC_FP64 = 0, TC_FP32 = 1, TC_FP16 = 2, TC_FP8 = 3 };
+
+/* Status codes. */
+enum {
+    TC_OK = 0,
+    TC_ERR_ARG = -1,        /* an argument is out of range or NULL where not allowed */
+    TC_ERR_STATE = -2,      /* call order: e.g. solve before a successful factor */
+    TC_ERR_CUDA = -100,     /* a CUDA call failed; see tc_last_error() */
+    TC_ERR_OOM = -101,      /* device memory (or the configured cache cap) too small */
+    TC_ERR_TIMEOUT = -102,  /* a bounded device-side wait gave up */
+    TC_ERR_HOSTMEM = -103,  /* page-locked host memory could not be allocated */
+    TC_ERR_UNSUPPORTED = -104 /* a configuration this build does not provide */
+};
+
+typedef struct tc_handle_s *tc_handle;
+
+/* Handle configuration.  Fill with tc_config_default() and override fields. */
+typedef struct {
+    int device;                 /* CUDA device ordinal (default 0) */
+    void *stream;               /* cudaStream_t to run on; NULL: the handle makes one */
+    int ooc;                    /* 0: out-of-core only when the factor does not fit,
+                                   1: always out-of-core, -1: never (TC_ERR_OOM instead) */
+    int64_t device_cap_bytes;   /* out-of-core device tile-cache cap; 0: free memory - 4 GiB */
+    int prefetch_depth;         /* out-of-core: tasks of look-ahead for tile prefetch (>= 1) */
+    int lookahead;              /* 1: overlap column k+1's independent updates with the
+                                   panel of column k on a second stream (default 1) */
+    int reserved[8];
+} tc_config;
+
+/* Per-call statistics (any field a call does not produce is left 0). */
+typedef struct {
+    double t_ms;                /* wall time of the call, device-synchronised */
+    double flops;               /* n^3/3, the algorithmic count of the factorization */
+    double update_flops[4];     /* SYRK/GEMM flops executed per output precision */
+    double trsm_flops, potrf_flops;
+    int64_t tiles[4];           /* lower off-diagonal + diagonal tiles per precision */
+    int64_t h2d_bytes, d2h_bytes;           /* out-of-core host<->device traffic */
+    int64_t cache_hits, cache_misses, evictions;
+    int64_t kernel_launches;    /* kernels this call launched */
+    int refine_iters;           /* solve: refinement steps taken */
+    double berr;                /* solve: final normwise backward error (max over RHS) */
+    int info;                   /* same as the return value for factor calls */
+    int ooc;                    /* 1 if the call ran out-of-core */
+} tc_stats;
+
+/* Defaults: device 0, own stream, ooc auto, cap 0 (auto), prefetch 2, lookahead 1. */
+void tc_config_default(tc_config *cfg);
+
+/* Create a handle on cfg->device.  cfg may be NULL (defaults).  *out is set on TC_OK. */
+int tc_create(tc_handle *out, const tc_config *cfg);
+
+/* Release every device and host resource of the handle (NULL is allowed). */
+void tc_destroy(tc_handle h);
+
+/* Message of the last failing call of this handle ("" if none).  Owned by the handle. */
+const char *tc_last_error(tc_handle h);
+
+/*
+ * Synthetic covariance, Eq. 2 (Section III-D): writes the lower tiles of
+ *   Sigma_ij = sigma2 / (2^(nu-1) Gamma(nu)) (h/a)^nu K_nu(h/a) + nugget [i == j],
+ * h = |s_i - s_j|, for nu in {0.5, 1.5, 2.5} (closed forms e^-x, (1+x)e^-x,
+ * (1+x+x^2/3)e^-x with x = h/a).  points: n x 2 row-major doubles (x_i, y_i).
+ * A_tiles: output, T b*b doubles in the tile layout above (padding set to identity).
+ * Errors: TC_ERR_ARG for n < 1, b not in [64, 4096] or not a multiple of 64, a <= 0,
+ * sigma2 <= 0 or another nu.
+ */
+int tc_matern_tiles(tc_handle h, int64_t n, int b, const double *points,
+                    double sigma2, double range_a, double nu, double nugget,
+                    double *A_tiles);
+
+/*
+ * Per-tile precision map, Section IV-C: tile (i, j), i > j, gets the lowest format p
+ * in the allowed set with  Nt ||A_ij||_F / ||A||_F < eps_high / u_p,  where u_p is the
+ * unit roundoff of p (FP32 2^-24, FP16 2^-11, FP8 E4M3 2^-4) and ||A||_F is taken over
+ * the full symmetric matrix; otherwise FP64.  Diagonal tiles and tiles with
+ * 1 <= i - j <= band stay FP64.  prec_set 1..4 allows {64}, {64,32}, {64,32,16},
+ * {64,32,16,8} (Fig. 4).  Norms are FP64, computed on the device from A_tiles.
+ * map_out: host or device, Nt*Nt bytes, row-major, entries TC_FP* (upper part 0).
+ * norms_out: optional (NULL allowed), Nt*Nt doubles (tile Frobenius norms, lower part)
+ * followed by one double ||A||_F.
+ */
+int tile_chol_precision_map(tc_handle h, int64_t n, int b, const double *A_tiles,
+                            double eps_high, int band, int prec_set,
+                            uint8_t *map_out, double *norms_out);
+
+/*
+ * Factor A = L L^T (Algorithm 1, left-looking, per-tile precision).
+ * A_tiles: the caller's matrix in the tile layout, host or device; it is read, never
+ *   written, and must stay valid (unchanged) until the handle's next factor or
+ *   destroy, because tile_chol_solve's refinement reads it.
+ * map: NULL for all-FP64, else Nt*Nt bytes (host or device) as produced by
+ *   tile_chol_precision_map; the diagonal is treated as FP64 whatever it holds.
+ *   Each update C_mk -= sum_{n<k} L_mn L_kn^T runs in the precision of its output
+ *   tile p(m, k): operand tiles stored wider are rounded to it (RNE, fresh power-of-two
+ *   scale for FP16/FP8), narrower ones are widened exactly.  FP64 updates use DFMA;
+ *   FP32 updates run as three TF32 tensor-core products (hi*hi + hi*lo + lo*hi),
+ *   FP16 and FP8 (E4M3) on the tensor cores, all with FP32 accumulation.  POTRF and
+ *   TRSM are FP64; each final L_mk is then stored in p(m, k).
+ * Runs in device memory when the factor fits (or cfg.ooc == -1), else out-of-core
+ *   with A_tiles in host memory (Section III-C/IV-B; see tc_config).
+ * Returns TC_OK, a positive column (not SPD), or an error.  stats may be NULL.
+ */
+int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles,
+                     const uint8_t *map, tc_stats *stats);
+
+/*
+ * Solve A X = B with the last factor: forward (L Z = B) and back (L^T X = Z)
+ * substitution in FP64, then up to max_refine steps of iterative refinement
+ * R = B - A X (FP64, with the caller's A), X += solve(R), stopping once the normwise
+ * backward error max_c ||R_c||_inf / (||A||_inf ||X_c||_inf + ||B_c||_inf) <= target_berr.
+ * B, X: n x nrhs column-major with leading dimensions ldb, ldx >= n; host or device;
+ * X may equal B.  Requires a successful tile_chol_factor (else TC_ERR_STATE).
+ */
+int tile_chol_solve(tc_handle h, int nrhs, const double *B, int64_t ldb,
+                    double *X, int64_t ldx, int max_refine, double target_berr,
+                    tc_stats *stats);
+
+/* log|A| = 2 sum_i log L_ii of the last factor (needed by Eq. 1). */
+int tile_chol_logdet(tc_handle h, double *logdet_out);
+
+/*
+ * Gaussian log-likelihood of Eq. 1 for the last factor:
+ *   l = -n/2 log(2 pi) - 1/2 log|A| - 1/2 ||L^{-1} y||^2.
+ * y: n doubles, host or device.  y == NULL evaluates Eq. 1 at y = 0 (the form used by
+ * the KL divergence of Eq. 3).
+ */
+int tile_chol_loglik(tc_handle h, const double *y, double *loglik_out);
+
+/*
+ * Copy the last factor out as FP64 values of the stored tiles (tile layout; upper
+ * triangles of diagonal tiles and padding are written as 0).  L_tiles: host or device.
+ */
+int tile_chol_get_factor(tc_handle h, double *L_tiles);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TILE_CHOL_H */

@@ -1,0 +1,565 @@
+// FP64 kernels of the tile Cholesky: SYRK/GEMM updates (Algorithm 1's inner n-loop,
+// Section III-A), the diagonal POTRF, the panel TRSM, and the substitution / residual
+// kernels of the solve.  GB300's FP64 pipe issues about two DFMA per clock per SM
+// (~1.05 TFLOP/s for the chip), so these kernels are DFMA-bound by a wide margin: the
+// 64 x 64 register-blocked tile below keeps the pipe saturated from one CTA per SM.
+#include "tc_internal.h"
+
+#include <cmath>
+
+namespace tc {
+
+// acc (rows tx + 16 i, columns ty + 16 j of a 64 x 64 block) += X[:, k0:k1] Y[:, k0:k1]^T.
+// X and Y point at the block's first row/column; column l of each is at l * ld.
+__device__ __forceinline__ void dgemm_block(double (&acc)[4][4], const double *__restrict__ X,
+                                            const double *__restrict__ Y, int ld, int k0, int k1,
+                                            double (*Xs)[64], double (*Ys)[64]) {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int k = k0; k < k1; k += 16) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = tid + 256 * e, l = idx >> 6, r = idx & 63;
+            const bool ok = (k + l) < k1;
+            Xs[l][r] = ok ? X[(int64_t)(k + l) * ld + r] : 0.0;
+            Ys[l][r] = ok ? Y[(int64_t)(k + l) * ld + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < 16; ++l) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Xs[l][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Ys[l][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ bool failed(const int *status) {
+    return status && *(volatile const int *)status != 0;
+}
+
+// ----------------------------------------------------------------------------- updates
+__global__ void __launch_bounds__(256, 2)
+k_dgemm_update(const DJob *__restrict__ jobs, const DItem *__restrict__ items, int ld,
+               double *__restrict__ partials, const int *status) {
+    if (failed(status)) return;
+    __shared__ double Xs[16][64], Ys[16][64];
+    const DItem it = items[blockIdx.x];
+    const DJob jb = jobs[it.job];
+    const int i0 = it.bi * 64, j0 = it.bj * 64;
+    double acc[4][4] = {};
+    dgemm_block(acc, jb.X + i0, jb.Y + j0, ld, it.k0, it.k1, Xs, Ys);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (it.part < 0) {
+        double *C = jb.C + (int64_t)j0 * ld + i0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) C[(int64_t)(ty + 16 * j) * ld + tx + 16 * i] -= acc[i][j];
+    } else {
+        double *P = partials + (int64_t)it.part * 4096;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) P[(ty + 16 * j) * 64 + tx + 16 * i] = acc[i][j];
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_dgemm_reduce(const DRed *__restrict__ reds, int ld, const double *__restrict__ partials,
+               const int *status) {
+    if (failed(status)) return;
+    const DRed r = reds[blockIdx.x];
+    for (int e = 0; e < 16; ++e) {
+        const int idx = threadIdx.x + 256 * e, rr = idx & 63, cc = idx >> 6;
+        double s = 0.0;
+        for (int p = 0; p < r.nparts; ++p) s += partials[(int64_t)(r.part0 + p) * 4096 + cc * 64 + rr];
+        r.C[(int64_t)cc * ld + rr] -= s;
+    }
+}
+
+// ------------------------------------------------------------------------------- POTRF
+// Factor the 64 x 64 lower block at D in place (right-looking in shared memory).  A
+// non-positive pivot records the 1-based global column in *status and stops.
+__global__ void __launch_bounds__(256) k_potrf_block(double *D, int ld, int col0, int *status) {
+    if (failed(status)) return;
+    __shared__ double S[64][65];
+    __shared__ int fail;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < 4096; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        S[r][c] = (r >= c) ? D[(int64_t)c * ld + r] : 0.0;
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int j = 0; j < 64; ++j) {
+        if (tid == 0) {
+            const double d = S[j][j];
+            if (!(d > 0.0)) fail = j + 1;
+            else S[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail) break;
+        const double p = S[j][j];
+        if (tid > j && tid < 64) S[tid][j] = S[tid][j] / p;
+        __syncthreads();
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int r = idx & 63, c = idx >> 6;
+            if (c > j && r >= c) S[r][c] = S[r][c] - S[r][j] * S[c][j];
+        }
+        __syncthreads();
+    }
+    if (fail) {
+        if (tid == 0) atomicCAS(status, 0, col0 + fail);
+        return;
+    }
+    for (int idx = tid; idx < 4096; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        if (r >= c) D[(int64_t)c * ld + r] = S[r][c];
+    }
+}
+
+// Right-side solve of a 64-row strip held in shared memory: X L^T = S in place, L the
+// 64 x 64 lower block in Ls.  Column j: X[r][j] = (S[r][j] - sum_{l<j} X[r][l] L[j][l]) / L[j][j],
+// applied right-looking (after X[:, j] is known, S[:, c] -= X[:, j] L[c][j] for c > j).
+__device__ __forceinline__ void strip_solve(double (*Ss)[65], double (*Ls)[65]) {
+    const int tid = threadIdx.x;
+    for (int j = 0; j < 64; ++j) {
+        if (tid < 64) Ss[tid][j] = Ss[tid][j] / Ls[j][j];
+        __syncthreads();
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int r = idx & 63, c = idx >> 6;
+            if (c > j) Ss[r][c] = Ss[r][c] - Ss[r][j] * Ls[c][j];
+        }
+        __syncthreads();
+    }
+}
+
+// POTRF panel: rows below the factored 64-block within the diagonal tile.
+__global__ void __launch_bounds__(256) k_trsm_rows(double *P, const double *L, int ld, const int *status) {
+    if (failed(status)) return;
+    __shared__ double Ls[64][65], Ss[64][65];
+    const int tid = threadIdx.x;
+    double *Pb = P + blockIdx.x * 64;
+    for (int idx = tid; idx < 4096; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        Ls[r][c] = (r >= c) ? L[(int64_t)c * ld + r] : 0.0;
+        Ss[r][c] = Pb[(int64_t)c * ld + r];
+    }
+    __syncthreads();
+    strip_solve(Ss, Ls);
+    for (int idx = tid; idx < 4096; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        Pb[(int64_t)c * ld + r] = Ss[r][c];
+    }
+}
+
+// Column TRSM (Algorithm 1: A_mk = A_mk L_kk^{-T}): one CTA per 64-row strip of a tile,
+// left-looking over the 64-column blocks of L_kk.
+__global__ void __launch_bounds__(256, 2)
+k_trsm_strips(const TStrip *__restrict__ strips, int ld, int b, const int *status) {
+    if (failed(status)) return;
+    extern __shared__ double smem[];
+    double(*Xs)[64] = reinterpret_cast<double(*)[64]>(smem);
+    double(*Ys)[64] = reinterpret_cast<double(*)[64]>(smem + 16 * 64);
+    double(*Ls)[65] = reinterpret_cast<double(*)[65]>(smem + 32 * 64);
+    double(*Ss)[65] = reinterpret_cast<double(*)[65]>(smem + 32 * 64 + 64 * 65);
+    const TStrip st = strips[blockIdx.x];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double *X = st.C + st.r0;
+    for (int jb = 0; jb < b / 64; ++jb) {
+        double acc[4][4] = {};
+        dgemm_block(acc, X, st.L + jb * 64, ld, 0, jb * 64, Xs, Ys);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                Ss[tx + 16 * i][ty + 16 * j] = X[(int64_t)(jb * 64 + ty + 16 * j) * ld + tx + 16 * i] - acc[i][j];
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int r = idx & 63, c = idx >> 6;
+            Ls[r][c] = (r >= c) ? st.L[(int64_t)(jb * 64 + c) * ld + jb * 64 + r] : 0.0;
+        }
+        __syncthreads();
+        strip_solve(Ss, Ls);
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int r = idx & 63, c = idx >> 6;
+            X[(int64_t)(jb * 64 + c) * ld + r] = Ss[r][c];
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------------- tile bookkeeping
+__device__ __forceinline__ double *diag_tile(double *W, int t, int b) {
+    return W + ((int64_t)t * (t + 1) / 2 + t) * (int64_t)b * b;
+}
+
+// log|A| = 2 sum log L_ii over the n valid diagonal entries, fixed summation order.
+__global__ void __launch_bounds__(1024) k_logdet(const double *W, int b, int64_t n, double *out) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int64_t g = threadIdx.x; g < n; g += 1024) {
+        const int t = (int)(g / b), r = (int)(g % b);
+        const double *D = W + ((int64_t)t * (t + 1) / 2 + t) * (int64_t)b * b;
+        s += log(D[(int64_t)r * b + r]);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = 2.0 * red[0];
+}
+
+// Padding of the last tile row: rows/columns >= n become those of the identity.
+__global__ void k_fix_padding(double *W, int nt, int b, int64_t n) {
+    const int j = blockIdx.y;                       // tile column in the last tile row
+    const int i = nt - 1;
+    const int nv = (int)(n - (int64_t)i * b);      // valid rows of the last tile row
+    double *T = W + ((int64_t)i * (i + 1) / 2 + j) * (int64_t)b * b;
+    const int64_t bb = (int64_t)b * b;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % b), c = (int)(e / b);
+        if (j < i) {
+            if (r >= nv) T[e] = 0.0;
+        } else if (r >= nv || c >= nv) {
+            T[e] = (r == c) ? 1.0 : 0.0;
+        }
+    }
+}
+
+// Export clean-up: strictly upper parts of diagonal tiles and all padding become 0.
+__global__ void k_zero_upper_diag(double *W, int nt, int b, int64_t n) {
+    const int t = blockIdx.y;
+    const int64_t bb = (int64_t)b * b;
+    const int nv_last = (int)(n - (int64_t)(nt - 1) * b);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % b), c = (int)(e / b);
+        if (t < nt) {  // diagonal tile t
+            double *D = W + ((int64_t)t * (t + 1) / 2 + t) * bb;
+            const bool pad = (t == nt - 1) && (r >= nv_last || c >= nv_last);
+            if (c > r || pad) D[e] = 0.0;
+        } else {       // off-diagonal tile (nt-1, j) of the last tile row, j = t - nt
+            const int j = t - nt, i = nt - 1;
+            double *T = W + ((int64_t)i * (i + 1) / 2 + j) * bb;
+            if (r >= nv_last) T[e] = 0.0;
+        }
+    }
+}
+
+// Sum the four per-part accumulators of each row in a fixed order and subtract them from
+// R[q * ldr + g0 + r] (rows r of a 64-row chunk, RHS q < nrhs).
+__device__ __forceinline__ void part_reduce_sub(double (*red)[17], const double (&acc)[16], int nrhs,
+                                                double *R, int64_t ldr, int64_t g0) {
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    for (int p = 0; p < 4; ++p) {
+        __syncthreads();
+        if (part == p)
+            for (int q = 0; q < nrhs; ++q) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < 64 * nrhs; e += 256) {
+        const int r = e % 64, q = e / 64;
+        R[q * ldr + g0 + r] -= red[r][q];
+    }
+}
+
+// -------------------------------------------------------------------------------- solves
+// Forward substitution with one diagonal tile: L_jj z = r for each RHS column.
+__global__ void __launch_bounds__(256) k_fwd_diag(const double *L, int b, double *R, int64_t ldr) {
+    __shared__ double z[4096];
+    __shared__ double red[4][64];
+    __shared__ double blk[64];
+    double *r = R + blockIdx.x * ldr;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < b; i += 256) z[i] = r[i];
+    __syncthreads();
+    const int rr = tid & 63, part = tid >> 6;
+    for (int jb = 0; jb < b / 64; ++jb) {
+        double s = 0.0;
+        for (int l = part; l < jb * 64; l += 4) s += L[(int64_t)l * b + jb * 64 + rr] * z[l];
+        red[part][rr] = s;
+        __syncthreads();
+        if (tid < 64) blk[tid] = z[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+        __syncthreads();
+        for (int jj = 0; jj < 64; ++jj) {
+            if (tid == jj) blk[jj] = blk[jj] / L[(int64_t)(jb * 64 + jj) * b + jb * 64 + jj];
+            __syncthreads();
+            if (tid > jj && tid < 64) blk[tid] -= L[(int64_t)(jb * 64 + jj) * b + jb * 64 + tid] * blk[jj];
+            __syncthreads();
+        }
+        if (tid < 64) z[jb * 64 + tid] = blk[tid];
+        __syncthreads();
+    }
+    for (int i = tid; i < b; i += 256) r[i] = z[i];
+}
+
+// r_i -= L_ij z_j for every tile row i > j; one CTA per 64-row chunk of a tile row.
+__global__ void __launch_bounds__(256)
+k_fwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
+    __shared__ double zs[128][16];
+    __shared__ double red[64][17];
+    const int chunks = b / 64;
+    const int i = j + 1 + blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * 64;
+    const double *L = W + ((int64_t)i * (i + 1) / 2 + j) * (int64_t)b * b;
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int c0 = 0; c0 < b; c0 += 128) {
+        __syncthreads();
+        for (int e = tid; e < 128 * nrhs; e += 256) {
+            const int c = e % 128, q = e / 128;
+            zs[c][q] = R[q * ldr + (int64_t)j * b + c0 + c];
+        }
+        __syncthreads();
+        for (int c = part; c < 128; c += 4) {
+            const double l = L[(int64_t)(c0 + c) * b + r0 + rr];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q < nrhs) acc[q] = fma(l, zs[c][q], acc[q]);
+        }
+    }
+    part_reduce_sub(red, acc, nrhs, R, ldr, (int64_t)i * b + r0);
+}
+
+// Back substitution with one diagonal tile: L_jj^T x = z for each RHS column (in place).
+__global__ void __launch_bounds__(256) k_bwd_diag(const double *L, int b, double *R, int64_t ldr) {
+    __shared__ double S[64][65];
+    __shared__ double red[4][64];
+    __shared__ double blk[64];
+    double *x = R + blockIdx.x * ldr;
+    const int tid = threadIdx.x;
+    const int rr = tid & 63, part = tid >> 6;
+    for (int jb = b / 64 - 1; jb >= 0; --jb) {
+        // s[r] = z[jb*64 + r] - sum_{l >= (jb+1)*64} L[l][jb*64 + r] x[l]
+        double s = 0.0;
+        for (int l0 = (jb + 1) * 64; l0 < b; l0 += 64) {
+            __syncthreads();
+            for (int idx = tid; idx < 4096; idx += 256) {
+                const int lr = idx & 63, rc = idx >> 6;
+                S[rc][lr] = L[(int64_t)(jb * 64 + rc) * b + l0 + lr];
+            }
+            __syncthreads();
+            for (int lr = part; lr < 64; lr += 4) s += S[rr][lr] * x[l0 + lr];
+        }
+        red[part][rr] = s;
+        __syncthreads();
+        if (tid < 64) blk[tid] = x[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int lr = idx & 63, rc = idx >> 6;
+            S[rc][lr] = L[(int64_t)(jb * 64 + rc) * b + jb * 64 + lr];  // S[r][l] = L[l][r]
+        }
+        __syncthreads();
+        for (int jj = 63; jj >= 0; --jj) {
+            if (tid == jj) blk[jj] = blk[jj] / S[jj][jj];
+            __syncthreads();
+            if (tid < jj) blk[tid] -= S[tid][jj] * blk[jj];
+            __syncthreads();
+        }
+        if (tid < 64) x[jb * 64 + tid] = blk[tid];
+        __syncthreads();
+    }
+}
+
+// z_i -= L_ji^T x_j for every tile row i < j; one CTA per 64-row chunk of tile row i.
+__global__ void __launch_bounds__(256)
+k_bwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
+    __shared__ double xs[64][16];
+    __shared__ double S[64][65];
+    const int chunks = b / 64;
+    const int i = blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * 64;
+    const double *L = W + ((int64_t)j * (j + 1) / 2 + i) * (int64_t)b * b;   // tile (j, i)
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int c0 = 0; c0 < b; c0 += 64) {
+        __syncthreads();
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int c = idx & 63, r = idx >> 6;
+            S[r][c] = L[(int64_t)(r0 + r) * b + c0 + c];      // (L_ji^T)[r][c] = L_ji[c][r]
+        }
+        for (int e = tid; e < 64 * nrhs; e += 256) {
+            const int c = e % 64, q = e / 64;
+            xs[c][q] = R[q * ldr + (int64_t)j * b + c0 + c];
+        }
+        __syncthreads();
+        for (int c = part; c < 64; c += 4) {
+            const double l = S[rr][c];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
+        }
+    }
+    part_reduce_sub(reinterpret_cast<double(*)[17]>(&S[0][0]), acc, nrhs, R, ldr, (int64_t)i * b + r0);
+}
+
+// R = B - A X (absmode 0) or R = |A| X (absmode 1, B unused) for the symmetric A held as
+// lower tiles; rows and columns >= n (padding) contribute nothing and R's padding is 0.
+__global__ void __launch_bounds__(256)
+k_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t ldx,
+             const double *B, int64_t ldb, double *R, int64_t ldr, int nrhs, int absmode) {
+    __shared__ double xs[64][16];
+    __shared__ double S[64][65];
+    const int chunks = b / 64;
+    const int i = blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * 64;
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    const int64_t bb = (int64_t)b * b;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int j = 0; j < nt; ++j) {
+        const bool lower = j <= i;
+        const double *T = lower ? A + ((int64_t)i * (i + 1) / 2 + j) * bb : A + ((int64_t)j * (j + 1) / 2 + i) * bb;
+        for (int c0 = 0; c0 < b; c0 += 64) {
+            __syncthreads();
+            for (int idx = tid; idx < 4096; idx += 256) {
+                const int lo = idx & 63, hi = idx >> 6;
+                double v;
+                int64_t gr, gc;
+                if (lower) {   // S[r][c] = A_ij[r0 + r][c0 + c], coalesced along r
+                    v = T[(int64_t)(c0 + hi) * b + r0 + lo];
+                    gr = (int64_t)i * b + r0 + lo; gc = (int64_t)j * b + c0 + hi;
+                    if (gr >= n || gc >= n) v = 0.0;
+                    S[lo][hi] = absmode ? fabs(v) : v;
+                } else {       // S[r][c] = A_ji[c0 + c][r0 + r], coalesced along c
+                    v = T[(int64_t)(r0 + hi) * b + c0 + lo];
+                    gr = (int64_t)i * b + r0 + hi; gc = (int64_t)j * b + c0 + lo;
+                    if (gr >= n || gc >= n) v = 0.0;
+                    S[hi][lo] = absmode ? fabs(v) : v;
+                }
+            }
+            for (int e = tid; e < 64 * nrhs; e += 256) {
+                const int c = e % 64, q = e / 64;
+                const int64_t g = (int64_t)j * b + c0 + c;
+                xs[c][q] = (g < n) ? X[q * ldx + g] : 0.0;
+            }
+            __syncthreads();
+            for (int c = part; c < 64; c += 4) {
+                const double l = S[rr][c];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
+            }
+        }
+    }
+    double(*red)[17] = reinterpret_cast<double(*)[17]>(&S[0][0]);
+    for (int p = 0; p < 4; ++p) {
+        __syncthreads();
+        if (part == p)
+            for (int q = 0; q < nrhs; ++q) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < 64 * nrhs; e += 256) {
+        const int r = e % 64, q = e / 64;
+        const int64_t g = (int64_t)i * b + r0 + r;
+        double out = 0.0;
+        if (g < n) out = absmode ? red[r][q] : B[q * ldb + g] - red[r][q];
+        R[q * ldr + g] = out;
+    }
+}
+
+// out[c] = max_r |V[c*ld + r]|, r < n (out must start at 0; max of non-negative doubles is
+// monotone in their bit patterns, so atomicMax on the bits is exact and order-free).
+__global__ void k_colmax_abs(const double *V, int64_t ld, int64_t n, double *out) {
+    const int c = blockIdx.y;
+    double m = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(V[c * ld + r]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long *>(out + c), (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n) {
+    const int c = blockIdx.y;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        X[c * ldx + r] += D[c * ldd + r];
+}
+
+__global__ void __launch_bounds__(1024) k_dot_self(const double *v, int64_t n, double *out) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) s = fma(v[i], v[i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// ---------------------------------------------------------------------------- launchers
+void launch_dgemm_update(const DJob *jobs, const DItem *items, int nitems, int ld, double *partials,
+                         const int *status, cudaStream_t s) {
+    if (nitems > 0) k_dgemm_update<<<nitems, 256, 0, s>>>(jobs, items, ld, partials, status);
+}
+void launch_dgemm_reduce(const DRed *reds, int nreds, int ld, const double *partials, const int *status,
+                         cudaStream_t s) {
+    if (nreds > 0) k_dgemm_reduce<<<nreds, 256, 0, s>>>(reds, ld, partials, status);
+}
+void launch_potrf_block(double *D, int ld, int col0, int *status, cudaStream_t s) {
+    k_potrf_block<<<1, 256, 0, s>>>(D, ld, col0, status);
+}
+void launch_trsm_rows(double *P, const double *L, int ld, int rows, const int *status, cudaStream_t s) {
+    if (rows > 0) k_trsm_rows<<<rows / 64, 256, 0, s>>>(P, L, ld, status);
+}
+void launch_trsm_strips(const TStrip *strips, int nstrips, int ld, int b, const int *status, cudaStream_t s) {
+    const size_t smem = (32 * 64 + 2 * 64 * 65) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_trsm_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    if (nstrips > 0) k_trsm_strips<<<nstrips, 256, smem, s>>>(strips, ld, b, status);
+}
+void launch_logdet(const double *W, int nt, int b, int64_t n, double *out, cudaStream_t s) {
+    (void)nt;
+    k_logdet<<<1, 1024, 0, s>>>(W, b, n, out);
+}
+void launch_fix_padding(double *W, int nt, int b, int64_t n, cudaStream_t s) {
+    if (n % b == 0) return;
+    k_fix_padding<<<dim3(64, nt), 256, 0, s>>>(W, nt, b, n);
+}
+void launch_zero_upper_diag(double *W, int nt, int b, int64_t n, cudaStream_t s) {
+    k_zero_upper_diag<<<dim3(64, (n % b) ? 2 * nt - 1 : nt), 256, 0, s>>>(W, nt, b, n);
+}
+void launch_fwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
+    k_fwd_diag<<<nrhs, 256, 0, s>>>(Ljj, b, R, ldr);
+}
+void launch_fwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
+    const int ntiles = nt - 1 - j;
+    if (ntiles > 0) k_fwd_update<<<ntiles * (b / 64), 256, 0, s>>>(W, b, j, R, ldr, nrhs);
+}
+void launch_bwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
+    k_bwd_diag<<<nrhs, 256, 0, s>>>(Ljj, b, R, ldr);
+}
+void launch_bwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
+    (void)nt;
+    if (j > 0) k_bwd_update<<<j * (b / 64), 256, 0, s>>>(W, b, j, R, ldr, nrhs);
+}
+void launch_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t ldx,
+                       const double *B, int64_t ldb, double *R, int64_t ldr, int nrhs, int absmode,
+                       cudaStream_t s) {
+    k_symv_resid<<<nt * (b / 64), 256, 0, s>>>(A, nt, b, n, X, ldx, B, ldb, R, ldr, nrhs, absmode);
+}
+void launch_colmax_abs(const double *V, int64_t ld, int64_t n, int ncols, double *out, cudaStream_t s) {
+    k_colmax_abs<<<dim3(64, ncols), 256, 0, s>>>(V, ld, n, out);
+}
+void launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n, int ncols, cudaStream_t s) {
+    k_axpy_cols<<<dim3(64, ncols), 256, 0, s>>>(X, ldx, D, ldd, n);
+}
+void launch_dot_self(const double *v, int64_t n, double *out, cudaStream_t s) {
+    k_dot_self<<<1, 1024, 0, s>>>(v, n, out);
+}
+
+}  // namespace tc

@@ -1,0 +1,708 @@
+// C ABI of tile_chol (include/tile_chol.h): handle, argument checks, the host-side
+// static scheduler of Algorithm 1 and the solve / log-likelihood drivers.
+//
+// Scheduling (Section III-B): the whole left-looking task order is fixed before the
+// first launch.  For every tile column k the scheduler emits, in this order,
+//   1. the SYRK/GEMM updates of column k (one grouped launch per precision; FP64 ones
+//      are split along K when the column has too few output blocks to fill 152 SMs),
+//   2. POTRF of the diagonal tile (blocked: 64-wide panels),
+//   3. the TRSMs of the tiles below it (one CTA per 64-row strip),
+// and uploads the tables once.  Stream order replaces the paper's Ready table: a launch
+// starts only after everything it reads has been written by earlier launches.
+#include "../../include/tile_chol.h"
+#include "tc_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace tc;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct tc_handle_s {
+    tc_config cfg{};
+    int device = 0;
+    cudaStream_t s = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // last factorization
+    int64_t n = 0;
+    int b = 0, nt = 0;
+    bool factored = false;
+    bool mixed = false;
+    double logdet = 0.0;
+    double normA_inf = -1.0;
+    std::vector<uint8_t> map;
+
+    DevBuf W;          // FP64 factor tiles (the working copy of A)
+    DevBuf Acopy;      // device copy of the caller's A when it was given in host memory
+    const double *A_dev = nullptr;
+    DevBuf status;     // int info word + padding
+    DevBuf scratch;    // small doubles: logdet, norms, maxima
+    DevBuf tables;     // schedule tables
+    DevBuf partials;   // split-K partial blocks
+    DevBuf vec;        // solve workspace
+    DevBuf sumsq;      // tile sums of squares
+    int64_t launches = 0;
+};
+
+namespace {
+
+int set_err(tc_handle h, int code, const std::string &msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(tc_handle h, cudaError_t e, const char *what, int line) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s failed: %s (%s) [tc_api.cu:%d]", what, cudaGetErrorName(e),
+             cudaGetErrorString(e), line);
+    return set_err(h, e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA, buf);
+}
+
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call, __LINE__); \
+    } while (0)
+
+#define CK_LAUNCH()                                                                   \
+    do {                                                                              \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, "kernel launch", __LINE__);    \
+        ++h->launches;                                                                \
+    } while (0)
+
+bool on_device(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ensure(tc_handle h, DevBuf &d, size_t bytes) {
+    if (d.bytes >= bytes && d.p) return TC_OK;
+    if (d.p) cudaFree(d.p);
+    d.p = nullptr;
+    d.bytes = 0;
+    cudaError_t e = cudaMalloc(&d.p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char buf[160];
+        snprintf(buf, sizeof buf, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return set_err(h, TC_ERR_OOM, buf);
+    }
+    d.bytes = bytes;
+    return TC_OK;
+}
+
+void release(DevBuf &d) {
+    if (d.p) cudaFree(d.p);
+    d.p = nullptr;
+    d.bytes = 0;
+}
+
+// Copy between any two pointers the runtime can classify (cudaMemcpyDefault).
+int copy_any(tc_handle h, void *dst, const void *src, size_t bytes) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->s));
+    return TC_OK;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int check_nb(tc_handle h, int64_t n, int b) {
+    if (!h) return TC_ERR_ARG;
+    if (n < 1) return set_err(h, TC_ERR_ARG, "n must be >= 1");
+    if (b < 64 || b > 4096 || b % 64) return set_err(h, TC_ERR_ARG, "tile size b must be a multiple of 64 in [64, 4096]");
+    const int64_t nt = (n + b - 1) / b;
+    if (nt > 65535) return set_err(h, TC_ERR_ARG, "too many tiles per column");
+    return TC_OK;
+}
+
+// ------------------------------------------------------------------ static schedule
+struct ColPlan {
+    int it0 = 0, nit = 0;        // FP64 update items
+    int red0 = 0, nred = 0;      // split-K reductions
+    int st0 = 0, nst = 0;        // TRSM strips
+    std::vector<std::pair<int, int>> potrf_items;  // (first item, count) per 64-panel (trailing update)
+};
+
+struct Plan {
+    std::vector<DJob> jobs;
+    std::vector<DItem> items;
+    std::vector<DRed> reds;
+    std::vector<TStrip> strips;
+    std::vector<ColPlan> cols;
+    int max_parts = 0;
+    double update_flops[4] = {0, 0, 0, 0};
+    double trsm_flops = 0, potrf_flops = 0;
+};
+
+constexpr int kTargetItems = 8 * 2 * NSM;   // >= 8 waves of 2 CTAs per SM before splitting K
+
+// Emit the items of one job: every 64 x 64 output block (lower ones only for a diagonal
+// SYRK), split along K into `splits` ranges when asked (the reduction then subtracts the
+// partial blocks from C in a fixed order, so results do not depend on timing).
+void emit_job_items(Plan &P, int job, int ld, int splits, int &part_next) {
+    const DJob J = P.jobs[job];
+    const int mb = J.M / 64, nb = J.N / 64;
+    for (int bj = 0; bj < nb; ++bj)
+        for (int bi = J.lower ? bj : 0; bi < mb; ++bi) {
+            if (splits <= 1) {
+                P.items.push_back({job, (uint16_t)bi, (uint16_t)bj, 0, J.K, -1});
+                continue;
+            }
+            const int part0 = part_next;
+            const int chunk = ((J.K + splits - 1) / splits + 15) / 16 * 16;
+            int np = 0;
+            for (int k0 = 0; k0 < J.K; k0 += chunk, ++np)
+                P.items.push_back({job, (uint16_t)bi, (uint16_t)bj, k0, std::min(J.K, k0 + chunk), part_next++});
+            P.reds.push_back({J.C + (int64_t)bj * 64 * ld + bi * 64, part0, np});
+        }
+}
+
+Plan build_plan(double *W, int nt, int b, const std::vector<uint8_t> &map, bool mixed) {
+    Plan P;
+    P.cols.resize(nt);
+    const int64_t bb = (int64_t)b * b;
+    auto T = [&](int i, int j) { return W + tidx(i, j) * bb; };
+    for (int k = 0; k < nt; ++k) {
+        ColPlan &C = P.cols[k];
+        // 1. updates of column k (FP64 output tiles here; low-precision ones elsewhere)
+        C.it0 = (int)P.items.size();
+        C.red0 = (int)P.reds.size();
+        if (k > 0) {
+            const int K = k * b;
+            std::vector<int> jobs_here;
+            int base = 0;
+            for (int m = k; m < nt; ++m) {
+                const bool fp64 = (m == k) || !mixed || map[(size_t)m * nt + k] == TC_FP64;
+                if (!fp64) continue;
+                jobs_here.push_back((int)P.jobs.size());
+                P.jobs.push_back({T(m, k), T(m, 0), T(k, 0), K, b, b, m == k ? 1 : 0});
+                base += (m == k) ? (b / 64) * (b / 64 + 1) / 2 : (b / 64) * (b / 64);
+                P.update_flops[TC_FP64] += (m == k ? 1.0 : 2.0) * (double)b * b * K;
+            }
+            int splits = 1;
+            if (base > 0 && base < kTargetItems) splits = std::min((kTargetItems + base - 1) / base, std::max(1, K / 256));
+            int part_next = 0;
+            for (int jj : jobs_here) emit_job_items(P, jj, b, splits, part_next);
+            P.max_parts = std::max(P.max_parts, part_next);
+        }
+        C.nit = (int)P.items.size() - C.it0;
+        C.nred = (int)P.reds.size() - C.red0;
+        // 2. POTRF trailing updates of the diagonal tile, panel by panel
+        double *D = T(k, k);
+        for (int jb = 0; jb + 1 < b / 64; ++jb) {
+            const int M = b - (jb + 1) * 64;
+            const int job = (int)P.jobs.size();
+            const double *Pn = D + (int64_t)jb * 64 * b + (jb + 1) * 64;
+            P.jobs.push_back({D + (int64_t)(jb + 1) * 64 * b + (jb + 1) * 64, Pn, Pn, 64, M, M, 1});
+            const int i0 = (int)P.items.size();
+            int dummy = 0;
+            emit_job_items(P, job, b, 1, dummy);
+            C.potrf_items.push_back({i0, (int)P.items.size() - i0});
+        }
+        P.potrf_flops += (double)b * b * b / 3.0;
+        // 3. TRSM strips of the tiles below the diagonal
+        C.st0 = (int)P.strips.size();
+        for (int m = k + 1; m < nt; ++m)
+            for (int r0 = 0; r0 < b; r0 += 64) P.strips.push_back({T(m, k), D, r0});
+        C.nst = (int)P.strips.size() - C.st0;
+        P.trsm_flops += (double)(nt - 1 - k) * b * b * b;
+    }
+    return P;
+}
+
+size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
+
+int run_fp64_factor(tc_handle h, const Plan &P) {
+    const int nt = h->nt, b = h->b;
+    // upload tables
+    const size_t sj = P.jobs.size() * sizeof(DJob), si = P.items.size() * sizeof(DItem);
+    const size_t sr = P.reds.size() * sizeof(DRed), ss = P.strips.size() * sizeof(TStrip);
+    const size_t oj = 0, oi = align_up(oj + sj), orr = align_up(oi + si), os = align_up(orr + sr);
+    const size_t total = align_up(os + ss);
+    int rc = ensure(h, h->tables, total);
+    if (rc) return rc;
+    std::vector<char> host(total);
+    if (sj) memcpy(host.data() + oj, P.jobs.data(), sj);
+    if (si) memcpy(host.data() + oi, P.items.data(), si);
+    if (sr) memcpy(host.data() + orr, P.reds.data(), sr);
+    if (ss) memcpy(host.data() + os, P.strips.data(), ss);
+    CK(cudaMemcpyAsync(h->tables.p, host.data(), total, cudaMemcpyHostToDevice, h->s));
+    char *base = static_cast<char *>(h->tables.p);
+    const DJob *djobs = reinterpret_cast<const DJob *>(base + oj);
+    const DItem *ditems = reinterpret_cast<const DItem *>(base + oi);
+    const DRed *dreds = reinterpret_cast<const DRed *>(base + orr);
+    const TStrip *dstrips = reinterpret_cast<const TStrip *>(base + os);
+    rc = ensure(h, h->partials, (size_t)std::max(1, P.max_parts) * 4096 * sizeof(double));
+    if (rc) return rc;
+    double *parts = static_cast<double *>(h->partials.p);
+    int *status = static_cast<int *>(h->status.p);
+    double *W = static_cast<double *>(h->W.p);
+    const int64_t bb = (int64_t)b * b;
+
+    for (int k = 0; k < nt; ++k) {
+        const ColPlan &C = P.cols[k];
+        if (C.nit) {
+            launch_dgemm_update(djobs, ditems + C.it0, C.nit, b, parts, status, h->s);
+            CK_LAUNCH();
+        }
+        if (C.nred) {
+            launch_dgemm_reduce(dreds + C.red0, C.nred, b, parts, status, h->s);
+            CK_LAUNCH();
+        }
+        double *D = W + tidx(k, k) * bb;
+        for (int jb = 0; jb < b / 64; ++jb) {
+            launch_potrf_block(D + (int64_t)jb * 64 * b + jb * 64, b, k * b + jb * 64, status, h->s);
+            CK_LAUNCH();
+            if (jb + 1 < b / 64) {
+                const int rows = b - (jb + 1) * 64;
+                launch_trsm_rows(D + (int64_t)jb * 64 * b + (jb + 1) * 64, D + (int64_t)jb * 64 * b + jb * 64, b,
+                                 rows, status, h->s);
+                CK_LAUNCH();
+                const auto &pi = C.potrf_items[jb];
+                launch_dgemm_update(djobs, ditems + pi.first, pi.second, b, parts, status, h->s);
+                CK_LAUNCH();
+            }
+        }
+        if (C.nst) {
+            launch_trsm_strips(dstrips + C.st0, C.nst, b, b, status, h->s);
+            CK_LAUNCH();
+        }
+    }
+    return TC_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void tc_config_default(tc_config *cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->device = 0;
+    cfg->stream = nullptr;
+    cfg->ooc = 0;
+    cfg->device_cap_bytes = 0;
+    cfg->prefetch_depth = 2;
+    cfg->lookahead = 1;
+}
+
+int tc_create(tc_handle *out, const tc_config *cfg) {
+    if (!out) return TC_ERR_ARG;
+    *out = nullptr;
+    tc_handle h = new tc_handle_s();
+    if (cfg) h->cfg = *cfg;
+    else tc_config_default(&h->cfg);
+    h->device = h->cfg.device;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || h->device < 0 || h->device >= ndev) {
+        cudaGetLastError();
+        delete h;
+        return TC_ERR_CUDA;
+    }
+    if (cudaSetDevice(h->device) != cudaSuccess) {
+        delete h;
+        return TC_ERR_CUDA;
+    }
+    if (h->cfg.stream) {
+        h->s = static_cast<cudaStream_t>(h->cfg.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return TC_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    if (ensure(h, h->status, 256) || ensure(h, h->scratch, 4096 * sizeof(double))) {
+        tc_destroy(h);
+        return TC_ERR_OOM;
+    }
+    *out = h;
+    return TC_OK;
+}
+
+void tc_destroy(tc_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->s) cudaStreamSynchronize(h->s);
+    for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq})
+        release(*d);
+    if (h->own_stream && h->s) cudaStreamDestroy(h->s);
+    delete h;
+}
+
+const char *tc_last_error(tc_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+int tc_matern_tiles(tc_handle h, int64_t n, int b, const double *points, double sigma2, double range_a,
+                    double nu, double nugget, double *A_tiles) {
+    int rc = check_nb(h, n, b);
+    if (rc) return rc;
+    if (!points || !A_tiles) return set_err(h, TC_ERR_ARG, "points and A_tiles must not be NULL");
+    if (!(range_a > 0) || !(sigma2 > 0)) return set_err(h, TC_ERR_ARG, "range and variance must be positive");
+    int nu2 = 0;
+    if (nu == 0.5) nu2 = 1;
+    else if (nu == 1.5) nu2 = 3;
+    else if (nu == 2.5) nu2 = 5;
+    else return set_err(h, TC_ERR_ARG, "smoothness must be 0.5, 1.5 or 2.5");
+    CK(cudaSetDevice(h->device));
+    const int nt = (int)((n + b - 1) / b);
+    const double *dpts = points;
+    DevBuf tmp_pts, tmp_out;
+    if (!on_device(points)) {
+        rc = ensure(h, tmp_pts, (size_t)n * 2 * sizeof(double));
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(tmp_pts.p, points, (size_t)n * 2 * sizeof(double), cudaMemcpyHostToDevice, h->s));
+        dpts = static_cast<const double *>(tmp_pts.p);
+    }
+    const size_t bytes = (size_t)nt * (nt + 1) / 2 * b * b * sizeof(double);
+    double *dout = A_tiles;
+    const bool out_dev = on_device(A_tiles);
+    if (!out_dev) {
+        rc = ensure(h, tmp_out, bytes);
+        if (rc) { release(tmp_pts); return rc; }
+        dout = static_cast<double *>(tmp_out.p);
+    }
+    launch_matern(dout, n, b, nt, dpts, sigma2, range_a, nu2, nugget, h->s);
+    CK_LAUNCH();
+    if (!out_dev) CK(cudaMemcpyAsync(A_tiles, dout, bytes, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    release(tmp_pts);
+    release(tmp_out);
+    return TC_OK;
+}
+
+int tile_chol_precision_map(tc_handle h, int64_t n, int b, const double *A_tiles, double eps_high, int band,
+                            int prec_set, uint8_t *map_out, double *norms_out) {
+    int rc = check_nb(h, n, b);
+    if (rc) return rc;
+    if (!A_tiles || !map_out) return set_err(h, TC_ERR_ARG, "A_tiles and map_out must not be NULL");
+    if (!(eps_high > 0) || band < 0 || prec_set < 1 || prec_set > 4)
+        return set_err(h, TC_ERR_ARG, "eps_high > 0, band >= 0 and prec_set in 1..4 are required");
+    CK(cudaSetDevice(h->device));
+    const int nt = (int)((n + b - 1) / b);
+    const int64_t T = (int64_t)nt * (nt + 1) / 2;
+    const double *dA = A_tiles;
+    DevBuf tmp;
+    if (!on_device(A_tiles)) {
+        const size_t bytes = (size_t)T * b * b * sizeof(double);
+        rc = ensure(h, tmp, bytes);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(tmp.p, A_tiles, bytes, cudaMemcpyHostToDevice, h->s));
+        dA = static_cast<const double *>(tmp.p);
+    }
+    rc = ensure(h, h->sumsq, (size_t)T * sizeof(double));
+    if (rc) { release(tmp); return rc; }
+    launch_tile_sumsq(dA, nt, b, n, static_cast<double *>(h->sumsq.p), h->s);
+    CK_LAUNCH();
+    std::vector<double> ss(T);
+    CK(cudaMemcpyAsync(ss.data(), h->sumsq.p, T * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    release(tmp);
+    // ||A||_F over the full symmetric matrix: off-diagonal tiles count twice
+    double tot = 0.0;
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j <= i; ++j) tot += (i == j ? 1.0 : 2.0) * ss[tidx(i, j)];
+    const double normA = std::sqrt(tot);
+    const double u[4] = {std::ldexp(1.0, -53), std::ldexp(1.0, -24), std::ldexp(1.0, -11), std::ldexp(1.0, -4)};
+    std::vector<uint8_t> pm((size_t)nt * nt, 0);
+    std::vector<double> norms((size_t)nt * nt + 1, 0.0);
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j <= i; ++j) {
+            const double nij = std::sqrt(ss[tidx(i, j)]);
+            norms[(size_t)i * nt + j] = nij;
+            if (i == j || i - j <= band) continue;
+            const double ratio = (double)nt * nij / normA;
+            // lowest allowed precision first: FP8, FP16, FP32
+            for (int p = TC_FP8; p >= TC_FP32; --p) {
+                if (p > prec_set - 1) continue;
+                if (ratio < eps_high / u[p]) {
+                    pm[(size_t)i * nt + j] = (uint8_t)p;
+                    break;
+                }
+            }
+        }
+    norms[(size_t)nt * nt] = normA;
+    if (on_device(map_out)) {
+        CK(cudaMemcpy(map_out, pm.data(), pm.size(), cudaMemcpyHostToDevice));
+    } else {
+        memcpy(map_out, pm.data(), pm.size());
+    }
+    if (norms_out) {
+        if (on_device(norms_out)) CK(cudaMemcpy(norms_out, norms.data(), norms.size() * sizeof(double), cudaMemcpyHostToDevice));
+        else memcpy(norms_out, norms.data(), norms.size() * sizeof(double));
+    }
+    return TC_OK;
+}
+
+int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const uint8_t *map, tc_stats *stats) {
+    int rc = check_nb(h, n, b);
+    if (rc) return rc;
+    if (!A_tiles) return set_err(h, TC_ERR_ARG, "A_tiles must not be NULL");
+    CK(cudaSetDevice(h->device));
+    const double t0 = now_ms();
+    const int64_t launches0 = h->launches;
+    h->factored = false;
+    h->normA_inf = -1.0;
+    const int nt = (int)((n + b - 1) / b);
+    const int64_t T = (int64_t)nt * (nt + 1) / 2;
+    const size_t bytes = (size_t)T * b * b * sizeof(double);
+    h->n = n;
+    h->b = b;
+    h->nt = nt;
+    // precision map (host copy)
+    h->map.assign((size_t)nt * nt, TC_FP64);
+    if (map) {
+        if (on_device(map)) CK(cudaMemcpy(h->map.data(), map, h->map.size(), cudaMemcpyDeviceToHost));
+        else memcpy(h->map.data(), map, h->map.size());
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j < nt; ++j) {
+                uint8_t &v = h->map[(size_t)i * nt + j];
+                if (j >= i) v = TC_FP64;
+                if (v > TC_FP8) return set_err(h, TC_ERR_ARG, "precision map entries must be 0..3");
+            }
+    }
+    h->mixed = false;
+    for (uint8_t v : h->map) h->mixed |= (v != TC_FP64);
+    if (h->mixed) return set_err(h, TC_ERR_UNSUPPORTED, "mixed-precision maps are not available in this build");
+    if (h->cfg.ooc == 1) return set_err(h, TC_ERR_UNSUPPORTED, "out-of-core mode is not available in this build");
+
+    rc = ensure(h, h->W, bytes);
+    if (rc) return rc;
+    // the caller's A stays readable for refinement: reference it on the device or copy it
+    if (on_device(A_tiles)) {
+        h->A_dev = A_tiles;
+    } else {
+        rc = ensure(h, h->Acopy, bytes);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(h->Acopy.p, A_tiles, bytes, cudaMemcpyHostToDevice, h->s));
+        h->A_dev = static_cast<const double *>(h->Acopy.p);
+    }
+    double *W = static_cast<double *>(h->W.p);
+    CK(cudaMemcpyAsync(W, h->A_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
+    launch_fix_padding(W, nt, b, n, h->s);
+    CK_LAUNCH();
+    CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->s));
+
+    Plan P = build_plan(W, nt, b, h->map, h->mixed);
+    rc = run_fp64_factor(h, P);
+    if (rc) return rc;
+    double *sc = static_cast<double *>(h->scratch.p);
+    launch_logdet(W, nt, b, n, sc, h->s);
+    CK_LAUNCH();
+    int info = 0;
+    CK(cudaMemcpyAsync(&info, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    double ld = 0.0;
+    CK(cudaMemcpyAsync(&ld, sc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    h->logdet = ld;
+    h->factored = (info == 0);
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->t_ms = now_ms() - t0;
+        stats->flops = (double)n * n * n / 3.0;
+        for (int p = 0; p < 4; ++p) stats->update_flops[p] = P.update_flops[p];
+        stats->trsm_flops = P.trsm_flops;
+        stats->potrf_flops = P.potrf_flops;
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j <= i; ++j) stats->tiles[h->map[(size_t)i * nt + j]]++;
+        stats->kernel_launches = h->launches - launches0;
+        stats->info = info;
+    }
+    if (info) set_err(h, info, "matrix is not positive definite (see the returned column)");
+    return info;
+}
+
+int tile_chol_logdet(tc_handle h, double *logdet_out) {
+    if (!h || !logdet_out) return TC_ERR_ARG;
+    if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");
+    *logdet_out = h->logdet;
+    return TC_OK;
+}
+
+// Forward (and optionally back) substitution on the padded column-major buffer R
+// (leading dimension ldr = nt*b), nrhs <= 16 per pass.
+static int subst(tc_handle h, double *R, int64_t ldr, int nrhs, bool back) {
+    const int nt = h->nt, b = h->b;
+    const double *W = static_cast<const double *>(h->W.p);
+    const int64_t bb = (int64_t)b * b;
+    for (int c0 = 0; c0 < nrhs; c0 += 16) {
+        const int nc = std::min(16, nrhs - c0);
+        double *Rc = R + (int64_t)c0 * ldr;
+        for (int j = 0; j < nt; ++j) {
+            launch_fwd_diag(W + tidx(j, j) * bb, b, Rc + (int64_t)j * b, ldr, nc, h->s);
+            CK_LAUNCH();
+            launch_fwd_update(W, nt, b, j, Rc, ldr, nc, h->s);
+            if (j + 1 < nt) CK_LAUNCH();
+        }
+        if (!back) continue;
+        for (int j = nt - 1; j >= 0; --j) {
+            launch_bwd_diag(W + tidx(j, j) * bb, b, Rc + (int64_t)j * b, ldr, nc, h->s);
+            CK_LAUNCH();
+            launch_bwd_update(W, nt, b, j, Rc, ldr, nc, h->s);
+            if (j > 0) CK_LAUNCH();
+        }
+    }
+    return TC_OK;
+}
+
+int tile_chol_solve(tc_handle h, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int max_refine,
+                    double target_berr, tc_stats *stats) {
+    if (!h) return TC_ERR_ARG;
+    if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");
+    if (nrhs < 1 || !B || !X || ldb < h->n || ldx < h->n || max_refine < 0)
+        return set_err(h, TC_ERR_ARG, "bad solve arguments");
+    CK(cudaSetDevice(h->device));
+    const double t0 = now_ms();
+    const int64_t launches0 = h->launches;
+    const int nt = h->nt, b = h->b;
+    const int64_t n = h->n, ldr = (int64_t)nt * b;
+    // workspace: Bd (padded copy of B), Xd, Rd  (each ldr x nrhs)
+    const size_t colbytes = (size_t)ldr * nrhs * sizeof(double);
+    int rc = ensure(h, h->vec, 3 * colbytes);
+    if (rc) return rc;
+    double *Bd = static_cast<double *>(h->vec.p);
+    double *Xd = Bd + (size_t)ldr * nrhs;
+    double *Rd = Xd + (size_t)ldr * nrhs;
+    CK(cudaMemsetAsync(Bd, 0, colbytes, h->s));
+    CK(cudaMemcpy2DAsync(Bd, ldr * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), nrhs,
+                         cudaMemcpyDefault, h->s));
+    CK(cudaMemcpyAsync(Xd, Bd, colbytes, cudaMemcpyDeviceToDevice, h->s));
+    rc = subst(h, Xd, ldr, nrhs, true);
+    if (rc) return rc;
+    double *sc = static_cast<double *>(h->scratch.p);
+    // ||A||_inf (once per factor): max row sum of |A| = max of |A| * ones
+    if (h->normA_inf < 0 && max_refine > 0) {
+        CK(cudaMemsetAsync(Rd, 0, (size_t)ldr * sizeof(double), h->s));
+        // ones vector in Rd[ldr .. 2 ldr) is not needed: use a dedicated column of Rd
+        std::vector<double> ones((size_t)ldr, 0.0);
+        for (int64_t i = 0; i < n; ++i) ones[i] = 1.0;
+        CK(cudaMemcpyAsync(Rd, ones.data(), (size_t)ldr * sizeof(double), cudaMemcpyHostToDevice, h->s));
+        double *rowsum = Rd + (nrhs > 1 ? ldr : 0);
+        DevBuf tmp;
+        if (nrhs == 1) {
+            rc = ensure(h, tmp, (size_t)ldr * sizeof(double));
+            if (rc) return rc;
+            rowsum = static_cast<double *>(tmp.p);
+        }
+        launch_symv_resid(h->A_dev, nt, b, n, Rd, ldr, nullptr, 0, rowsum, ldr, 1, 1, h->s);
+        CK_LAUNCH();
+        CK(cudaMemsetAsync(sc, 0, sizeof(double), h->s));
+        launch_colmax_abs(rowsum, ldr, n, 1, sc, h->s);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(&h->normA_inf, sc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        release(tmp);
+    }
+    int it = 0;
+    double berr = -1.0;
+    for (;; ++it) {
+        if (max_refine == 0) break;
+        // R = B - A X and the normwise backward error per column
+        for (int c0 = 0; c0 < nrhs; c0 += 16) {
+            const int nc = std::min(16, nrhs - c0);
+            launch_symv_resid(h->A_dev, nt, b, n, Xd + (int64_t)c0 * ldr, ldr, Bd + (int64_t)c0 * ldr, ldr,
+                              Rd + (int64_t)c0 * ldr, ldr, nc, 0, h->s);
+            CK_LAUNCH();
+        }
+        CK(cudaMemsetAsync(sc, 0, 3 * nrhs * sizeof(double), h->s));
+        launch_colmax_abs(Rd, ldr, n, nrhs, sc, h->s);
+        CK_LAUNCH();
+        launch_colmax_abs(Xd, ldr, n, nrhs, sc + nrhs, h->s);
+        CK_LAUNCH();
+        launch_colmax_abs(Bd, ldr, n, nrhs, sc + 2 * nrhs, h->s);
+        CK_LAUNCH();
+        std::vector<double> mx(3 * nrhs);
+        CK(cudaMemcpyAsync(mx.data(), sc, 3 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        berr = 0.0;
+        for (int c = 0; c < nrhs; ++c) {
+            const double den = h->normA_inf * mx[nrhs + c] + mx[2 * nrhs + c];
+            berr = std::max(berr, den > 0 ? mx[c] / den : 0.0);
+        }
+        if (berr <= target_berr || it >= max_refine) break;
+        rc = subst(h, Rd, ldr, nrhs, true);
+        if (rc) return rc;
+        launch_axpy_cols(Xd, ldr, Rd, ldr, n, nrhs, h->s);
+        CK_LAUNCH();
+    }
+    CK(cudaMemcpy2DAsync(X, ldx * sizeof(double), Xd, ldr * sizeof(double), n * sizeof(double), nrhs,
+                         cudaMemcpyDefault, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->t_ms = now_ms() - t0;
+        stats->refine_iters = it;
+        stats->berr = berr;
+        stats->kernel_launches = h->launches - launches0;
+    }
+    return TC_OK;
+}
+
+int tile_chol_loglik(tc_handle h, const double *y, double *loglik_out) {
+    if (!h || !loglik_out) return TC_ERR_ARG;
+    if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");
+    CK(cudaSetDevice(h->device));
+    const double two_pi = 6.283185307179586476925286766559;
+    double quad = 0.0;
+    if (y) {
+        const int64_t ldr = (int64_t)h->nt * h->b;
+        int rc = ensure(h, h->vec, (size_t)ldr * sizeof(double) * 3);
+        if (rc) return rc;
+        double *z = static_cast<double *>(h->vec.p);
+        CK(cudaMemsetAsync(z, 0, (size_t)ldr * sizeof(double), h->s));
+        CK(cudaMemcpyAsync(z, y, (size_t)h->n * sizeof(double), cudaMemcpyDefault, h->s));
+        rc = subst(h, z, ldr, 1, false);
+        if (rc) return rc;
+        double *sc = static_cast<double *>(h->scratch.p);
+        launch_dot_self(z, h->n, sc, h->s);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(&quad, sc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+    }
+    *loglik_out = -0.5 * (double)h->n * std::log(two_pi) - 0.5 * h->logdet - 0.5 * quad;
+    return TC_OK;
+}
+
+int tile_chol_get_factor(tc_handle h, double *L_tiles) {
+    if (!h || !L_tiles) return TC_ERR_ARG;
+    if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");
+    CK(cudaSetDevice(h->device));
+    const int nt = h->nt, b = h->b;
+    const size_t bytes = (size_t)nt * (nt + 1) / 2 * b * b * sizeof(double);
+    double *dst = L_tiles;
+    DevBuf tmp;
+    const bool dev = on_device(L_tiles);
+    if (!dev) {
+        int rc = ensure(h, tmp, bytes);
+        if (rc) return rc;
+        dst = static_cast<double *>(tmp.p);
+    }
+    CK(cudaMemcpyAsync(dst, h->W.p, bytes, cudaMemcpyDeviceToDevice, h->s));
+    launch_zero_upper_diag(dst, nt, b, h->n, h->s);
+    CK_LAUNCH();
+    if (!dev) CK(cudaMemcpyAsync(L_tiles, dst, bytes, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    release(tmp);
+    return TC_OK;
+}
+
+}  // extern "C"

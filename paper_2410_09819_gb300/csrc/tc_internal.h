@@ -1,0 +1,85 @@
+// Internal declarations shared by the tile_chol translation units (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tc {
+
+constexpr int BLK = 64;         // FP64 kernels work on 64 x 64 blocks
+constexpr int NSM = 152;        // GB300 streaming multiprocessors
+
+inline int64_t tidx(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
+
+// C -= X Y^T on a (M x N) block grid; X is M x K and Y is N x K, all column-major with
+// leading dimension ld (the tile size): the layout of a tile row of the factor.
+struct DJob {
+    double *C;
+    const double *X;
+    const double *Y;
+    int K, M, N, lower;
+};
+
+// One CTA of the FP64 update: 64 x 64 output block (bi, bj) of job `job`, contraction
+// range [k0, k1).  part < 0: subtract straight into C, else write the block to
+// partial buffer `part` (split-K; a reduce launch subtracts the partials in order).
+struct DItem {
+    int job;
+    uint16_t bi, bj;
+    int k0, k1;
+    int part;
+};
+
+// Reduce: C_block -= sum_{p < nparts} partial[part0 + p]; C_block is the 64 x 64 block
+// at C (leading dimension ld).
+struct DRed {
+    double *C;
+    int part0, nparts;
+};
+
+// A 64-row strip of one TRSM tile: solve X L^T = C in place for rows [r0, r0 + 64).
+struct TStrip {
+    double *C;          // tile (m, k) of the factor
+    const double *L;    // L_kk
+    int r0;
+};
+
+// Low-precision update job (tensor cores): C -= sum_n 2^(ex[n] + ey[n]) X_n Y_n^T over
+// the source tiles n of one output tile, operands taken from per-precision pools.
+struct QJob {
+    double *C;              // FP64 output tile (column-major, ld = b)
+    int xs0, ys0;           // index into the slot list (K-ordered source tiles)
+    int nsrc;               // number of source tiles
+    int lower;              // unused for low precision (never diagonal)
+};
+
+// ------------------------------------------------------------------ launchers (k_fp64.cu)
+void launch_dgemm_update(const DJob *jobs, const DItem *items, int nitems, int ld,
+                         double *partials, const int *status, cudaStream_t s);
+void launch_dgemm_reduce(const DRed *reds, int nreds, int ld, const double *partials,
+                         const int *status, cudaStream_t s);
+void launch_potrf_block(double *D, int ld, int col0, int *status, cudaStream_t s);
+void launch_trsm_rows(double *P, const double *L, int ld, int rows, const int *status, cudaStream_t s);
+void launch_trsm_strips(const TStrip *strips, int nstrips, int ld, int b, const int *status, cudaStream_t s);
+void launch_logdet(const double *W, int nt, int b, int64_t n, double *out, cudaStream_t s);
+void launch_fix_padding(double *W, int nt, int b, int64_t n, cudaStream_t s);
+void launch_zero_upper_diag(double *W, int nt, int b, int64_t n, cudaStream_t s);
+
+// solves (column-major right-hand sides, leading dimension ldr, nrhs <= 16 per launch)
+void launch_fwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs, cudaStream_t s);
+void launch_fwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s);
+void launch_bwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs, cudaStream_t s);
+void launch_bwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s);
+void launch_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t ldx,
+                       const double *B, int64_t ldb, double *R, int64_t ldr, int nrhs, int absmode,
+                       cudaStream_t s);
+void launch_colmax_abs(const double *V, int64_t ld, int64_t n, int ncols, double *out, cudaStream_t s);
+void launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
+void launch_dot_self(const double *v, int64_t n, double *out, cudaStream_t s);
+
+// ------------------------------------------------------------------ launchers (k_gen.cu)
+void launch_matern(double *A, int64_t n, int b, int nt, const double *pts, double sigma2,
+                   double a, int nu2, double nugget, cudaStream_t s);
+void launch_tile_sumsq(const double *A, int nt, int b, int64_t n, double *out, cudaStream_t s);
+
+}  // namespace tc
