@@ -88,6 +88,12 @@ typedef struct {
     double berr;                /* solve: final normwise backward error (max over RHS) */
     int info;                   /* same as the return value for factor calls */
     int ooc;                    /* 1 if the call ran out-of-core */
+    /* device time (CUDA events on the launching stream) spent in the SYRK/GEMM update
+       launches of each output precision, in the POTRF and TRSM launches, and in the
+       down-cast / operand-copy launches of the factorization */
+    double t_update_ms[4];
+    double t_potrf_ms, t_trsm_ms, t_convert_ms;
+    int64_t update_launches[4];
 } tc_stats;
 
 /* Defaults: device 0, own stream, ooc auto, cap 0 (auto), prefetch 2, lookahead 1. */

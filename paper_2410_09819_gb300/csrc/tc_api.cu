@@ -53,7 +53,16 @@ struct tc_handle_s {
     DevBuf vec;        // solve workspace
     DevBuf sumsq;      // tile sums of squares
     int64_t launches = 0;
+    int64_t upd_launches[4] = {0, 0, 0, 0};
+
+    // CUDA-event spans of the last factorization, by category (see Cat)
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    struct Span { int cat; cudaEvent_t a, b; };
+    std::vector<Span> spans;
 };
+
+enum Cat { CAT_UPD64 = 0, CAT_UPD32, CAT_UPD16, CAT_UPD8, CAT_POTRF, CAT_TRSM, CAT_CONVERT, CAT_N };
 
 namespace {
 
@@ -118,6 +127,43 @@ void release(DevBuf &d) {
 int copy_any(tc_handle h, void *dst, const void *src, size_t bytes) {
     CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->s));
     return TC_OK;
+}
+
+cudaEvent_t next_event(tc_handle h) {
+    if (h->events_used == h->events.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->events.push_back(e);
+    }
+    return h->events[h->events_used++];
+}
+
+// Open a timed span on the handle's stream; close it with span_end.
+int span_begin(tc_handle h, int cat) {
+    cudaEvent_t a = next_event(h), b = next_event(h);
+    if (!a || !b) return -1;
+    cudaEventRecord(a, h->s);
+    h->spans.push_back({cat, a, b});
+    return (int)h->spans.size() - 1;
+}
+
+void span_end(tc_handle h, int id) {
+    if (id >= 0) cudaEventRecord(h->spans[id].b, h->s);
+}
+
+// Sum the spans per category (the stream must be synchronised).
+void span_totals(tc_handle h, double *ms) {
+    for (int c = 0; c < CAT_N; ++c) ms[c] = 0.0;
+    for (auto &sp : h->spans) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess) ms[sp.cat] += t;
+        else cudaGetLastError();
+    }
+}
+
+void spans_reset(tc_handle h) {
+    h->spans.clear();
+    h->events_used = 0;
 }
 
 double now_ms() {
@@ -260,14 +306,18 @@ int run_fp64_factor(tc_handle h, const Plan &P) {
     for (int k = 0; k < nt; ++k) {
         const ColPlan &C = P.cols[k];
         if (C.nit) {
+            const int sp = span_begin(h, CAT_UPD64);
             launch_dgemm_update(djobs, ditems + C.it0, C.nit, b, parts, status, h->s);
+            span_end(h, sp);
             CK_LAUNCH();
+            ++h->upd_launches[TC_FP64];
         }
         if (C.nred) {
             launch_dgemm_reduce(dreds + C.red0, C.nred, b, parts, status, h->s);
             CK_LAUNCH();
         }
         double *D = W + tidx(k, k) * bb;
+        const int sp_potrf = span_begin(h, CAT_POTRF);
         for (int jb = 0; jb < b / 64; ++jb) {
             launch_potrf_block(D + (int64_t)jb * 64 * b + jb * 64, b, k * b + jb * 64, status, h->s);
             CK_LAUNCH();
@@ -281,8 +331,11 @@ int run_fp64_factor(tc_handle h, const Plan &P) {
                 CK_LAUNCH();
             }
         }
+        span_end(h, sp_potrf);
         if (C.nst) {
+            const int sp = span_begin(h, CAT_TRSM);
             launch_trsm_strips(dstrips + C.st0, C.nst, b, b, status, h->s);
+            span_end(h, sp);
             CK_LAUNCH();
         }
     }
@@ -346,6 +399,7 @@ void tc_destroy(tc_handle h) {
     if (h->s) cudaStreamSynchronize(h->s);
     for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq})
         release(*d);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     if (h->own_stream && h->s) cudaStreamDestroy(h->s);
     delete h;
 }
@@ -502,6 +556,8 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
     CK_LAUNCH();
     CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->s));
 
+    spans_reset(h);
+    for (int p = 0; p < 4; ++p) h->upd_launches[p] = 0;
     Plan P = build_plan(W, nt, b, h->map, h->mixed);
     rc = run_fp64_factor(h, P);
     if (rc) return rc;
@@ -526,6 +582,15 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
             for (int j = 0; j <= i; ++j) stats->tiles[h->map[(size_t)i * nt + j]]++;
         stats->kernel_launches = h->launches - launches0;
         stats->info = info;
+        double ms[CAT_N];
+        span_totals(h, ms);
+        for (int p = 0; p < 4; ++p) {
+            stats->t_update_ms[p] = ms[CAT_UPD64 + p];
+            stats->update_launches[p] = h->upd_launches[p];
+        }
+        stats->t_potrf_ms = ms[CAT_POTRF];
+        stats->t_trsm_ms = ms[CAT_TRSM];
+        stats->t_convert_ms = ms[CAT_CONVERT];
     }
     if (info) set_err(h, info, "matrix is not positive definite (see the returned column)");
     return info;

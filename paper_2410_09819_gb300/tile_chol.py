@@ -45,7 +45,10 @@ class tc_stats(ctypes.Structure):
                 ("tiles", ctypes.c_int64 * 4), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("cache_hits", ctypes.c_int64), ("cache_misses", ctypes.c_int64), ("evictions", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("refine_iters", ctypes.c_int), ("berr", ctypes.c_double),
-                ("info", ctypes.c_int), ("ooc", ctypes.c_int)]
+                ("info", ctypes.c_int), ("ooc", ctypes.c_int),
+                ("t_update_ms", ctypes.c_double * 4), ("t_potrf_ms", ctypes.c_double),
+                ("t_trsm_ms", ctypes.c_double), ("t_convert_ms", ctypes.c_double),
+                ("update_launches", ctypes.c_int64 * 4)]
 
     def as_dict(self) -> dict:
         out = {}
