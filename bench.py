@@ -33,7 +33,8 @@ from paper_2410_09819_gb300 import inputs  # noqa: E402
 
 METRIC = "Cholesky TFLOP/s (n^3/3) MxP vs FP64 on 1 GB300 at stated error; OOC link GB/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_OVER_BF16_NOMINAL = 1.25 / 2250.0     # nominal dense FP64 / BF16 rates of GB300
+FP64_FLOPS_PER_CLK_SM = 4.0   # GB300: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / 152 SMs / 2.07 GHz)
+NSM = 152
 CPU_SAMPLE_N = 8192
 
 
@@ -204,15 +205,16 @@ def run_ours(args, ws, rank, local):
     value = ws * flops * args.steps / t / 1e12
     st, ss, ll = agg
 
-    # roofline of the dominant kernel (FP64 SYRK/GEMM update, DFMA pipe)
+    # roofline of the dominant kernel (FP64 SYRK/GEMM update on the DFMA pipe): ALU peak
+    # = 152 SMs x 4 FP64 flops per clock x the maximum SM clock
     pk, pk_kind = peaks()
-    fp64_peak = pk["bf16_tflops"] * FP64_OVER_BF16_NOMINAL
+    fp64_peak = NSM * FP64_FLOPS_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = (upd_flops / (upd_ms / 1e3) / 1e12) if upd_ms > 0 else None
     sha = kernel_source_sha()
     traffic = profiled_traffic("dgemm_update_fp64_n65536", sha) if (n == 65536 and not w.mixed) else None
     roofline = {"kernel": "k_dgemm_update", "bound": "alu", "achieved": achieved, "peak": round(fp64_peak, 4),
                 "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": traffic,
-                "peak_source": f"{pk_kind} bf16 x nominal FP64/BF16 ratio (1.25/2250)",
+                "peak_source": f"ALU: 152 SMs x 4 FP64 flop/clk x {pk_kind} max SM clock",
                 "update_share_of_step": (upd_ms / 1e3) / t if t > 0 else None}
 
     # end to end: the same step through host (pinned) buffers, copies inside the timed region
