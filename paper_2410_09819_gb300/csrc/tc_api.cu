@@ -52,6 +52,10 @@ struct tc_handle_s {
     DevBuf partials;   // split-K partial blocks
     DevBuf vec;        // solve workspace
     DevBuf sumsq;      // tile sums of squares
+    // mixed precision: operand pools, tables and tensor maps
+    DevBuf pool_hi, pool_lo, pool16, pool8;
+    DevBuf mxtab;
+    CUtensorMap map_hi{}, map_lo{}, map16{}, map8{};
     int64_t launches = 0;
     int64_t upd_launches[4] = {0, 0, 0, 0};
 
@@ -276,7 +280,166 @@ Plan build_plan(double *W, int nt, int b, const std::vector<uint8_t> &map, bool 
 
 size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
 
-int run_fp64_factor(tc_handle h, const Plan &P) {
+
+// ----------------------------------------------------------- mixed-precision schedule
+// Which low-precision operand copies each final tile needs (Section IV-C: an update runs
+// in the precision of the tile it writes, so tile (i, j) is needed in p(i, k') for every
+// output (i, k'), j < k' < i, that reads it as X, and in p(m, i) for every output (m, i),
+// m > i, that reads it as Y), the pool slot of each copy, and per column the tensor-core
+// work items, the tiles to store in their precision and the copies to make.
+struct MxpPlan {
+    std::vector<int> slot[3];          // [q-1][packed tile] -> slot, -1 if not needed
+    int64_t nslots[3] = {0, 0, 0};
+    std::vector<uint8_t> prec;         // precision of every packed tile (diagonal FP64)
+    std::vector<int> tiles;            // per column: off-diagonal tiles to store / copy
+    std::vector<CopyJob> copies;
+    std::vector<QItem> qitems;
+    struct Col { int t0, nt, c0, nc, q0[3], nq[3]; };
+    std::vector<Col> cols;
+    double flops[4] = {0, 0, 0, 0};
+};
+
+MxpPlan build_mxp(int nt, int b, const std::vector<uint8_t> &map) {
+    MxpPlan M;
+    const int64_t T = tidx(nt, 0);
+    auto P = [&](int i, int j) { return (int)map[(size_t)i * nt + j]; };
+    for (int q = 0; q < 3; ++q) M.slot[q].assign(T, -1);
+    M.prec.assign(T, 0);
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < i; ++j) {
+            M.prec[tidx(i, j)] = (uint8_t)P(i, j);
+            unsigned mask = 0;
+            for (int kk = j + 1; kk < i; ++kk) mask |= 1u << P(i, kk);
+            for (int m = i + 1; m < nt; ++m) mask |= 1u << P(m, i);
+            for (int q = 1; q <= 3; ++q)
+                if (mask & (1u << q)) M.slot[q - 1][tidx(i, j)] = (int)M.nslots[q - 1]++;
+        }
+    M.cols.resize(nt);
+    const int nbk = b / 128;
+    for (int k = 0; k < nt; ++k) {
+        MxpPlan::Col &C = M.cols[k];
+        for (int q = 1; q <= 3; ++q) {
+            C.q0[q - 1] = (int)M.qitems.size();
+            if (k > 0)
+                for (int m = k + 1; m < nt; ++m) {
+                    if (P(m, k) != q) continue;
+                    for (int bn = 0; bn < nbk; ++bn)
+                        for (int bm = 0; bm < nbk; ++bm) M.qitems.push_back({m, (uint16_t)bm, (uint16_t)bn});
+                    M.flops[q] += 2.0 * b * (double)b * k * b;
+                }
+            C.nq[q - 1] = (int)M.qitems.size() - C.q0[q - 1];
+        }
+        C.t0 = (int)M.tiles.size();
+        C.c0 = (int)M.copies.size();
+        for (int m = k + 1; m < nt; ++m) {
+            const int t = (int)tidx(m, k);
+            M.tiles.push_back(t);
+            for (int q = 1; q <= 3; ++q)
+                if (M.slot[q - 1][t] >= 0) M.copies.push_back({t, q, M.slot[q - 1][t]});
+        }
+        C.nt = (int)M.tiles.size() - C.t0;
+        C.nc = (int)M.copies.size() - C.c0;
+    }
+    return M;
+}
+
+struct MxpDev {
+    const int *slot[3];
+    int *exps16, *exps8;
+    const uint8_t *prec;
+    double *amaxL, *amaxS;
+    const int *tiles;
+    const CopyJob *copies;
+    const QItem *qitems;
+};
+
+int setup_mxp(tc_handle h, const MxpPlan &M, MxpDev &D) {
+    const int b = h->b;
+    const int64_t T = tidx(h->nt, 0);
+    const size_t bb = (size_t)b * b;
+    int rc;
+    if (M.nslots[0]) {
+        if ((rc = ensure(h, h->pool_hi, M.nslots[0] * bb * 4)) || (rc = ensure(h, h->pool_lo, M.nslots[0] * bb * 4)))
+            return rc;
+    }
+    if (M.nslots[1] && (rc = ensure(h, h->pool16, M.nslots[1] * bb * 2))) return rc;
+    if (M.nslots[2] && (rc = ensure(h, h->pool8, M.nslots[2] * bb * 1))) return rc;
+    // one table buffer: slots (3T ints), exps16, exps8 (T ints each), amaxL, amaxS (T doubles),
+    // prec (T bytes), tiles, copies, qitems
+    const size_t o_slot = 0, o_e16 = align_up(o_slot + 3 * T * 4), o_e8 = align_up(o_e16 + T * 4);
+    const size_t o_aL = align_up(o_e8 + T * 4), o_aS = align_up(o_aL + T * 8), o_prec = align_up(o_aS + T * 8);
+    const size_t o_tiles = align_up(o_prec + T), o_cp = align_up(o_tiles + M.tiles.size() * 4);
+    const size_t o_q = align_up(o_cp + M.copies.size() * sizeof(CopyJob));
+    const size_t total = align_up(o_q + M.qitems.size() * sizeof(QItem));
+    if ((rc = ensure(h, h->mxtab, total))) return rc;
+    std::vector<char> host(total, 0);
+    for (int q = 0; q < 3; ++q) memcpy(host.data() + o_slot + (size_t)q * T * 4, M.slot[q].data(), T * 4);
+    memcpy(host.data() + o_prec, M.prec.data(), T);
+    if (!M.tiles.empty()) memcpy(host.data() + o_tiles, M.tiles.data(), M.tiles.size() * 4);
+    if (!M.copies.empty()) memcpy(host.data() + o_cp, M.copies.data(), M.copies.size() * sizeof(CopyJob));
+    if (!M.qitems.empty()) memcpy(host.data() + o_q, M.qitems.data(), M.qitems.size() * sizeof(QItem));
+    CK(cudaMemcpyAsync(h->mxtab.p, host.data(), total, cudaMemcpyHostToDevice, h->s));
+    char *base = static_cast<char *>(h->mxtab.p);
+    for (int q = 0; q < 3; ++q) D.slot[q] = reinterpret_cast<const int *>(base + o_slot + (size_t)q * T * 4);
+    D.exps16 = reinterpret_cast<int *>(base + o_e16);
+    D.exps8 = reinterpret_cast<int *>(base + o_e8);
+    D.amaxL = reinterpret_cast<double *>(base + o_aL);
+    D.amaxS = reinterpret_cast<double *>(base + o_aS);
+    D.prec = reinterpret_cast<const uint8_t *>(base + o_prec);
+    D.tiles = reinterpret_cast<const int *>(base + o_tiles);
+    D.copies = reinterpret_cast<const CopyJob *>(base + o_cp);
+    D.qitems = reinterpret_cast<const QItem *>(base + o_q);
+    // tensor maps over the pools (128 x 128-byte boxes, 128-byte swizzle)
+    if (M.nslots[0] && (make_pool_map(&h->map_hi, h->pool_hi.p, M.nslots[0], b, 4, 128) ||
+                        make_pool_map(&h->map_lo, h->pool_lo.p, M.nslots[0], b, 4, 128)))
+        return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the TF32 pools");
+    if (M.nslots[1] && make_pool_map(&h->map16, h->pool16.p, M.nslots[1], b, 2, 128))
+        return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the FP16 pool");
+    if (M.nslots[2] && make_pool_map(&h->map8, h->pool8.p, M.nslots[2], b, 1, 128))
+        return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the FP8 pool");
+    return TC_OK;
+}
+
+// Low-precision updates of column k (before its POTRF) and the stores / operand copies of
+// its final tiles (after its TRSMs).
+int mxp_updates(tc_handle h, const MxpPlan &M, const MxpDev &D, int k) {
+    const MxpPlan::Col &C = M.cols[k];
+    int *err = static_cast<int *>(h->status.p) + 1;
+    double *W = static_cast<double *>(h->W.p);
+    for (int q = 1; q <= 3; ++q) {
+        if (!C.nq[q - 1]) continue;
+        const CUtensorMap &a0 = q == 1 ? h->map_hi : q == 2 ? h->map16 : h->map8;
+        const CUtensorMap &a1 = q == 1 ? h->map_lo : a0;
+        const int sp = span_begin(h, CAT_UPD64 + q);
+        launch_qgemm(q, a0, a1, a0, a1, W, D.qitems + C.q0[q - 1], C.nq[q - 1], D.slot[q - 1],
+                     q == 2 ? D.exps16 : q == 3 ? D.exps8 : nullptr, k, h->b, h->nt, err, h->s);
+        span_end(h, sp);
+        CK_LAUNCH();
+        ++h->upd_launches[q];
+    }
+    return TC_OK;
+}
+
+int mxp_convert(tc_handle h, const MxpPlan &M, const MxpDev &D, int k) {
+    const MxpPlan::Col &C = M.cols[k];
+    if (!C.nt) return TC_OK;
+    double *W = static_cast<double *>(h->W.p);
+    const int sp = span_begin(h, CAT_CONVERT);
+    launch_tile_amax(W, h->b, D.tiles + C.t0, C.nt, D.amaxL, h->s);
+    CK_LAUNCH();
+    launch_store_round(W, h->b, D.tiles + C.t0, C.nt, D.prec, D.amaxL, D.amaxS, h->s);
+    CK_LAUNCH();
+    if (C.nc) {
+        launch_make_copies(W, h->b, D.copies + C.c0, C.nc, D.amaxS, static_cast<float *>(h->pool_hi.p),
+                           static_cast<float *>(h->pool_lo.p), static_cast<__half *>(h->pool16.p),
+                           static_cast<uint8_t *>(h->pool8.p), D.exps16, D.exps8, h->s);
+        CK_LAUNCH();
+    }
+    span_end(h, sp);
+    return TC_OK;
+}
+
+int run_factor(tc_handle h, const Plan &P, const MxpPlan *M) {
     const int nt = h->nt, b = h->b;
     // upload tables
     const size_t sj = P.jobs.size() * sizeof(DJob), si = P.items.size() * sizeof(DItem);
@@ -302,6 +465,16 @@ int run_fp64_factor(tc_handle h, const Plan &P) {
     int *status = static_cast<int *>(h->status.p);
     double *W = static_cast<double *>(h->W.p);
     const int64_t bb = (int64_t)b * b;
+    MxpDev D{};
+    if (M) {
+        rc = setup_mxp(h, *M, D);
+        if (rc) return rc;
+        const int64_t T = tidx(nt, 0);
+        CK(cudaMemsetAsync(D.amaxL, 0, T * sizeof(double), h->s));
+        CK(cudaMemsetAsync(D.amaxS, 0, T * sizeof(double), h->s));
+        CK(cudaMemsetAsync(D.exps16, 0, T * sizeof(int), h->s));
+        CK(cudaMemsetAsync(D.exps8, 0, T * sizeof(int), h->s));
+    }
 
     for (int k = 0; k < nt; ++k) {
         const ColPlan &C = P.cols[k];
@@ -316,14 +489,15 @@ int run_fp64_factor(tc_handle h, const Plan &P) {
             launch_dgemm_reduce(dreds + C.red0, C.nred, b, parts, status, h->s);
             CK_LAUNCH();
         }
-        double *D = W + tidx(k, k) * bb;
+        if (M && (rc = mxp_updates(h, *M, D, k))) return rc;
+        double *Dk = W + tidx(k, k) * bb;
         const int sp_potrf = span_begin(h, CAT_POTRF);
         for (int jb = 0; jb < b / 64; ++jb) {
-            launch_potrf_block(D + (int64_t)jb * 64 * b + jb * 64, b, k * b + jb * 64, status, h->s);
+            launch_potrf_block(Dk + (int64_t)jb * 64 * b + jb * 64, b, k * b + jb * 64, status, h->s);
             CK_LAUNCH();
             if (jb + 1 < b / 64) {
                 const int rows = b - (jb + 1) * 64;
-                launch_trsm_rows(D + (int64_t)jb * 64 * b + (jb + 1) * 64, D + (int64_t)jb * 64 * b + jb * 64, b,
+                launch_trsm_rows(Dk + (int64_t)jb * 64 * b + (jb + 1) * 64, Dk + (int64_t)jb * 64 * b + jb * 64, b,
                                  rows, status, h->s);
                 CK_LAUNCH();
                 const auto &pi = C.potrf_items[jb];
@@ -338,6 +512,7 @@ int run_fp64_factor(tc_handle h, const Plan &P) {
             span_end(h, sp);
             CK_LAUNCH();
         }
+        if (M && (rc = mxp_convert(h, *M, D, k))) return rc;
     }
     return TC_OK;
 }
@@ -397,7 +572,8 @@ void tc_destroy(tc_handle h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->s) cudaStreamSynchronize(h->s);
-    for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq})
+    for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq,
+                      &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab})
         release(*d);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     if (h->own_stream && h->s) cudaStreamDestroy(h->s);
@@ -536,7 +712,7 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
     }
     h->mixed = false;
     for (uint8_t v : h->map) h->mixed |= (v != TC_FP64);
-    if (h->mixed) return set_err(h, TC_ERR_UNSUPPORTED, "mixed-precision maps are not available in this build");
+    if (h->mixed && b % 128) return set_err(h, TC_ERR_UNSUPPORTED, "mixed precision needs a tile size that is a multiple of 128");
     if (h->cfg.ooc == 1) return set_err(h, TC_ERR_UNSUPPORTED, "out-of-core mode is not available in this build");
 
     rc = ensure(h, h->W, bytes);
@@ -554,21 +730,32 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
     CK(cudaMemcpyAsync(W, h->A_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
     launch_fix_padding(W, nt, b, n, h->s);
     CK_LAUNCH();
-    CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->s));
+    CK(cudaMemsetAsync(h->status.p, 0, 2 * sizeof(int), h->s));
 
     spans_reset(h);
     for (int p = 0; p < 4; ++p) h->upd_launches[p] = 0;
     Plan P = build_plan(W, nt, b, h->map, h->mixed);
-    rc = run_fp64_factor(h, P);
+    MxpPlan M;
+    if (h->mixed) {
+        M = build_mxp(nt, b, h->map);
+        for (int p = 1; p < 4; ++p) P.update_flops[p] = M.flops[p];
+    }
+    rc = run_factor(h, P, h->mixed ? &M : nullptr);
     if (rc) return rc;
     double *sc = static_cast<double *>(h->scratch.p);
     launch_logdet(W, nt, b, n, sc, h->s);
     CK_LAUNCH();
-    int info = 0;
-    CK(cudaMemcpyAsync(&info, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    int st2[2] = {0, 0};
+    CK(cudaMemcpyAsync(st2, h->status.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
     double ld = 0.0;
     CK(cudaMemcpyAsync(&ld, sc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
+    const int info = st2[0];
+    if (st2[1]) {
+        h->factored = false;
+        return set_err(h, TC_ERR_TIMEOUT, st2[1] == 2 ? "tensor-core update found no operand copy (internal)"
+                                                        : "a tensor-core update timed out waiting on its pipeline");
+    }
     h->logdet = ld;
     h->factored = (info == 0);
     if (stats) {

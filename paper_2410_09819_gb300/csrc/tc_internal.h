@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace tc {
@@ -9,7 +11,7 @@ namespace tc {
 constexpr int BLK = 64;         // FP64 kernels work on 64 x 64 blocks
 constexpr int NSM = 152;        // GB300 streaming multiprocessors
 
-inline int64_t tidx(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
+__host__ __device__ __forceinline__ int64_t tidx(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
 
 // C -= X Y^T on a (M x N) block grid; X is M x K and Y is N x K, all column-major with
 // leading dimension ld (the tile size): the layout of a tile row of the factor.
@@ -44,13 +46,18 @@ struct TStrip {
     int r0;
 };
 
-// Low-precision update job (tensor cores): C -= sum_n 2^(ex[n] + ey[n]) X_n Y_n^T over
-// the source tiles n of one output tile, operands taken from per-precision pools.
-struct QJob {
-    double *C;              // FP64 output tile (column-major, ld = b)
-    int xs0, ys0;           // index into the slot list (K-ordered source tiles)
-    int nsrc;               // number of source tiles
-    int lower;              // unused for low precision (never diagonal)
+// Tensor-core update of one 128 x 256 block (bm, bn) of output tile (m, k) (k_mxp.cu).
+struct QItem {
+    int m;
+    uint16_t bm, bn;
+};
+
+// Operand copy of packed tile `tile` in precision q (1 TF32 pair, 2 FP16, 3 FP8) into
+// slot `slot` of that precision's pool.
+struct CopyJob {
+    int tile;
+    int q;
+    int slot;
 };
 
 // ------------------------------------------------------------------ launchers (k_fp64.cu)
@@ -81,5 +88,17 @@ void launch_dot_self(const double *v, int64_t n, double *out, cudaStream_t s);
 void launch_matern(double *A, int64_t n, int b, int nt, const double *pts, double sigma2,
                    double a, int nu2, double nugget, cudaStream_t s);
 void launch_tile_sumsq(const double *A, int nt, int b, int64_t n, double *out, cudaStream_t s);
+
+// ------------------------------------------------------------------ launchers (k_mxp.cu)
+int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows);
+size_t qgemm_smem_bytes();
+void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
+                  const CUtensorMap &b1, double *W, const QItem *items, int nitems, const int *slot, const int *exps,
+                  int k, int b, int nt, int *err, cudaStream_t s);
+void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, double *amax, cudaStream_t s);
+void launch_store_round(double *W, int b, const int *tiles, int ntiles, const uint8_t *prec, const double *amaxL,
+                        double *amaxS, cudaStream_t s);
+void launch_make_copies(const double *W, int b, const CopyJob *jobs, int njobs, const double *amaxS, float *hi,
+                        float *lo, __half *p16, uint8_t *p8, int *e16, int *e8, cudaStream_t s);
 
 }  // namespace tc

@@ -1,0 +1,159 @@
+"""GPU parity of the mixed-precision path (tcgen05 FP32/FP16/FP8 updates, FP64 POTRF/TRSM,
+per-tile storage) against the oracle's Algorithm 1 emulation and exact cases."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_09819_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2410_09819_gb300 import tile_chol as tc  # noqa: E402
+
+from gpu_util import pack_padded, to_dev, unpack_lower  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def H():
+    with tc.Handle(0) as h:
+        yield h
+
+
+def gpu_mxp(H, A, b, pmap):
+    n = A.shape[0]
+    At = to_dev(pack_padded(A, b))
+    st = tc.tc_stats()
+    info = tc.tile_chol_factor(H.h, n, b, At, np.ascontiguousarray(pmap, dtype=np.uint8).reshape(-1), st)
+    L = torch.empty_like(At)
+    if info == 0:
+        tc.tile_chol_get_factor(H.h, L)
+    return info, unpack_lower(L, n, b) if info == 0 else None, st
+
+
+@pytest.mark.parametrize("n,b,seed", [(1024, 128, 1), (2048, 256, 2), (896, 128, 3)])
+def test_integer_factor_exact_for_any_precision_map(H, n, b, seed):
+    # entries of L in {-1, 0, 1}: every operand copy, tensor-core product and FP32 partial
+    # sum is exact, so the factor must come back bit for bit whatever the map says
+    rng = np.random.default_rng(seed)
+    L = np.tril(rng.integers(-1, 2, (n, n)).astype(np.float64), -1) + np.eye(n)
+    A = L @ L.T
+    nt = n // b
+    pm = np.zeros((nt, nt), dtype=np.uint8)
+    for i in range(nt):
+        for j in range(i):
+            pm[i, j] = rng.integers(0, 4)
+    info, Lg, st = gpu_mxp(H, A, b, pm)
+    assert info == 0
+    assert np.array_equal(Lg, L)
+    assert tc.tile_chol_logdet(H.h) == 0.0
+    for p in (1, 2, 3):
+        if np.any(np.tril(pm, -1)[1:, :] == p):
+            assert st.update_launches[p] >= 0
+
+
+CASES = {
+    # (n, b, nu, range, nugget, eps_high, band, prec_set)
+    "n1024_b128_eps1e-6": (1024, 128, 0.5, 0.02, 1e-4, 1e-6, 1, 4),
+    "n1536_b128_eps1e-4": (1536, 128, 0.5, 0.05, 1e-4, 1e-4, 1, 4),
+    "n2048_b256_eps1e-5": (2048, 256, 1.5, 0.03, 1e-4, 1e-5, 1, 4),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def mxp_case(request, H):
+    n, b, nu, a, nug, eps, band, ps = CASES[request.param]
+    pts = inputs.uniform_points(n, 31, morton=True)
+    A = oracle.matern(pts, 1.0, a, nu, nug)
+    nt = n // b
+    pm = np.empty(nt * nt, dtype=np.uint8)
+    tc.tile_chol_precision_map(H.h, n, b, to_dev(pack_padded(A, b)), eps, band, ps, pm)
+    pm = pm.reshape(nt, nt)
+    info, Lg, st = gpu_mxp(H, A, b, pm)
+    assert info == 0
+    ld_gpu = tc.tile_chol_logdet(H.h)
+    Lo, info_o = oracle.mxp_cholesky(A, b, pm)
+    assert info_o == 0
+    return dict(A=A, b=b, nt=nt, pm=pm, Lg=Lg, Lo=Lo, eps=eps, st=st, ld_gpu=ld_gpu, name=request.param)
+
+
+def test_mxp_map_uses_several_precisions(mxp_case):
+    pm = mxp_case["pm"]
+    low = pm[np.tril_indices(mxp_case["nt"], -1)]
+    assert len(set(low.tolist())) >= 3
+
+
+def test_mxp_stored_tiles_are_representable(mxp_case):
+    b, nt, pm, Lg = mxp_case["b"], mxp_case["nt"], mxp_case["pm"], mxp_case["Lg"]
+    for i in range(nt):
+        for j in range(i):
+            t = Lg[i * b:(i + 1) * b, j * b:(j + 1) * b]
+            if pm[i, j]:
+                assert np.array_equal(oracle.to_storage(t, int(pm[i, j])), t), (i, j, pm[i, j])
+
+
+def test_mxp_factor_matches_emulation(mxp_case):
+    b, nt, pm, Lg, Lo, eps = (mxp_case[k] for k in ("b", "nt", "pm", "Lg", "Lo", "eps"))
+    A = mxp_case["A"]
+    # Both sides run Algorithm 1 with the same map and the same operand roundings; they
+    # differ only in how update sums are accumulated (FP32 in tensor memory + an FP32
+    # running sum over source tiles vs FP64 here), and TF32x3 products for FP32 tiles.
+    # A stored low-precision element may therefore land one unit in the last place of its
+    # format away (2 u_p relative), and those differences propagate into later tiles at the
+    # size the criterion allows for the tile that produced them (~eps_high ||A||).
+    normA = np.linalg.norm(A)
+    worst = {}
+    for i in range(nt):
+        for j in range(i + 1):
+            p = int(pm[i, j]) if i != j else 0
+            d = np.abs(Lg[i * b:(i + 1) * b, j * b:(j + 1) * b] - Lo[i * b:(i + 1) * b, j * b:(j + 1) * b]).max()
+            ref = np.abs(Lo[i * b:(i + 1) * b, j * b:(j + 1) * b]).max()
+            tol = 2.0 * oracle.UNIT_ROUNDOFF[p] * ref + 8 * eps * normA / nt
+            worst[(i, j)] = d / tol if tol > 0 else 0.0
+            assert d <= tol, (mxp_case["name"], i, j, p, d, ref, tol)
+    be_g = np.linalg.norm(A - Lg @ Lg.T) / normA
+    be_o = np.linalg.norm(A - Lo @ Lo.T) / normA
+    assert be_g <= 10 * eps and be_o <= 10 * eps
+    assert be_g <= 4 * be_o + 1e-13
+
+
+def test_mxp_logdet_and_kl(mxp_case):
+    A, Lo, eps = mxp_case["A"], mxp_case["Lo"], mxp_case["eps"]
+    ld_o = oracle.logdet(Lo)
+    ld64 = oracle.logdet(oracle.cholesky(A))
+    n = A.shape[0]
+    # both MxP factors are within eps of A; their log-determinants agree to ~ n * eps-level
+    assert abs(mxp_case["ld_gpu"] - ld_o) <= 1e-6 * abs(ld_o) + n * eps
+    kl_gpu = oracle.kl_divergence(ld64, mxp_case["ld_gpu"])
+    kl_o = oracle.kl_divergence(ld64, ld_o)
+    assert abs(kl_gpu) <= 10 * abs(kl_o) + n * eps
+
+
+def test_mxp_solve_refines_to_fp64_accuracy(H):
+    n, b = 1024, 128
+    pts = inputs.uniform_points(n, 31, morton=True)
+    A = oracle.matern(pts, 1.0, 0.02, 0.5, 1e-4)
+    nt = n // b
+    At = to_dev(pack_padded(A, b))
+    pm = np.empty(nt * nt, dtype=np.uint8)
+    tc.tile_chol_precision_map(H.h, n, b, At, 1e-7, 1, 4, pm)
+    assert tc.tile_chol_factor(H.h, n, b, At, pm) == 0
+    B = inputs.gaussian(n, 4, seed=3)
+    Bd = to_dev(B.T.copy())
+    X = torch.empty_like(Bd)
+    st = tc.tc_stats()
+    tc.tile_chol_solve(H.h, 4, Bd, n, X, n, 10, 1e-13, st)
+    Xg = X.cpu().numpy().reshape(4, n).T
+    berr = np.max(np.abs(B - A @ Xg).max(0) / (np.abs(A).sum(1).max() * np.abs(Xg).max(0) + np.abs(B).max(0)))
+    assert berr <= 1e-13
+    assert 1 <= st.refine_iters <= 10
+    ll = tc.tile_chol_loglik(H.h, to_dev(B[:, 0].copy()))
+    ref = oracle.loglik(oracle.cholesky(A), B[:, 0])
+    # the log-likelihood of the MxP factor: relative error of order eps_high
+    assert abs(ll - ref) <= 1e-5 * abs(ref)
+    assert math.isfinite(ll)
