@@ -185,6 +185,28 @@ int tile_chol_loglik(tc_handle h, const double *y, double *loglik_out);
  */
 int tile_chol_get_factor(tc_handle h, double *L_tiles);
 
+/*
+ * Precision map without any allocation (the paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running while a stream
+ * is captured into a CUDA graph, code held to a fixed memory budget or a custom
+ * allocator, real-time loops).  Same map as tile_chol_precision_map, for the current CUDA
+ * device, without a handle:
+ *   A_tiles: device memory, the tile layout above (read only).
+ *   map_out: device memory, Nt*Nt bytes, row-major (written, upper part TC_FP64 = 0).
+ *   stream:  cudaStream_t to run on (NULL: the legacy default stream).  The call only
+ *            enqueues work; it does not wait for it.
+ * The per-tile sums of squares go to a fixed scratch array inside the library (263 KB,
+ * held on every GPU that loads the library until the process exits), so the size is
+ * limited to Nt = ceil(n / b) <= 256 tiles per column; larger problems get TC_ERR_ARG.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a
+ * device looks up the scratch array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls on a device share the one scratch
+ * array, so calls whose GPU work overlaps (different streams, no ordering) race and must
+ * be serialised by the caller.  Returns TC_OK, TC_ERR_ARG or TC_ERR_CUDA.
+ */
+int tile_chol_precision_map_noalloc(int64_t n, int b, const double *A_tiles, double eps_high, int band,
+                                    int prec_set, uint8_t *map_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,8 @@ __all__ = [
     "TC_FP64", "TC_FP32", "TC_FP16", "TC_FP8", "TC_OK", "TileCholError", "tc_config", "tc_stats",
     "lib", "tc_config_default", "tc_create", "tc_destroy", "tc_last_error", "tc_matern_tiles",
     "tile_chol_precision_map", "tile_chol_factor", "tile_chol_solve", "tile_chol_logdet",
-    "tile_chol_loglik", "tile_chol_get_factor", "Handle", "ntiles", "tile_count",
+    "tile_chol_loglik", "tile_chol_get_factor", "tile_chol_precision_map_noalloc", "Handle", "ntiles",
+    "tile_count",
 ]
 
 TC_FP64, TC_FP32, TC_FP16, TC_FP8 = 0, 1, 2, 3
@@ -83,6 +84,7 @@ def lib() -> ctypes.CDLL:
         "tile_chol_logdet": (ci, [H, ctypes.POINTER(cd)]),
         "tile_chol_loglik": (ci, [H, vp, ctypes.POINTER(cd)]),
         "tile_chol_get_factor": (ci, [H, vp]),
+        "tile_chol_precision_map_noalloc": (ci, [i64, ci, vp, cd, ci, ci, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -182,6 +184,16 @@ def tile_chol_loglik(h, y=None) -> float:
 
 def tile_chol_get_factor(h, L_tiles) -> None:
     _check(h, lib().tile_chol_get_factor(h, _ptr(L_tiles)))
+
+
+def tile_chol_precision_map_noalloc(n, b, A_tiles, eps_high, band, prec_set, map_out, stream=None) -> None:
+    """Precision map into a caller-owned device buffer without any allocation (see the header)."""
+    rc = lib().tile_chol_precision_map_noalloc(n, b, _ptr(A_tiles), eps_high, band, prec_set, _ptr(map_out),
+                                               stream)
+    if rc != TC_OK:
+        why = ("arguments out of range (the allocation-free path takes at most 256 tiles per column)"
+               if rc == -1 else "CUDA error")
+        raise TileCholError(rc, f"tile_chol_precision_map_noalloc: {why}")
 
 
 class Handle:
