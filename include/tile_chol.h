@@ -65,12 +65,12 @@ typedef struct tc_handle_s *tc_handle;
 typedef struct {
     int device;                 /* CUDA device ordinal (default 0) */
     void *stream;               /* cudaStream_t to run on; NULL: the handle makes one */
-    int ooc;                    /* 0: out-of-core only when the factor does not fit,
-                                   1: always out-of-core, -1: never (TC_ERR_OOM instead) */
-    int64_t device_cap_bytes;   /* out-of-core device tile-cache cap; 0: free memory - 4 GiB */
-    int prefetch_depth;         /* out-of-core: tasks of look-ahead for tile prefetch (>= 1) */
-    int lookahead;              /* 1: overlap column k+1's independent updates with the
-                                   panel of column k on a second stream (default 1) */
+    int ooc;                    /* reserved (out-of-core runs go through tile_chol_factor_ooc) */
+    int64_t device_cap_bytes;   /* tile_chol_factor_ooc: device tile-cache cap in bytes;
+                                   0: free device memory minus 4 GiB */
+    int prefetch_depth;         /* reserved: tile_chol_factor_ooc enqueues its whole static
+                                   schedule, so copies run ahead as far as free slots allow */
+    int lookahead;              /* reserved */
     int reserved[8];
 } tc_config;
 
@@ -96,7 +96,7 @@ typedef struct {
     int64_t update_launches[4];
 } tc_stats;
 
-/* Defaults: device 0, own stream, ooc auto, cap 0 (auto), prefetch 2, lookahead 1. */
+/* Defaults: device 0, own stream, cap 0 (auto), prefetch 2, lookahead 1. */
 void tc_config_default(tc_config *cfg);
 
 /* Create a handle on cfg->device.  cfg may be NULL (defaults).  *out is set on TC_OK. */
@@ -149,12 +149,31 @@ int tile_chol_precision_map(tc_handle h, int64_t n, int b, const double *A_tiles
  *   FP32 updates run as three TF32 tensor-core products (hi*hi + hi*lo + lo*hi),
  *   FP16 and FP8 (E4M3) on the tensor cores, all with FP32 accumulation.  POTRF and
  *   TRSM are FP64; each final L_mk is then stored in p(m, k).
- * Runs in device memory when the factor fits (or cfg.ooc == -1), else out-of-core
- *   with A_tiles in host memory (Section III-C/IV-B; see tc_config).
+ * Runs in device memory: the handle holds a working copy of the factor (and, when
+ *   A_tiles is host memory, a device copy of A); TC_ERR_OOM when that does not fit (use
+ *   tile_chol_factor_ooc).
  * Returns TC_OK, a positive column (not SPD), or an error.  stats may be NULL.
  */
 int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles,
                      const uint8_t *map, tc_stats *stats);
+
+/*
+ * Out-of-core factorization (Sections III-C and IV-B, Algorithms 2 and 3): A_tiles is HOST
+ * memory (best page-locked) holding A in the tile layout; on return it holds the factor L
+ * (in place, as the paper's write-back does; upper triangles of diagonal tiles are left as
+ * they were, padding rows/columns as those of the identity).  The device keeps a cache of
+ * at most cfg.device_cap_bytes of tiles: a tile an update needs is reused when cached, else
+ * copied in, evicting the least-recently-used tile that no pending task pins; the
+ * accumulator tile stays resident through its updates and L_kk until every TRSM of
+ * column k is done.  Copies run on their own streams, overlapped with the kernels.
+ * map must be NULL or all-FP64 in this build (TC_ERR_UNSUPPORTED otherwise).
+ * stats reports host<->device bytes, cache hits/misses/evictions.  Afterwards
+ * tile_chol_solve / tile_chol_loglik stream the factor from A_tiles (no refinement: A is
+ * gone) and tile_chol_logdet is available.  A_tiles must stay valid until then.
+ * Returns TC_OK, a positive column (not SPD), or an error (TC_ERR_OOM: cache below 4
+ * tiles or too small for the schedule).
+ */
+int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_tiles, const uint8_t *map, tc_stats *stats);
 
 /*
  * Solve A X = B with the last factor: forward (L Z = B) and back (L^T X = Z)

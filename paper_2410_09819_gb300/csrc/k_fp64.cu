@@ -562,4 +562,164 @@ void launch_dot_self(const double *v, int64_t n, double *out, cudaStream_t s) {
     k_dot_self<<<1, 1024, 0, s>>>(v, n, out);
 }
 
+// ------------------------------------------------------------- tile-pointer variants
+// Used by the out-of-core executor, whose tiles live in cache slots at arbitrary
+// addresses: the job comes by value and the grid is the 64 x 64 block grid.
+__global__ void __launch_bounds__(256, 2) k_dgemm_tile(const DJob job, int ld) {
+    const int bi = blockIdx.x, bj = blockIdx.y;
+    if (job.lower && bi < bj) return;
+    __shared__ double Xs[16][64], Ys[16][64];
+    double acc[4][4] = {};
+    dgemm_block(acc, job.X + bi * 64, job.Y + bj * 64, ld, 0, job.K, Xs, Ys);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double *C = job.C + (int64_t)bj * 64 * ld + bi * 64;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) C[(int64_t)(ty + 16 * j) * ld + tx + 16 * i] -= acc[i][j];
+}
+
+// TRSM of one tile held at C with L_kk at L (one CTA per 64-row strip).
+__global__ void __launch_bounds__(256, 2) k_trsm_tile(double *C, const double *L, int ld, int b, const int *status) {
+    if (failed(status)) return;
+    extern __shared__ double smem[];
+    double(*Xs)[64] = reinterpret_cast<double(*)[64]>(smem);
+    double(*Ys)[64] = reinterpret_cast<double(*)[64]>(smem + 16 * 64);
+    double(*Ls)[65] = reinterpret_cast<double(*)[65]>(smem + 32 * 64);
+    double(*Ss)[65] = reinterpret_cast<double(*)[65]>(smem + 32 * 64 + 64 * 65);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double *X = C + blockIdx.x * 64;
+    for (int jb = 0; jb < b / 64; ++jb) {
+        double acc[4][4] = {};
+        dgemm_block(acc, X, L + jb * 64, ld, 0, jb * 64, Xs, Ys);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                Ss[tx + 16 * i][ty + 16 * j] = X[(int64_t)(jb * 64 + ty + 16 * j) * ld + tx + 16 * i] - acc[i][j];
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int r = idx & 63, c = idx >> 6;
+            Ls[r][c] = (r >= c) ? L[(int64_t)(jb * 64 + c) * ld + jb * 64 + r] : 0.0;
+        }
+        __syncthreads();
+        strip_solve(Ss, Ls);
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int r = idx & 63, c = idx >> 6;
+            X[(int64_t)(jb * 64 + c) * ld + r] = Ss[r][c];
+        }
+        __syncthreads();
+    }
+}
+
+// sum of log of the nv leading diagonal entries of one tile, fixed order, into *out
+__global__ void __launch_bounds__(256) k_logdiag_tile(const double *D, int b, int nv, double *out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int r = threadIdx.x; r < nv; r += 256) s += log(D[(int64_t)r * b + r]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// padding of one tile of the last tile row: rows >= nv zero (off-diagonal), identity
+// outside the nv x nv block (diagonal)
+__global__ void k_fix_padding_tile(double *T, int b, int nv, int diag) {
+    const int64_t bb = (int64_t)b * b;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % b), c = (int)(e / b);
+        if (!diag) {
+            if (r >= nv) T[e] = 0.0;
+        } else if (r >= nv || c >= nv) {
+            T[e] = (r == c) ? 1.0 : 0.0;
+        }
+    }
+}
+
+// r_i -= L_ij z_j for one tile L_ij (ptr), rows of tile row i; grid = b/64 chunks
+__global__ void __launch_bounds__(256)
+k_fwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs) {
+    __shared__ double zs[128][16];
+    __shared__ double red[64][17];
+    const int r0 = blockIdx.x * 64;
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int c0 = 0; c0 < b; c0 += 128) {
+        __syncthreads();
+        for (int e = tid; e < 128 * nrhs; e += 256) {
+            const int c = e % 128, q = e / 128;
+            zs[c][q] = R[q * ldr + (int64_t)j * b + c0 + c];
+        }
+        __syncthreads();
+        for (int c = part; c < 128; c += 4) {
+            const double l = L[(int64_t)(c0 + c) * b + r0 + rr];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q < nrhs) acc[q] = fma(l, zs[c][q], acc[q]);
+        }
+    }
+    part_reduce_sub(red, acc, nrhs, R, ldr, (int64_t)i * b + r0);
+}
+
+// z_i -= L_ji^T x_j for one tile L_ji (ptr); grid = b/64 chunks of tile row i
+__global__ void __launch_bounds__(256)
+k_bwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs) {
+    __shared__ double xs[64][16];
+    __shared__ double S[64][65];
+    const int r0 = blockIdx.x * 64;
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int c0 = 0; c0 < b; c0 += 64) {
+        __syncthreads();
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int c = idx & 63, r = idx >> 6;
+            S[r][c] = L[(int64_t)(r0 + r) * b + c0 + c];
+        }
+        for (int e = tid; e < 64 * nrhs; e += 256) {
+            const int c = e % 64, q = e / 64;
+            xs[c][q] = R[q * ldr + (int64_t)j * b + c0 + c];
+        }
+        __syncthreads();
+        for (int c = part; c < 64; c += 4) {
+            const double l = S[rr][c];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
+        }
+    }
+    part_reduce_sub(reinterpret_cast<double(*)[17]>(&S[0][0]), acc, nrhs, R, ldr, (int64_t)i * b + r0);
+}
+
+void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s) {
+    k_dgemm_tile<<<dim3(job.M / 64, job.N / 64), 256, 0, s>>>(job, ld);
+}
+void launch_trsm_tile(double *C, const double *L, int ld, int b, const int *status, cudaStream_t s) {
+    const size_t smem = (32 * 64 + 2 * 64 * 65) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_trsm_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_trsm_tile<<<b / 64, 256, smem, s>>>(C, L, ld, b, status);
+}
+void launch_logdiag_tile(const double *D, int b, int nv, double *out, cudaStream_t s) {
+    k_logdiag_tile<<<1, 256, 0, s>>>(D, b, nv, out);
+}
+void launch_fix_padding_tile(double *T, int b, int nv, int diag, cudaStream_t s) {
+    k_fix_padding_tile<<<64, 256, 0, s>>>(T, b, nv, diag);
+}
+void launch_fwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
+    k_fwd_update_tile<<<b / 64, 256, 0, s>>>(L, b, i, j, R, ldr, nrhs);
+}
+void launch_bwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
+    k_bwd_update_tile<<<b / 64, 256, 0, s>>>(L, b, i, j, R, ldr, nrhs);
+}
+
 }  // namespace tc

@@ -9,8 +9,7 @@
 //   3. the TRSMs of the tiles below it (one CTA per 64-row strip),
 // and uploads the tables once.  Stream order replaces the paper's Ready table: a launch
 // starts only after everything it reads has been written by earlier launches.
-#include "../../include/tile_chol.h"
-#include "tc_internal.h"
+#include "tc_handle.h"
 
 #include <algorithm>
 #include <chrono>
@@ -22,166 +21,7 @@
 
 using namespace tc;
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-struct tc_handle_s {
-    tc_config cfg{};
-    int device = 0;
-    cudaStream_t s = nullptr;
-    bool own_stream = false;
-    std::string err;
-
-    // last factorization
-    int64_t n = 0;
-    int b = 0, nt = 0;
-    bool factored = false;
-    bool mixed = false;
-    double logdet = 0.0;
-    double normA_inf = -1.0;
-    std::vector<uint8_t> map;
-
-    DevBuf W;          // FP64 factor tiles (the working copy of A)
-    DevBuf Acopy;      // device copy of the caller's A when it was given in host memory
-    const double *A_dev = nullptr;
-    DevBuf status;     // int info word + padding
-    DevBuf scratch;    // small doubles: logdet, norms, maxima
-    DevBuf tables;     // schedule tables
-    DevBuf partials;   // split-K partial blocks
-    DevBuf vec;        // solve workspace
-    DevBuf sumsq;      // tile sums of squares
-    // mixed precision: operand pools, tables and tensor maps
-    DevBuf pool_hi, pool_lo, pool16, pool8;
-    DevBuf mxtab;
-    CUtensorMap map_hi{}, map_lo{}, map16{}, map8{};
-    int64_t launches = 0;
-    int64_t upd_launches[4] = {0, 0, 0, 0};
-
-    // CUDA-event spans of the last factorization, by category (see Cat)
-    std::vector<cudaEvent_t> events;
-    size_t events_used = 0;
-    struct Span { int cat; cudaEvent_t a, b; };
-    std::vector<Span> spans;
-};
-
-enum Cat { CAT_UPD64 = 0, CAT_UPD32, CAT_UPD16, CAT_UPD8, CAT_POTRF, CAT_TRSM, CAT_CONVERT, CAT_N };
-
 namespace {
-
-int set_err(tc_handle h, int code, const std::string &msg) {
-    if (h) h->err = msg;
-    return code;
-}
-
-int cuda_fail(tc_handle h, cudaError_t e, const char *what, int line) {
-    char buf[512];
-    snprintf(buf, sizeof buf, "%s failed: %s (%s) [tc_api.cu:%d]", what, cudaGetErrorName(e),
-             cudaGetErrorString(e), line);
-    return set_err(h, e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA, buf);
-}
-
-#define CK(call)                                                        \
-    do {                                                                \
-        cudaError_t e_ = (call);                                        \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call, __LINE__); \
-    } while (0)
-
-#define CK_LAUNCH()                                                                   \
-    do {                                                                              \
-        cudaError_t e_ = cudaGetLastError();                                          \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, "kernel launch", __LINE__);    \
-        ++h->launches;                                                                \
-    } while (0)
-
-bool on_device(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-int ensure(tc_handle h, DevBuf &d, size_t bytes) {
-    if (d.bytes >= bytes && d.p) return TC_OK;
-    if (d.p) cudaFree(d.p);
-    d.p = nullptr;
-    d.bytes = 0;
-    cudaError_t e = cudaMalloc(&d.p, bytes ? bytes : 16);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        char buf[160];
-        snprintf(buf, sizeof buf, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
-        return set_err(h, TC_ERR_OOM, buf);
-    }
-    d.bytes = bytes;
-    return TC_OK;
-}
-
-void release(DevBuf &d) {
-    if (d.p) cudaFree(d.p);
-    d.p = nullptr;
-    d.bytes = 0;
-}
-
-// Copy between any two pointers the runtime can classify (cudaMemcpyDefault).
-int copy_any(tc_handle h, void *dst, const void *src, size_t bytes) {
-    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->s));
-    return TC_OK;
-}
-
-cudaEvent_t next_event(tc_handle h) {
-    if (h->events_used == h->events.size()) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-        h->events.push_back(e);
-    }
-    return h->events[h->events_used++];
-}
-
-// Open a timed span on the handle's stream; close it with span_end.
-int span_begin(tc_handle h, int cat) {
-    cudaEvent_t a = next_event(h), b = next_event(h);
-    if (!a || !b) return -1;
-    cudaEventRecord(a, h->s);
-    h->spans.push_back({cat, a, b});
-    return (int)h->spans.size() - 1;
-}
-
-void span_end(tc_handle h, int id) {
-    if (id >= 0) cudaEventRecord(h->spans[id].b, h->s);
-}
-
-// Sum the spans per category (the stream must be synchronised).
-void span_totals(tc_handle h, double *ms) {
-    for (int c = 0; c < CAT_N; ++c) ms[c] = 0.0;
-    for (auto &sp : h->spans) {
-        float t = 0.f;
-        if (cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess) ms[sp.cat] += t;
-        else cudaGetLastError();
-    }
-}
-
-void spans_reset(tc_handle h) {
-    h->spans.clear();
-    h->events_used = 0;
-}
-
-double now_ms() {
-    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-
-int check_nb(tc_handle h, int64_t n, int b) {
-    if (!h) return TC_ERR_ARG;
-    if (n < 1) return set_err(h, TC_ERR_ARG, "n must be >= 1");
-    if (b < 64 || b > 4096 || b % 64) return set_err(h, TC_ERR_ARG, "tile size b must be a multiple of 64 in [64, 4096]");
-    const int64_t nt = (n + b - 1) / b;
-    if (nt > 65535) return set_err(h, TC_ERR_ARG, "too many tiles per column");
-    return TC_OK;
-}
 
 // ------------------------------------------------------------------ static schedule
 struct ColPlan {
@@ -573,8 +413,10 @@ void tc_destroy(tc_handle h) {
     cudaSetDevice(h->device);
     if (h->s) cudaStreamSynchronize(h->s);
     for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq,
-                      &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab})
+                      &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab, &h->logdiag})
         release(*d);
+    if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
+    if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     if (h->own_stream && h->s) cudaStreamDestroy(h->s);
     delete h;
@@ -691,6 +533,7 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
     const double t0 = now_ms();
     const int64_t launches0 = h->launches;
     h->factored = false;
+    h->ooc = false;
     h->normA_inf = -1.0;
     const int nt = (int)((n + b - 1) / b);
     const int64_t T = (int64_t)nt * (nt + 1) / 2;
@@ -793,6 +636,7 @@ int tile_chol_logdet(tc_handle h, double *logdet_out) {
 // Forward (and optionally back) substitution on the padded column-major buffer R
 // (leading dimension ldr = nt*b), nrhs <= 16 per pass.
 static int subst(tc_handle h, double *R, int64_t ldr, int nrhs, bool back) {
+    if (h->ooc) return ooc_subst(h, R, ldr, nrhs, back, nullptr);
     const int nt = h->nt, b = h->b;
     const double *W = static_cast<const double *>(h->W.p);
     const int64_t bb = (int64_t)b * b;
@@ -842,6 +686,7 @@ int tile_chol_solve(tc_handle h, int nrhs, const double *B, int64_t ldb, double 
     if (rc) return rc;
     double *sc = static_cast<double *>(h->scratch.p);
     // ||A||_inf (once per factor): max row sum of |A| = max of |A| * ones
+    if (h->ooc) max_refine = 0;      // A was overwritten by the out-of-core factor: no residuals
     if (h->normA_inf < 0 && max_refine > 0) {
         CK(cudaMemsetAsync(Rd, 0, (size_t)ldr * sizeof(double), h->s));
         // ones vector in Rd[ldr .. 2 ldr) is not needed: use a dedicated column of Rd
@@ -948,7 +793,8 @@ int tile_chol_get_factor(tc_handle h, double *L_tiles) {
         if (rc) return rc;
         dst = static_cast<double *>(tmp.p);
     }
-    CK(cudaMemcpyAsync(dst, h->W.p, bytes, cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(dst, h->ooc ? static_cast<const void *>(h->host_factor) : h->W.p, bytes, cudaMemcpyDefault,
+                       h->s));
     launch_zero_upper_diag(dst, nt, b, h->n, h->s);
     CK_LAUNCH();
     if (!dev) CK(cudaMemcpyAsync(L_tiles, dst, bytes, cudaMemcpyDeviceToHost, h->s));

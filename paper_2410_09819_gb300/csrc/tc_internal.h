@@ -72,6 +72,14 @@ void launch_logdet(const double *W, int nt, int b, int64_t n, double *out, cudaS
 void launch_fix_padding(double *W, int nt, int b, int64_t n, cudaStream_t s);
 void launch_zero_upper_diag(double *W, int nt, int b, int64_t n, cudaStream_t s);
 
+// tile-pointer variants (out-of-core executor)
+void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s);
+void launch_trsm_tile(double *C, const double *L, int ld, int b, const int *status, cudaStream_t s);
+void launch_logdiag_tile(const double *D, int b, int nv, double *out, cudaStream_t s);
+void launch_fix_padding_tile(double *T, int b, int nv, int diag, cudaStream_t s);
+void launch_fwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s);
+void launch_bwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s);
+
 // solves (column-major right-hand sides, leading dimension ldr, nrhs <= 16 per launch)
 void launch_fwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs, cudaStream_t s);
 void launch_fwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s);

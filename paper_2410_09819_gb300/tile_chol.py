@@ -15,7 +15,7 @@ import numpy as np
 __all__ = [
     "TC_FP64", "TC_FP32", "TC_FP16", "TC_FP8", "TC_OK", "TileCholError", "tc_config", "tc_stats",
     "lib", "tc_config_default", "tc_create", "tc_destroy", "tc_last_error", "tc_matern_tiles",
-    "tile_chol_precision_map", "tile_chol_factor", "tile_chol_solve", "tile_chol_logdet",
+    "tile_chol_precision_map", "tile_chol_factor", "tile_chol_factor_ooc", "tile_chol_solve", "tile_chol_logdet",
     "tile_chol_loglik", "tile_chol_get_factor", "tile_chol_precision_map_noalloc", "Handle", "ntiles",
     "tile_count",
 ]
@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
         "tc_matern_tiles": (ci, [H, i64, ci, vp, cd, cd, cd, cd, vp]),
         "tile_chol_precision_map": (ci, [H, i64, ci, vp, cd, ci, ci, vp, vp]),
         "tile_chol_factor": (ci, [H, i64, ci, vp, vp, ctypes.POINTER(tc_stats)]),
+        "tile_chol_factor_ooc": (ci, [H, i64, ci, vp, vp, ctypes.POINTER(tc_stats)]),
         "tile_chol_solve": (ci, [H, ci, vp, i64, vp, i64, ci, cd, ctypes.POINTER(tc_stats)]),
         "tile_chol_logdet": (ci, [H, ctypes.POINTER(cd)]),
         "tile_chol_loglik": (ci, [H, vp, ctypes.POINTER(cd)]),
@@ -162,6 +163,13 @@ def tile_chol_factor(h, n, b, A_tiles, map=None, stats: tc_stats | None = None) 
     """Returns 0, or the 1-based column of a non-positive pivot (matrix not SPD)."""
     return _check(h, lib().tile_chol_factor(h, n, b, _ptr(A_tiles), _ptr(map),
                                             ctypes.byref(stats) if stats is not None else None),
+                  allow_positive=True)
+
+
+def tile_chol_factor_ooc(h, n, b, A_tiles, map=None, stats: tc_stats | None = None) -> int:
+    """Out-of-core factor: A_tiles (host) is overwritten by L.  Returns 0 or the failing column."""
+    return _check(h, lib().tile_chol_factor_ooc(h, n, b, _ptr(A_tiles), _ptr(map),
+                                                ctypes.byref(stats) if stats is not None else None),
                   allow_positive=True)
 
 
