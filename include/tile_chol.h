@@ -205,6 +205,36 @@ int tile_chol_loglik(tc_handle h, const double *y, double *loglik_out);
 int tile_chol_get_factor(tc_handle h, double *L_tiles);
 
 /*
+ * Batched factorization of many independent SPD matrices sharing one tile size b (the
+ * geospatial batched workload: uneven n, one map each).  Every column step of the
+ * left-looking algorithm is one grouped launch over all matrices that have that column,
+ * and the whole launch sequence is captured once into a CUDA graph and replayed while
+ * the batch (count, n[], b, the A pointers and the maps) repeats.
+ *   n[count]:        orders (each >= 1; ceil(n/b) <= 65535).
+ *   A_tiles[count]:  pointers, each host or device memory, each in the tile layout of its n.
+ *                    Read only; must stay valid until the handle's next factor or destroy.
+ *   maps:            NULL (all FP64) or count pointers, each NULL or Nt_i*Nt_i bytes.
+ *   info_out[count], logdet_out[count]: optional outputs per matrix (0 / log|A_i|).
+ * Returns TC_OK, the info of the first failing matrix (> 0), or an error.  tile_chol_logdet
+ * afterwards reports the first matrix; the *_batched solve/likelihood cover all of them.
+ */
+int tile_chol_factor_batched(tc_handle h, int count, const int64_t *n, int b, const double *const *A_tiles,
+                             const uint8_t *const *maps, int *info_out, double *logdet_out, tc_stats *stats);
+
+/*
+ * Solve A_i X_i = B_i for every matrix of the last batched factorization, with up to
+ * max_refine refinement steps per matrix (FP64 residuals with the caller's A_i) until its
+ * normwise backward error is <= target_berr.  B[i], X[i]: n_i x nrhs column-major with
+ * leading dimension n_i, host or device.  berr_out[count] (optional): final backward errors.
+ */
+int tile_chol_solve_batched(tc_handle h, int nrhs, const double *const *B, double *const *X, int max_refine,
+                            double target_berr, double *berr_out, tc_stats *stats);
+
+/* Eq. 1 for every matrix of the last batched factorization; y NULL: at y = 0; else y[i]
+ * (n_i doubles, host or device).  loglik_out[count]. */
+int tile_chol_loglik_batched(tc_handle h, const double *const *y, double *loglik_out);
+
+/*
  * Precision map without any allocation (the paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- code running while a stream
  * is captured into a CUDA graph, code held to a fixed memory budget or a custom

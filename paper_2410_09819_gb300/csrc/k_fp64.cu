@@ -48,10 +48,10 @@ __device__ __forceinline__ bool failed(const int *status) {
 __global__ void __launch_bounds__(256, 2)
 k_dgemm_update(const DJob *__restrict__ jobs, const DItem *__restrict__ items, int ld,
                double *__restrict__ partials, const int *status) {
-    if (failed(status)) return;
     __shared__ double Xs[16][64], Ys[16][64];
     const DItem it = items[blockIdx.x];
     const DJob jb = jobs[it.job];
+    if (failed(status) || failed(jb.status)) return;
     const int i0 = it.bi * 64, j0 = it.bj * 64;
     double acc[4][4] = {};
     dgemm_block(acc, jb.X + i0, jb.Y + j0, ld, it.k0, it.k1, Xs, Ys);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_trsm_rows(double *P, const double *L, i
 // left-looking over the 64-column blocks of L_kk.
 __global__ void __launch_bounds__(256, 2)
 k_trsm_strips(const TStrip *__restrict__ strips, int ld, int b, const int *status) {
-    if (failed(status)) return;
+    if (failed(status) || failed(strips[blockIdx.x].status)) return;
     extern __shared__ double smem[];
     double(*Xs)[64] = reinterpret_cast<double(*)[64]>(smem);
     double(*Ys)[64] = reinterpret_cast<double(*)[64]>(smem + 16 * 64);
@@ -496,6 +496,121 @@ __global__ void __launch_bounds__(1024) k_dot_self(const double *v, int64_t n, d
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = red[0];
+}
+
+
+// Batched POTRF step: one CTA per matrix entry (same 64-block position in each).
+__global__ void __launch_bounds__(256) k_potrf_blocks(const PEntry *__restrict__ e, int ld) {
+    const PEntry E = e[blockIdx.x];
+    if (failed(E.status)) return;
+    __shared__ double S[64][65];
+    __shared__ int fail;
+    const int tid = threadIdx.x;
+    double *D = E.D;
+    for (int idx = tid; idx < 4096; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        S[r][c] = (r >= c) ? D[(int64_t)c * ld + r] : 0.0;
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int j = 0; j < 64; ++j) {
+        if (tid == 0) {
+            const double d = S[j][j];
+            if (!(d > 0.0)) fail = j + 1;
+            else S[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail) break;
+        const double p = S[j][j];
+        if (tid > j && tid < 64) S[tid][j] = S[tid][j] / p;
+        __syncthreads();
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int r = idx & 63, c = idx >> 6;
+            if (c > j && r >= c) S[r][c] = S[r][c] - S[r][j] * S[c][j];
+        }
+        __syncthreads();
+    }
+    if (fail) {
+        if (tid == 0) atomicCAS(E.status, 0, E.col0 + fail);
+        return;
+    }
+    for (int idx = tid; idx < 4096; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        if (r >= c) D[(int64_t)c * ld + r] = S[r][c];
+    }
+}
+
+// Batched POTRF panel: rows below each entry's factored 64-block (grid.y = entry).
+__global__ void __launch_bounds__(256) k_trsm_rows_batched(const PEntry *__restrict__ e, int ld) {
+    const PEntry E = e[blockIdx.y];
+    if (failed(E.status) || (int)blockIdx.x * 64 >= E.rows) return;
+    __shared__ double Ls[64][65], Ss[64][65];
+    const int tid = threadIdx.x;
+    const double *L = E.D;
+    double *Pb = E.D + 64 + blockIdx.x * 64;
+    for (int idx = tid; idx < 4096; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        Ls[r][c] = (r >= c) ? L[(int64_t)c * ld + r] : 0.0;
+        Ss[r][c] = Pb[(int64_t)c * ld + r];
+    }
+    __syncthreads();
+    strip_solve(Ss, Ls);
+    for (int idx = tid; idx < 4096; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        Pb[(int64_t)c * ld + r] = Ss[r][c];
+    }
+}
+
+void launch_potrf_blocks(const PEntry *e, int n, int ld, cudaStream_t s) {
+    if (n > 0) k_potrf_blocks<<<n, 256, 0, s>>>(e, ld);
+}
+void launch_trsm_rows_batched(const PEntry *e, int n, int max_rows, int ld, cudaStream_t s) {
+    if (n > 0 && max_rows > 0) k_trsm_rows_batched<<<dim3(max_rows / 64, n), 256, 0, s>>>(e, ld);
+}
+
+
+// log|A_i| = 2 sum log L_ii for every matrix of a batch (one CTA each, fixed order)
+__global__ void __launch_bounds__(256) k_logdet_batched(const LEntry *__restrict__ e, int b, double *out) {
+    __shared__ double red[256];
+    const LEntry E = e[blockIdx.x];
+    double s = 0.0;
+    for (int64_t g = threadIdx.x; g < E.n; g += 256) {
+        const int t = (int)(g / b), r = (int)(g % b);
+        const double *D = E.W + ((int64_t)t * (t + 1) / 2 + t) * (int64_t)b * b;
+        s += log(D[(int64_t)r * b + r]);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = 2.0 * red[0];
+}
+
+// identity padding of the last tile row of every ragged matrix (grid.z = matrix)
+__global__ void k_fix_padding_batched(const LEntry *__restrict__ e, int b) {
+    const LEntry E = e[blockIdx.z];
+    const int j = blockIdx.y, i = E.nt - 1;
+    if (j > i || E.n % b == 0) return;
+    const int nv = (int)(E.n - (int64_t)i * b);
+    double *T = E.W + ((int64_t)i * (i + 1) / 2 + j) * (int64_t)b * b;
+    const int64_t bb = (int64_t)b * b;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < bb; x += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(x % b), c = (int)(x / b);
+        if (j < i) {
+            if (r >= nv) T[x] = 0.0;
+        } else if (r >= nv || c >= nv) {
+            T[x] = (r == c) ? 1.0 : 0.0;
+        }
+    }
+}
+
+void launch_logdet_batched(const LEntry *e, int count, int b, double *out, cudaStream_t s) {
+    if (count > 0) k_logdet_batched<<<count, 256, 0, s>>>(e, b, out);
+}
+void launch_fix_padding_batched(const LEntry *e, int count, int ntmax, int b, cudaStream_t s) {
+    if (count > 0) k_fix_padding_batched<<<dim3(16, ntmax, count), 256, 0, s>>>(e, b);
 }
 
 // ---------------------------------------------------------------------------- launchers

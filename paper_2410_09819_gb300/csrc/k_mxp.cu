@@ -145,11 +145,10 @@ constexpr int QTHREADS = 320;
 constexpr unsigned long long QTIMEOUT_NS = 4000000000ull;  // 4 s per wait, then give up
 
 struct QArgs {
-    double *W;            // FP64 factor tiles
     const QItem *items;
-    const int *slot;      // slot of each packed tile in this precision's pool (-1: none)
+    const int *slot;      // slot of each (global) packed tile in this precision's pool (-1: none)
     const int *exps;      // scale exponents of the copies (FP16/FP8), nullptr for TF32
-    int k, b, nt;
+    int k, b;
     int *err;             // error word: set on a timed-out wait or a missing operand slot
 };
 
@@ -307,7 +306,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
     const uint32_t tmem = *tmem_holder;
 
     const int *slot = args.slot;
-    const int tx_row = it.m, ty_row = k;   // X tiles from tile row m, Y tiles from tile row k
+    const int xoff = it.xoff, yoff = it.yoff;   // X tiles (m, n) = xoff + n, Y tiles (k, n) = yoff + n
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
@@ -322,7 +321,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
                 }
                 const int n = s / steps_per_src, j = s % steps_per_src;
                 const int kb = j / PASSES, pass = j % PASSES;
-                const int sx = slot[tidx(tx_row, n)], sy = slot[tidx(ty_row, n)];
+                const int sx = slot[xoff + n], sy = slot[yoff + n];
                 if (sx < 0 || sy < 0) {
                     *abort_flag = 1;
                     atomicExch(args.err, 2);
@@ -394,7 +393,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
         if (KIND != 1) {
             eref = -100000;
             for (int n = 0; n < nsrc; ++n) {
-                const int e = args.exps[tidx(tx_row, n)] + args.exps[tidx(ty_row, n)];
+                const int e = args.exps[xoff + n] + args.exps[yoff + n];
                 eref = e > eref ? e : eref;
             }
         }
@@ -404,7 +403,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
             if (!mbar_wait(accf + a, use & 1, abort_flag)) { ok = false; break; }
             tc_fence_after();
             float sc = 1.f;
-            if (KIND != 1) sc = ldexpf(1.f, args.exps[tidx(tx_row, n)] + args.exps[tidx(ty_row, n)] - eref);
+            if (KIND != 1) sc = ldexpf(1.f, args.exps[xoff + n] + args.exps[yoff + n] - eref);
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + a * QBN + half * EC;
 #pragma unroll
             for (int c = 0; c < EC / 32; ++c) {
@@ -422,7 +421,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
             atomicExch(args.err, 1);
         } else {
             const int row = it.bm * QBM + quarter * 32 + lane;
-            double *C = args.W + tidx(it.m, k) * (int64_t)b * b;
+            double *C = it.C;
             const double sref = ldexp(1.0, eref);
 #pragma unroll
             for (int j = 0; j < EC; ++j) {
@@ -486,10 +485,10 @@ static void launch_q(const CUtensorMap &a0, const CUtensorMap &a1, const CUtenso
 }
 
 void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
-                  const CUtensorMap &b1, double *W, const QItem *items, int nitems, const int *slot, const int *exps,
-                  int k, int b, int nt, int *err, cudaStream_t s) {
+                  const CUtensorMap &b1, const QItem *items, int nitems, const int *slot, const int *exps,
+                  int k, int b, int *err, cudaStream_t s) {
     if (nitems <= 0) return;
-    QArgs args{W, items, slot, exps, k, b, nt, err};
+    QArgs args{items, slot, exps, k, b, err};
     if (kind == 1) launch_q<1>(a0, a1, b0, b1, args, nitems, s);
     else if (kind == 2) launch_q<2>(a0, a1, b0, b1, args, nitems, s);
     else launch_q<3>(a0, a1, b0, b1, args, nitems, s);

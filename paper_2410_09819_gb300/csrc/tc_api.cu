@@ -24,11 +24,20 @@ using namespace tc;
 namespace {
 
 // ------------------------------------------------------------------ static schedule
+// The plan covers a list of matrices sharing one tile size (a single factorization is a
+// list of one): column step k groups the work of column k of every matrix that has one,
+// so each launch below serves the whole batch.
+struct PotrfStep {
+    int pe0 = 0, npe = 0;        // PEntry range (one per matrix)
+    int it0 = 0, nit = 0;        // trailing-update items
+    int rows = 0;                // panel rows below the 64-block
+};
+
 struct ColPlan {
     int it0 = 0, nit = 0;        // FP64 update items
     int red0 = 0, nred = 0;      // split-K reductions
     int st0 = 0, nst = 0;        // TRSM strips
-    std::vector<std::pair<int, int>> potrf_items;  // (first item, count) per 64-panel (trailing update)
+    std::vector<PotrfStep> potrf;
 };
 
 struct Plan {
@@ -36,8 +45,10 @@ struct Plan {
     std::vector<DItem> items;
     std::vector<DRed> reds;
     std::vector<TStrip> strips;
+    std::vector<PEntry> pentries;
+    std::vector<LEntry> lentries;
     std::vector<ColPlan> cols;
-    int max_parts = 0;
+    int max_parts = 0, ntmax = 0;
     double update_flops[4] = {0, 0, 0, 0};
     double trsm_flops = 0, potrf_flops = 0;
 };
@@ -65,122 +76,176 @@ void emit_job_items(Plan &P, int job, int ld, int splits, int &part_next) {
         }
 }
 
-Plan build_plan(double *W, int nt, int b, const std::vector<uint8_t> &map, bool mixed) {
+Plan build_plan(tc_handle h, double *W, int *status) {
     Plan P;
-    P.cols.resize(nt);
+    const int b = h->b;
     const int64_t bb = (int64_t)b * b;
-    auto T = [&](int i, int j) { return W + tidx(i, j) * bb; };
-    for (int k = 0; k < nt; ++k) {
+    for (const MatDesc &M : h->mats) P.ntmax = std::max(P.ntmax, M.nt);
+    P.cols.resize(P.ntmax);
+    auto T = [&](const MatDesc &M, int i, int j) { return W + (M.tile0 + tidx(i, j)) * bb; };
+    const int nmat = (int)h->mats.size();
+    for (int mi = 0; mi < nmat; ++mi) {
+        const MatDesc &M = h->mats[mi];
+        P.lentries.push_back({W + M.tile0 * bb, M.n, M.nt});
+    }
+    for (int k = 0; k < P.ntmax; ++k) {
         ColPlan &C = P.cols[k];
-        // 1. updates of column k (FP64 output tiles here; low-precision ones elsewhere)
+        // 1. updates of column k (FP64 output tiles here; low-precision ones in build_mxp)
         C.it0 = (int)P.items.size();
         C.red0 = (int)P.reds.size();
         if (k > 0) {
             const int K = k * b;
             std::vector<int> jobs_here;
             int base = 0;
-            for (int m = k; m < nt; ++m) {
-                const bool fp64 = (m == k) || !mixed || map[(size_t)m * nt + k] == TC_FP64;
-                if (!fp64) continue;
-                jobs_here.push_back((int)P.jobs.size());
-                P.jobs.push_back({T(m, k), T(m, 0), T(k, 0), K, b, b, m == k ? 1 : 0});
-                base += (m == k) ? (b / 64) * (b / 64 + 1) / 2 : (b / 64) * (b / 64);
-                P.update_flops[TC_FP64] += (m == k ? 1.0 : 2.0) * (double)b * b * K;
+            for (int mi = 0; mi < nmat; ++mi) {
+                const MatDesc &M = h->mats[mi];
+                if (M.nt <= k) continue;
+                for (int m = k; m < M.nt; ++m) {
+                    const bool fp64 = (m == k) || !M.mixed || M.map[(size_t)m * M.nt + k] == TC_FP64;
+                    if (!fp64) continue;
+                    jobs_here.push_back((int)P.jobs.size());
+                    P.jobs.push_back({T(M, m, k), T(M, m, 0), T(M, k, 0), K, b, b, m == k ? 1 : 0, status + 2 + mi});
+                    base += (m == k) ? (b / 64) * (b / 64 + 1) / 2 : (b / 64) * (b / 64);
+                    P.update_flops[TC_FP64] += (m == k ? 1.0 : 2.0) * (double)b * b * K;
+                }
             }
             int splits = 1;
-            if (base > 0 && base < kTargetItems) splits = std::min((kTargetItems + base - 1) / base, std::max(1, K / 256));
+            if (base > 0 && base < kTargetItems)
+                splits = std::min((kTargetItems + base - 1) / base, std::max(1, K / 256));
             int part_next = 0;
             for (int jj : jobs_here) emit_job_items(P, jj, b, splits, part_next);
             P.max_parts = std::max(P.max_parts, part_next);
         }
         C.nit = (int)P.items.size() - C.it0;
         C.nred = (int)P.reds.size() - C.red0;
-        // 2. POTRF trailing updates of the diagonal tile, panel by panel
-        double *D = T(k, k);
-        for (int jb = 0; jb + 1 < b / 64; ++jb) {
-            const int M = b - (jb + 1) * 64;
-            const int job = (int)P.jobs.size();
-            const double *Pn = D + (int64_t)jb * 64 * b + (jb + 1) * 64;
-            P.jobs.push_back({D + (int64_t)(jb + 1) * 64 * b + (jb + 1) * 64, Pn, Pn, 64, M, M, 1});
-            const int i0 = (int)P.items.size();
-            int dummy = 0;
-            emit_job_items(P, job, b, 1, dummy);
-            C.potrf_items.push_back({i0, (int)P.items.size() - i0});
+        // 2. blocked POTRF of the diagonal tiles: per 64-panel, the block, its panel and the
+        //    trailing update, each one launch over all matrices
+        for (int jb = 0; jb < b / 64; ++jb) {
+            PotrfStep ps;
+            ps.rows = b - (jb + 1) * 64;
+            ps.pe0 = (int)P.pentries.size();
+            for (int mi = 0; mi < nmat; ++mi) {
+                const MatDesc &M = h->mats[mi];
+                if (M.nt <= k) continue;
+                double *D = T(M, k, k);
+                P.pentries.push_back({D + (int64_t)jb * 64 * b + jb * 64, status + 2 + mi, k * b + jb * 64, ps.rows});
+            }
+            ps.npe = (int)P.pentries.size() - ps.pe0;
+            ps.it0 = (int)P.items.size();
+            if (ps.rows > 0)
+                for (int mi = 0; mi < nmat; ++mi) {
+                    const MatDesc &M = h->mats[mi];
+                    if (M.nt <= k) continue;
+                    double *D = T(M, k, k);
+                    const double *Pn = D + (int64_t)jb * 64 * b + (jb + 1) * 64;
+                    const int job = (int)P.jobs.size();
+                    P.jobs.push_back({D + (int64_t)(jb + 1) * 64 * b + (jb + 1) * 64, Pn, Pn, 64, ps.rows, ps.rows, 1,
+                                      status + 2 + mi});
+                    int dummy = 0;
+                    emit_job_items(P, job, b, 1, dummy);
+                }
+            ps.nit = (int)P.items.size() - ps.it0;
+            C.potrf.push_back(ps);
         }
-        P.potrf_flops += (double)b * b * b / 3.0;
         // 3. TRSM strips of the tiles below the diagonal
         C.st0 = (int)P.strips.size();
-        for (int m = k + 1; m < nt; ++m)
-            for (int r0 = 0; r0 < b; r0 += 64) P.strips.push_back({T(m, k), D, r0});
+        for (int mi = 0; mi < nmat; ++mi) {
+            const MatDesc &M = h->mats[mi];
+            if (M.nt <= k) continue;
+            P.potrf_flops += (double)b * b * b / 3.0;
+            for (int m = k + 1; m < M.nt; ++m) {
+                for (int r0 = 0; r0 < b; r0 += 64) P.strips.push_back({T(M, m, k), T(M, k, k), status + 2 + mi, r0});
+                P.trsm_flops += (double)b * b * b;
+            }
+        }
         C.nst = (int)P.strips.size() - C.st0;
-        P.trsm_flops += (double)(nt - 1 - k) * b * b * b;
     }
     return P;
 }
 
 size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
 
-
 // ----------------------------------------------------------- mixed-precision schedule
 // Which low-precision operand copies each final tile needs (Section IV-C: an update runs
 // in the precision of the tile it writes, so tile (i, j) is needed in p(i, k') for every
 // output (i, k'), j < k' < i, that reads it as X, and in p(m, i) for every output (m, i),
-// m > i, that reads it as Y), the pool slot of each copy, and per column the tensor-core
-// work items, the tiles to store in their precision and the copies to make.
+// m > i, that reads it as Y), the pool slot of each copy, and per column step the
+// tensor-core work items, the tiles to store in their precision and the copies to make.
+// Tile indices are global: matrix tile0 + packed index.
 struct MxpPlan {
-    std::vector<int> slot[3];          // [q-1][packed tile] -> slot, -1 if not needed
+    std::vector<int> slot[3];          // [q-1][global tile] -> slot, -1 if not needed
     int64_t nslots[3] = {0, 0, 0};
-    std::vector<uint8_t> prec;         // precision of every packed tile (diagonal FP64)
-    std::vector<int> tiles;            // per column: off-diagonal tiles to store / copy
+    std::vector<uint8_t> prec;         // precision of every tile (diagonal FP64)
+    std::vector<int> tiles;            // per column step: off-diagonal tiles to store / copy
     std::vector<CopyJob> copies;
     std::vector<QItem> qitems;
     struct Col { int t0, nt, c0, nc, q0[3], nq[3]; };
     std::vector<Col> cols;
+    int64_t T = 0;
     double flops[4] = {0, 0, 0, 0};
 };
 
-MxpPlan build_mxp(int nt, int b, const std::vector<uint8_t> &map) {
-    MxpPlan M;
-    const int64_t T = tidx(nt, 0);
-    auto P = [&](int i, int j) { return (int)map[(size_t)i * nt + j]; };
-    for (int q = 0; q < 3; ++q) M.slot[q].assign(T, -1);
-    M.prec.assign(T, 0);
-    for (int i = 0; i < nt; ++i)
-        for (int j = 0; j < i; ++j) {
-            M.prec[tidx(i, j)] = (uint8_t)P(i, j);
-            unsigned mask = 0;
-            for (int kk = j + 1; kk < i; ++kk) mask |= 1u << P(i, kk);
-            for (int m = i + 1; m < nt; ++m) mask |= 1u << P(m, i);
-            for (int q = 1; q <= 3; ++q)
-                if (mask & (1u << q)) M.slot[q - 1][tidx(i, j)] = (int)M.nslots[q - 1]++;
-        }
-    M.cols.resize(nt);
-    const int nbk = b / 128;
-    for (int k = 0; k < nt; ++k) {
-        MxpPlan::Col &C = M.cols[k];
-        for (int q = 1; q <= 3; ++q) {
-            C.q0[q - 1] = (int)M.qitems.size();
-            if (k > 0)
-                for (int m = k + 1; m < nt; ++m) {
-                    if (P(m, k) != q) continue;
-                    for (int bn = 0; bn < nbk; ++bn)
-                        for (int bm = 0; bm < nbk; ++bm) M.qitems.push_back({m, (uint16_t)bm, (uint16_t)bn});
-                    M.flops[q] += 2.0 * b * (double)b * k * b;
-                }
-            C.nq[q - 1] = (int)M.qitems.size() - C.q0[q - 1];
-        }
-        C.t0 = (int)M.tiles.size();
-        C.c0 = (int)M.copies.size();
-        for (int m = k + 1; m < nt; ++m) {
-            const int t = (int)tidx(m, k);
-            M.tiles.push_back(t);
-            for (int q = 1; q <= 3; ++q)
-                if (M.slot[q - 1][t] >= 0) M.copies.push_back({t, q, M.slot[q - 1][t]});
-        }
-        C.nt = (int)M.tiles.size() - C.t0;
-        C.nc = (int)M.copies.size() - C.c0;
+MxpPlan build_mxp(tc_handle h, double *W) {
+    MxpPlan X;
+    const int b = h->b;
+    const int64_t bb = (int64_t)b * b;
+    int ntmax = 0;
+    for (const MatDesc &M : h->mats) {
+        X.T = std::max<int64_t>(X.T, M.tile0 + tidx(M.nt, 0));
+        ntmax = std::max(ntmax, M.nt);
     }
-    return M;
+    for (int q = 0; q < 3; ++q) X.slot[q].assign(X.T, -1);
+    X.prec.assign(X.T, 0);
+    for (const MatDesc &M : h->mats) {
+        if (!M.mixed) continue;
+        const int nt = M.nt;
+        auto P = [&](int i, int j) { return (int)M.map[(size_t)i * nt + j]; };
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j < i; ++j) {
+                const int64_t g = M.tile0 + tidx(i, j);
+                X.prec[g] = (uint8_t)P(i, j);
+                unsigned mask = 0;
+                for (int kk = j + 1; kk < i; ++kk) mask |= 1u << P(i, kk);
+                for (int m = i + 1; m < nt; ++m) mask |= 1u << P(m, i);
+                for (int q = 1; q <= 3; ++q)
+                    if (mask & (1u << q)) X.slot[q - 1][g] = (int)X.nslots[q - 1]++;
+            }
+    }
+    X.cols.resize(ntmax);
+    const int nbk = b / 128;
+    for (int k = 0; k < ntmax; ++k) {
+        MxpPlan::Col &C = X.cols[k];
+        for (int q = 1; q <= 3; ++q) {
+            C.q0[q - 1] = (int)X.qitems.size();
+            if (k > 0)
+                for (const MatDesc &M : h->mats) {
+                    if (!M.mixed || M.nt <= k) continue;
+                    for (int m = k + 1; m < M.nt; ++m) {
+                        if ((int)M.map[(size_t)m * M.nt + k] != q) continue;
+                        double *Cp = W + (M.tile0 + tidx(m, k)) * bb;
+                        const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
+                        for (int bn = 0; bn < nbk; ++bn)
+                            for (int bm = 0; bm < nbk; ++bm) X.qitems.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn});
+                        X.flops[q] += 2.0 * b * (double)b * k * b;
+                    }
+                }
+            C.nq[q - 1] = (int)X.qitems.size() - C.q0[q - 1];
+        }
+        C.t0 = (int)X.tiles.size();
+        C.c0 = (int)X.copies.size();
+        for (const MatDesc &M : h->mats) {
+            if (!M.mixed || M.nt <= k) continue;
+            for (int m = k + 1; m < M.nt; ++m) {
+                const int g = (int)(M.tile0 + tidx(m, k));
+                X.tiles.push_back(g);
+                for (int q = 1; q <= 3; ++q)
+                    if (X.slot[q - 1][g] >= 0) X.copies.push_back({g, q, X.slot[q - 1][g]});
+            }
+        }
+        C.nt = (int)X.tiles.size() - C.t0;
+        C.nc = (int)X.copies.size() - C.c0;
+    }
+    return X;
 }
 
 struct MxpDev {
@@ -195,7 +260,7 @@ struct MxpDev {
 
 int setup_mxp(tc_handle h, const MxpPlan &M, MxpDev &D) {
     const int b = h->b;
-    const int64_t T = tidx(h->nt, 0);
+    const int64_t T = M.T;
     const size_t bb = (size_t)b * b;
     int rc;
     if (M.nslots[0]) {
@@ -218,7 +283,7 @@ int setup_mxp(tc_handle h, const MxpPlan &M, MxpDev &D) {
     if (!M.tiles.empty()) memcpy(host.data() + o_tiles, M.tiles.data(), M.tiles.size() * 4);
     if (!M.copies.empty()) memcpy(host.data() + o_cp, M.copies.data(), M.copies.size() * sizeof(CopyJob));
     if (!M.qitems.empty()) memcpy(host.data() + o_q, M.qitems.data(), M.qitems.size() * sizeof(QItem));
-    CK(cudaMemcpyAsync(h->mxtab.p, host.data(), total, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpy(h->mxtab.p, host.data(), total, cudaMemcpyHostToDevice));
     char *base = static_cast<char *>(h->mxtab.p);
     for (int q = 0; q < 3; ++q) D.slot[q] = reinterpret_cast<const int *>(base + o_slot + (size_t)q * T * 4);
     D.exps16 = reinterpret_cast<int *>(base + o_e16);
@@ -240,19 +305,17 @@ int setup_mxp(tc_handle h, const MxpPlan &M, MxpDev &D) {
     return TC_OK;
 }
 
-// Low-precision updates of column k (before its POTRF) and the stores / operand copies of
-// its final tiles (after its TRSMs).
-int mxp_updates(tc_handle h, const MxpPlan &M, const MxpDev &D, int k) {
+// Low-precision updates of column step k (before its POTRF).
+int mxp_updates(tc_handle h, const MxpPlan &M, const MxpDev &D, int k, bool spans) {
     const MxpPlan::Col &C = M.cols[k];
     int *err = static_cast<int *>(h->status.p) + 1;
-    double *W = static_cast<double *>(h->W.p);
     for (int q = 1; q <= 3; ++q) {
         if (!C.nq[q - 1]) continue;
         const CUtensorMap &a0 = q == 1 ? h->map_hi : q == 2 ? h->map16 : h->map8;
         const CUtensorMap &a1 = q == 1 ? h->map_lo : a0;
-        const int sp = span_begin(h, CAT_UPD64 + q);
-        launch_qgemm(q, a0, a1, a0, a1, W, D.qitems + C.q0[q - 1], C.nq[q - 1], D.slot[q - 1],
-                     q == 2 ? D.exps16 : q == 3 ? D.exps8 : nullptr, k, h->b, h->nt, err, h->s);
+        const int sp = spans ? span_begin(h, CAT_UPD64 + q) : -1;
+        launch_qgemm(q, a0, a1, a0, a1, D.qitems + C.q0[q - 1], C.nq[q - 1], D.slot[q - 1],
+                     q == 2 ? D.exps16 : q == 3 ? D.exps8 : nullptr, k, h->b, err, h->s);
         span_end(h, sp);
         CK_LAUNCH();
         ++h->upd_launches[q];
@@ -260,11 +323,12 @@ int mxp_updates(tc_handle h, const MxpPlan &M, const MxpDev &D, int k) {
     return TC_OK;
 }
 
-int mxp_convert(tc_handle h, const MxpPlan &M, const MxpDev &D, int k) {
+// Stores and operand copies of the final tiles of column step k (after its TRSMs).
+int mxp_convert(tc_handle h, const MxpPlan &M, const MxpDev &D, int k, bool spans) {
     const MxpPlan::Col &C = M.cols[k];
     if (!C.nt) return TC_OK;
     double *W = static_cast<double *>(h->W.p);
-    const int sp = span_begin(h, CAT_CONVERT);
+    const int sp = spans ? span_begin(h, CAT_CONVERT) : -1;
     launch_tile_amax(W, h->b, D.tiles + C.t0, C.nt, D.amaxL, h->s);
     CK_LAUNCH();
     launch_store_round(W, h->b, D.tiles + C.t0, C.nt, D.prec, D.amaxL, D.amaxS, h->s);
@@ -279,13 +343,25 @@ int mxp_convert(tc_handle h, const MxpPlan &M, const MxpDev &D, int k) {
     return TC_OK;
 }
 
-int run_factor(tc_handle h, const Plan &P, const MxpPlan *M) {
-    const int nt = h->nt, b = h->b;
-    // upload tables
+// Device copies of the plan's tables (uploaded before any launch so that the launch
+// sequence itself can be captured into a CUDA graph).
+struct PlanDev {
+    const DJob *jobs;
+    const DItem *items;
+    const DRed *reds;
+    const TStrip *strips;
+    const PEntry *pentries;
+    const LEntry *lentries;
+    MxpDev mx{};
+    bool mixed = false;
+};
+
+int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
     const size_t sj = P.jobs.size() * sizeof(DJob), si = P.items.size() * sizeof(DItem);
     const size_t sr = P.reds.size() * sizeof(DRed), ss = P.strips.size() * sizeof(TStrip);
+    const size_t sp = P.pentries.size() * sizeof(PEntry), sl = P.lentries.size() * sizeof(LEntry);
     const size_t oj = 0, oi = align_up(oj + sj), orr = align_up(oi + si), os = align_up(orr + sr);
-    const size_t total = align_up(os + ss);
+    const size_t op = align_up(os + ss), ol = align_up(op + sp), total = align_up(ol + sl);
     int rc = ensure(h, h->tables, total);
     if (rc) return rc;
     std::vector<char> host(total);
@@ -293,67 +369,186 @@ int run_factor(tc_handle h, const Plan &P, const MxpPlan *M) {
     if (si) memcpy(host.data() + oi, P.items.data(), si);
     if (sr) memcpy(host.data() + orr, P.reds.data(), sr);
     if (ss) memcpy(host.data() + os, P.strips.data(), ss);
-    CK(cudaMemcpyAsync(h->tables.p, host.data(), total, cudaMemcpyHostToDevice, h->s));
+    if (sp) memcpy(host.data() + op, P.pentries.data(), sp);
+    if (sl) memcpy(host.data() + ol, P.lentries.data(), sl);
+    CK(cudaMemcpy(h->tables.p, host.data(), total, cudaMemcpyHostToDevice));
     char *base = static_cast<char *>(h->tables.p);
-    const DJob *djobs = reinterpret_cast<const DJob *>(base + oj);
-    const DItem *ditems = reinterpret_cast<const DItem *>(base + oi);
-    const DRed *dreds = reinterpret_cast<const DRed *>(base + orr);
-    const TStrip *dstrips = reinterpret_cast<const TStrip *>(base + os);
-    rc = ensure(h, h->partials, (size_t)std::max(1, P.max_parts) * 4096 * sizeof(double));
-    if (rc) return rc;
-    double *parts = static_cast<double *>(h->partials.p);
+    D.jobs = reinterpret_cast<const DJob *>(base + oj);
+    D.items = reinterpret_cast<const DItem *>(base + oi);
+    D.reds = reinterpret_cast<const DRed *>(base + orr);
+    D.strips = reinterpret_cast<const TStrip *>(base + os);
+    D.pentries = reinterpret_cast<const PEntry *>(base + op);
+    D.lentries = reinterpret_cast<const LEntry *>(base + ol);
+    if ((rc = ensure(h, h->partials, (size_t)std::max(1, P.max_parts) * 4096 * sizeof(double)))) return rc;
+    D.mixed = M != nullptr;
+    if (M && (rc = setup_mxp(h, *M, D.mx))) return rc;
+    return TC_OK;
+}
+
+// The launch sequence of one factorization (capturable: device-side copies, memsets and
+// kernels only).  A_dev of every matrix is copied into W first.
+int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &D, bool spans) {
+    const int b = h->b;
+    const int64_t bb = (int64_t)b * b;
     int *status = static_cast<int *>(h->status.p);
     double *W = static_cast<double *>(h->W.p);
-    const int64_t bb = (int64_t)b * b;
-    MxpDev D{};
+    double *parts = static_cast<double *>(h->partials.p);
+    const int nmat = (int)h->mats.size();
+    for (const MatDesc &Md : h->mats)
+        CK(cudaMemcpyAsync(W + Md.tile0 * bb, Md.A_dev, (size_t)tidx(Md.nt, 0) * bb * sizeof(double),
+                           cudaMemcpyDeviceToDevice, h->s));
+    launch_fix_padding_batched(D.lentries, nmat, P.ntmax, b, h->s);
+    CK_LAUNCH();
+    CK(cudaMemsetAsync(status, 0, (2 + nmat) * sizeof(int), h->s));
     if (M) {
-        rc = setup_mxp(h, *M, D);
-        if (rc) return rc;
-        const int64_t T = tidx(nt, 0);
-        CK(cudaMemsetAsync(D.amaxL, 0, T * sizeof(double), h->s));
-        CK(cudaMemsetAsync(D.amaxS, 0, T * sizeof(double), h->s));
-        CK(cudaMemsetAsync(D.exps16, 0, T * sizeof(int), h->s));
-        CK(cudaMemsetAsync(D.exps8, 0, T * sizeof(int), h->s));
+        CK(cudaMemsetAsync(D.mx.amaxL, 0, M->T * sizeof(double), h->s));
+        CK(cudaMemsetAsync(D.mx.amaxS, 0, M->T * sizeof(double), h->s));
+        CK(cudaMemsetAsync(D.mx.exps16, 0, M->T * sizeof(int), h->s));
+        CK(cudaMemsetAsync(D.mx.exps8, 0, M->T * sizeof(int), h->s));
     }
-
-    for (int k = 0; k < nt; ++k) {
+    for (int k = 0; k < P.ntmax; ++k) {
         const ColPlan &C = P.cols[k];
         if (C.nit) {
-            const int sp = span_begin(h, CAT_UPD64);
-            launch_dgemm_update(djobs, ditems + C.it0, C.nit, b, parts, status, h->s);
+            const int sp = spans ? span_begin(h, CAT_UPD64) : -1;
+            launch_dgemm_update(D.jobs, D.items + C.it0, C.nit, b, parts, nullptr, h->s);
             span_end(h, sp);
             CK_LAUNCH();
             ++h->upd_launches[TC_FP64];
         }
         if (C.nred) {
-            launch_dgemm_reduce(dreds + C.red0, C.nred, b, parts, status, h->s);
+            launch_dgemm_reduce(D.reds + C.red0, C.nred, b, parts, nullptr, h->s);
             CK_LAUNCH();
         }
-        if (M && (rc = mxp_updates(h, *M, D, k))) return rc;
-        double *Dk = W + tidx(k, k) * bb;
-        const int sp_potrf = span_begin(h, CAT_POTRF);
-        for (int jb = 0; jb < b / 64; ++jb) {
-            launch_potrf_block(Dk + (int64_t)jb * 64 * b + jb * 64, b, k * b + jb * 64, status, h->s);
+        if (M) {
+            const int rc = mxp_updates(h, *M, D.mx, k, spans);
+            if (rc) return rc;
+        }
+        const int sp_potrf = spans ? span_begin(h, CAT_POTRF) : -1;
+        for (const PotrfStep &ps : C.potrf) {
+            launch_potrf_blocks(D.pentries + ps.pe0, ps.npe, b, h->s);
             CK_LAUNCH();
-            if (jb + 1 < b / 64) {
-                const int rows = b - (jb + 1) * 64;
-                launch_trsm_rows(Dk + (int64_t)jb * 64 * b + (jb + 1) * 64, Dk + (int64_t)jb * 64 * b + jb * 64, b,
-                                 rows, status, h->s);
+            if (ps.rows > 0) {
+                launch_trsm_rows_batched(D.pentries + ps.pe0, ps.npe, ps.rows, b, h->s);
                 CK_LAUNCH();
-                const auto &pi = C.potrf_items[jb];
-                launch_dgemm_update(djobs, ditems + pi.first, pi.second, b, parts, status, h->s);
+                launch_dgemm_update(D.jobs, D.items + ps.it0, ps.nit, b, parts, nullptr, h->s);
                 CK_LAUNCH();
             }
         }
         span_end(h, sp_potrf);
         if (C.nst) {
-            const int sp = span_begin(h, CAT_TRSM);
-            launch_trsm_strips(dstrips + C.st0, C.nst, b, b, status, h->s);
+            const int sp = spans ? span_begin(h, CAT_TRSM) : -1;
+            launch_trsm_strips(D.strips + C.st0, C.nst, b, b, nullptr, h->s);
             span_end(h, sp);
             CK_LAUNCH();
         }
-        if (M && (rc = mxp_convert(h, *M, D, k))) return rc;
+        if (M) {
+            const int rc = mxp_convert(h, *M, D.mx, k, spans);
+            if (rc) return rc;
+        }
     }
+    double *sc = static_cast<double *>(h->scratch.p);
+    launch_logdet_batched(D.lentries, nmat, b, sc, h->s);
+    CK_LAUNCH();
+    return TC_OK;
+}
+
+// Results of the last execute: info words and log-determinants of every matrix.
+int collect_results(tc_handle h, int *first_bad, int *err_word) {
+    const int nmat = (int)h->mats.size();
+    std::vector<int> st(2 + nmat);
+    h->logdets.assign(nmat, 0.0);
+    CK(cudaMemcpyAsync(st.data(), h->status.p, st.size() * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h->logdets.data(), h->scratch.p, nmat * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    h->infos.assign(st.begin() + 2, st.end());
+    *err_word = st[1];
+    *first_bad = 0;
+    for (int i = 0; i < nmat && !*first_bad; ++i) *first_bad = h->infos[i];
+    return TC_OK;
+}
+
+void fill_stats(tc_handle h, const Plan &P, const MxpPlan *M, tc_stats *stats, double t0, int64_t launches0,
+                int info) {
+    memset(stats, 0, sizeof *stats);
+    stats->t_ms = now_ms() - t0;
+    for (const MatDesc &Md : h->mats) {
+        stats->flops += (double)Md.n * Md.n * Md.n / 3.0;
+        for (int i = 0; i < Md.nt; ++i)
+            for (int j = 0; j <= i; ++j) stats->tiles[i == j ? 0 : Md.map[(size_t)i * Md.nt + j]]++;
+    }
+    stats->update_flops[0] = P.update_flops[0];
+    if (M)
+        for (int p = 1; p < 4; ++p) stats->update_flops[p] = M->flops[p];
+    stats->trsm_flops = P.trsm_flops;
+    stats->potrf_flops = P.potrf_flops;
+    stats->kernel_launches = h->launches - launches0;
+    stats->info = info;
+    double ms[CAT_N];
+    span_totals(h, ms);
+    for (int p = 0; p < 4; ++p) {
+        stats->t_update_ms[p] = ms[CAT_UPD64 + p];
+        stats->update_launches[p] = h->upd_launches[p];
+    }
+    stats->t_potrf_ms = ms[CAT_POTRF];
+    stats->t_trsm_ms = ms[CAT_TRSM];
+    stats->t_convert_ms = ms[CAT_CONVERT];
+}
+
+// Plan + prepare + execute the matrices in h->mats (W already sized).  With use_graph the
+// launch sequence is captured once into a CUDA graph and replayed while the batch repeats.
+int factor_matrices(tc_handle h, tc_stats *stats, bool use_graph, const std::vector<int64_t> *key) {
+    const double t0 = now_ms();
+    const int64_t launches0 = h->launches;
+    spans_reset(h);
+    for (int p = 0; p < 4; ++p) h->upd_launches[p] = 0;
+    bool mixed = false;
+    for (const MatDesc &Md : h->mats) mixed |= Md.mixed;
+    int *status = static_cast<int *>(h->status.p);
+    double *W = static_cast<double *>(h->W.p);
+    int rc = ensure(h, h->status, (2 + h->mats.size()) * sizeof(int));
+    if (rc) return rc;
+    status = static_cast<int *>(h->status.p);
+    if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, h->mats.size()) * sizeof(double)))) return rc;
+    Plan P = build_plan(h, W, status);
+    MxpPlan M;
+    if (mixed) M = build_mxp(h, W);
+    const MxpPlan *Mp = mixed ? &M : nullptr;
+    const bool replay = use_graph && h->graph && key && *key == h->graph_key;
+    if (!replay) {
+        PlanDev D;
+        if ((rc = prepare_factor(h, P, Mp, D))) return rc;
+        if (use_graph) {
+            if (h->graph) {
+                cudaGraphExecDestroy(h->graph);
+                h->graph = nullptr;
+                h->graph_key.clear();
+            }
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+            rc = execute_factor(h, P, Mp, D, false);
+            cudaError_t e = cudaStreamEndCapture(h->s, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture", __LINE__);
+            e = cudaGraphInstantiate(&h->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate", __LINE__);
+            h->graph_key = *key;
+        } else {
+            if ((rc = execute_factor(h, P, Mp, D, true))) return rc;
+        }
+    }
+    if (use_graph) CK(cudaGraphLaunch(h->graph, h->s));
+    int bad = 0, err = 0;
+    if ((rc = collect_results(h, &bad, &err))) return rc;
+    if (err) {
+        h->factored = false;
+        return set_err(h, TC_ERR_TIMEOUT, err == 2 ? "tensor-core update found no operand copy (internal)"
+                                                     : "a tensor-core update timed out waiting on its pipeline");
+    }
+    if (stats) fill_stats(h, P, Mp, stats, t0, launches0, bad);
     return TC_OK;
 }
 
@@ -415,6 +610,8 @@ void tc_destroy(tc_handle h) {
     for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq,
                       &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab, &h->logdiag})
         release(*d);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    release(h->bstage);
     if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
     if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
@@ -530,98 +727,50 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
     if (rc) return rc;
     if (!A_tiles) return set_err(h, TC_ERR_ARG, "A_tiles must not be NULL");
     CK(cudaSetDevice(h->device));
-    const double t0 = now_ms();
-    const int64_t launches0 = h->launches;
     h->factored = false;
     h->ooc = false;
-    h->normA_inf = -1.0;
     const int nt = (int)((n + b - 1) / b);
-    const int64_t T = (int64_t)nt * (nt + 1) / 2;
+    const int64_t T = tidx(nt, 0);
     const size_t bytes = (size_t)T * b * b * sizeof(double);
-    h->n = n;
-    h->b = b;
-    h->nt = nt;
-    // precision map (host copy)
-    h->map.assign((size_t)nt * nt, TC_FP64);
+    MatDesc M;
+    M.n = n;
+    M.nt = nt;
+    M.tile0 = 0;
+    M.map.assign((size_t)nt * nt, TC_FP64);
     if (map) {
-        if (on_device(map)) CK(cudaMemcpy(h->map.data(), map, h->map.size(), cudaMemcpyDeviceToHost));
-        else memcpy(h->map.data(), map, h->map.size());
+        if (on_device(map)) CK(cudaMemcpy(M.map.data(), map, M.map.size(), cudaMemcpyDeviceToHost));
+        else memcpy(M.map.data(), map, M.map.size());
         for (int i = 0; i < nt; ++i)
             for (int j = 0; j < nt; ++j) {
-                uint8_t &v = h->map[(size_t)i * nt + j];
+                uint8_t &v = M.map[(size_t)i * nt + j];
                 if (j >= i) v = TC_FP64;
                 if (v > TC_FP8) return set_err(h, TC_ERR_ARG, "precision map entries must be 0..3");
             }
     }
-    h->mixed = false;
-    for (uint8_t v : h->map) h->mixed |= (v != TC_FP64);
-    if (h->mixed && b % 128) return set_err(h, TC_ERR_UNSUPPORTED, "mixed precision needs a tile size that is a multiple of 128");
-    if (h->cfg.ooc == 1) return set_err(h, TC_ERR_UNSUPPORTED, "out-of-core mode is not available in this build");
-
-    rc = ensure(h, h->W, bytes);
-    if (rc) return rc;
+    for (uint8_t v : M.map) M.mixed |= (v != TC_FP64);
+    if (M.mixed && b % 128) return set_err(h, TC_ERR_UNSUPPORTED, "mixed precision needs a tile size that is a multiple of 128");
+    if ((rc = ensure(h, h->W, bytes))) return rc;
     // the caller's A stays readable for refinement: reference it on the device or copy it
     if (on_device(A_tiles)) {
-        h->A_dev = A_tiles;
+        M.A_dev = A_tiles;
     } else {
-        rc = ensure(h, h->Acopy, bytes);
-        if (rc) return rc;
+        if ((rc = ensure(h, h->Acopy, bytes))) return rc;
         CK(cudaMemcpyAsync(h->Acopy.p, A_tiles, bytes, cudaMemcpyHostToDevice, h->s));
-        h->A_dev = static_cast<const double *>(h->Acopy.p);
+        M.A_dev = static_cast<const double *>(h->Acopy.p);
     }
-    double *W = static_cast<double *>(h->W.p);
-    CK(cudaMemcpyAsync(W, h->A_dev, bytes, cudaMemcpyDeviceToDevice, h->s));
-    launch_fix_padding(W, nt, b, n, h->s);
-    CK_LAUNCH();
-    CK(cudaMemsetAsync(h->status.p, 0, 2 * sizeof(int), h->s));
-
-    spans_reset(h);
-    for (int p = 0; p < 4; ++p) h->upd_launches[p] = 0;
-    Plan P = build_plan(W, nt, b, h->map, h->mixed);
-    MxpPlan M;
-    if (h->mixed) {
-        M = build_mxp(nt, b, h->map);
-        for (int p = 1; p < 4; ++p) P.update_flops[p] = M.flops[p];
-    }
-    rc = run_factor(h, P, h->mixed ? &M : nullptr);
-    if (rc) return rc;
-    double *sc = static_cast<double *>(h->scratch.p);
-    launch_logdet(W, nt, b, n, sc, h->s);
-    CK_LAUNCH();
-    int st2[2] = {0, 0};
-    CK(cudaMemcpyAsync(st2, h->status.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
-    double ld = 0.0;
-    CK(cudaMemcpyAsync(&ld, sc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    const int info = st2[0];
-    if (st2[1]) {
-        h->factored = false;
-        return set_err(h, TC_ERR_TIMEOUT, st2[1] == 2 ? "tensor-core update found no operand copy (internal)"
-                                                        : "a tensor-core update timed out waiting on its pipeline");
-    }
-    h->logdet = ld;
+    h->mats.assign(1, M);
+    h->n = n;
+    h->b = b;
+    h->nt = nt;
+    h->map = M.map;
+    h->mixed = M.mixed;
+    h->A_dev = M.A_dev;
+    h->normA_inf = -1.0;
+    h->normA_infs.assign(1, -1.0);
+    if ((rc = factor_matrices(h, stats, false, nullptr))) return rc;
+    const int info = h->infos[0];
+    h->logdet = h->logdets[0];
     h->factored = (info == 0);
-    if (stats) {
-        memset(stats, 0, sizeof *stats);
-        stats->t_ms = now_ms() - t0;
-        stats->flops = (double)n * n * n / 3.0;
-        for (int p = 0; p < 4; ++p) stats->update_flops[p] = P.update_flops[p];
-        stats->trsm_flops = P.trsm_flops;
-        stats->potrf_flops = P.potrf_flops;
-        for (int i = 0; i < nt; ++i)
-            for (int j = 0; j <= i; ++j) stats->tiles[h->map[(size_t)i * nt + j]]++;
-        stats->kernel_launches = h->launches - launches0;
-        stats->info = info;
-        double ms[CAT_N];
-        span_totals(h, ms);
-        for (int p = 0; p < 4; ++p) {
-            stats->t_update_ms[p] = ms[CAT_UPD64 + p];
-            stats->update_launches[p] = h->upd_launches[p];
-        }
-        stats->t_potrf_ms = ms[CAT_POTRF];
-        stats->t_trsm_ms = ms[CAT_TRSM];
-        stats->t_convert_ms = ms[CAT_CONVERT];
-    }
     if (info) set_err(h, info, "matrix is not positive definite (see the returned column)");
     return info;
 }
@@ -633,12 +782,10 @@ int tile_chol_logdet(tc_handle h, double *logdet_out) {
     return TC_OK;
 }
 
-// Forward (and optionally back) substitution on the padded column-major buffer R
-// (leading dimension ldr = nt*b), nrhs <= 16 per pass.
-static int subst(tc_handle h, double *R, int64_t ldr, int nrhs, bool back) {
-    if (h->ooc) return ooc_subst(h, R, ldr, nrhs, back, nullptr);
-    const int nt = h->nt, b = h->b;
-    const double *W = static_cast<const double *>(h->W.p);
+// Forward (and optionally back) substitution with the factor tiles at W (nt tile rows) on
+// the padded column-major buffer R (leading dimension ldr = nt*b), nrhs <= 16 per pass.
+static int subst_w(tc_handle h, const double *W, int nt, double *R, int64_t ldr, int nrhs, bool back) {
+    const int b = h->b;
     const int64_t bb = (int64_t)b * b;
     for (int c0 = 0; c0 < nrhs; c0 += 16) {
         const int nc = std::min(16, nrhs - c0);
@@ -658,6 +805,11 @@ static int subst(tc_handle h, double *R, int64_t ldr, int nrhs, bool back) {
         }
     }
     return TC_OK;
+}
+
+static int subst(tc_handle h, double *R, int64_t ldr, int nrhs, bool back) {
+    if (h->ooc) return ooc_subst(h, R, ldr, nrhs, back, nullptr);
+    return subst_w(h, static_cast<const double *>(h->W.p), h->nt, R, ldr, nrhs, back);
 }
 
 int tile_chol_solve(tc_handle h, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int max_refine,
@@ -800,6 +952,249 @@ int tile_chol_get_factor(tc_handle h, double *L_tiles) {
     if (!dev) CK(cudaMemcpyAsync(L_tiles, dst, bytes, cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
     release(tmp);
+    return TC_OK;
+}
+
+// ----------------------------------------------------------------------- batched
+int tile_chol_factor_batched(tc_handle h, int count, const int64_t *n, int b, const double *const *A_tiles,
+                             const uint8_t *const *maps, int *info_out, double *logdet_out, tc_stats *stats) {
+    if (!h) return TC_ERR_ARG;
+    if (count < 1 || !n || !A_tiles) return set_err(h, TC_ERR_ARG, "count >= 1, n and A_tiles are required");
+    for (int i = 0; i < count; ++i) {
+        int rc = check_nb(h, n[i], b);
+        if (rc) return rc;
+        if (!A_tiles[i]) return set_err(h, TC_ERR_ARG, "A_tiles entries must not be NULL");
+    }
+    CK(cudaSetDevice(h->device));
+    h->factored = false;
+    h->ooc = false;
+    const int64_t bb = (int64_t)b * b;
+    std::vector<MatDesc> mats(count);
+    int64_t T = 0, Thost = 0;
+    for (int i = 0; i < count; ++i) {
+        MatDesc &M = mats[i];
+        M.n = n[i];
+        M.nt = (int)((n[i] + b - 1) / b);
+        M.tile0 = T;
+        T += tidx(M.nt, 0);
+        M.map.assign((size_t)M.nt * M.nt, TC_FP64);
+        if (maps && maps[i]) {
+            if (on_device(maps[i])) CK(cudaMemcpy(M.map.data(), maps[i], M.map.size(), cudaMemcpyDeviceToHost));
+            else memcpy(M.map.data(), maps[i], M.map.size());
+            for (int r = 0; r < M.nt; ++r)
+                for (int c = 0; c < M.nt; ++c) {
+                    uint8_t &v = M.map[(size_t)r * M.nt + c];
+                    if (c >= r) v = TC_FP64;
+                    if (v > TC_FP8) return set_err(h, TC_ERR_ARG, "precision map entries must be 0..3");
+                }
+        }
+        for (uint8_t v : M.map) M.mixed |= (v != TC_FP64);
+        if (M.mixed && b % 128) return set_err(h, TC_ERR_UNSUPPORTED, "mixed precision needs a tile size that is a multiple of 128");
+        if (!on_device(A_tiles[i])) Thost += tidx(M.nt, 0);
+    }
+    int rc = ensure(h, h->W, (size_t)T * bb * sizeof(double));
+    if (rc) return rc;
+    // inputs in host memory are staged on the device (outside the captured graph)
+    if (Thost && (rc = ensure(h, h->bstage, (size_t)Thost * bb * sizeof(double)))) return rc;
+    int64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        const size_t bytes = (size_t)tidx(mats[i].nt, 0) * bb * sizeof(double);
+        if (on_device(A_tiles[i])) {
+            mats[i].A_dev = A_tiles[i];
+        } else {
+            double *dst = static_cast<double *>(h->bstage.p) + off * bb;
+            CK(cudaMemcpyAsync(dst, A_tiles[i], bytes, cudaMemcpyHostToDevice, h->s));
+            mats[i].A_dev = dst;
+            off += tidx(mats[i].nt, 0);
+        }
+    }
+    // graph key: everything the captured launch sequence depends on
+    std::vector<int64_t> key = {count, b, (int64_t)(uintptr_t)h->W.p, (int64_t)(uintptr_t)h->status.p};
+    uint64_t mh = 1469598103934665603ull;
+    for (int i = 0; i < count; ++i) {
+        key.push_back(n[i]);
+        key.push_back((int64_t)(uintptr_t)mats[i].A_dev);
+        for (uint8_t v : mats[i].map) mh = (mh ^ v) * 1099511628211ull;
+    }
+    key.push_back((int64_t)mh);
+    h->mats = std::move(mats);
+    h->b = b;
+    h->n = h->mats[0].n;
+    h->nt = h->mats[0].nt;
+    h->map = h->mats[0].map;
+    h->mixed = h->mats[0].mixed;
+    h->A_dev = h->mats[0].A_dev;
+    h->normA_inf = -1.0;
+    h->normA_infs.assign(count, -1.0);
+    if ((rc = factor_matrices(h, stats, true, &key))) return rc;
+    int first_bad = 0;
+    for (int i = 0; i < count; ++i) {
+        if (info_out) info_out[i] = h->infos[i];
+        if (logdet_out) logdet_out[i] = h->logdets[i];
+        if (!first_bad && h->infos[i]) first_bad = i + 1;
+    }
+    h->logdet = h->logdets[0];
+    h->factored = (first_bad == 0);
+    if (first_bad) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "matrix %d of the batch is not positive definite (see info_out)", first_bad - 1);
+        set_err(h, TC_ERR_ARG, buf);
+        return h->infos[first_bad - 1];
+    }
+    return TC_OK;
+}
+
+int tile_chol_solve_batched(tc_handle h, int nrhs, const double *const *B, double *const *X, int max_refine,
+                            double target_berr, double *berr_out, tc_stats *stats) {
+    if (!h) return TC_ERR_ARG;
+    if (!h->factored || h->ooc) return set_err(h, TC_ERR_STATE, "no successful in-core factorization");
+    if (nrhs < 1 || !B || !X || max_refine < 0) return set_err(h, TC_ERR_ARG, "bad batched solve arguments");
+    CK(cudaSetDevice(h->device));
+    const double t0 = now_ms();
+    const int64_t launches0 = h->launches;
+    const int count = (int)h->mats.size(), b = h->b;
+    const int64_t bb = (int64_t)b * b;
+    std::vector<int64_t> off(count + 1, 0);
+    int64_t ldmax = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t ldr = (int64_t)h->mats[i].nt * b;
+        off[i + 1] = off[i] + ldr * nrhs;
+        ldmax = std::max(ldmax, ldr);
+    }
+    int rc = ensure(h, h->vec, (size_t)(3 * off[count] + 2 * ldmax) * sizeof(double));
+    if (rc) return rc;
+    if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, (size_t)(3 * nrhs + 1) * count) * sizeof(double)))) return rc;
+    double *Bd = static_cast<double *>(h->vec.p), *Xd = Bd + off[count], *Rd = Xd + off[count];
+    double *ones = Rd + off[count], *rowsum = ones + ldmax;
+    double *sc = static_cast<double *>(h->scratch.p);
+    const double *W = static_cast<const double *>(h->W.p);
+    CK(cudaMemsetAsync(Bd, 0, off[count] * sizeof(double), h->s));
+    for (int i = 0; i < count; ++i) {
+        const MatDesc &M = h->mats[i];
+        const int64_t ldr = (int64_t)M.nt * b;
+        CK(cudaMemcpy2DAsync(Bd + off[i], ldr * sizeof(double), B[i], M.n * sizeof(double), M.n * sizeof(double),
+                             nrhs, cudaMemcpyDefault, h->s));
+    }
+    CK(cudaMemcpyAsync(Xd, Bd, off[count] * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    for (int i = 0; i < count; ++i) {
+        const MatDesc &M = h->mats[i];
+        if ((rc = subst_w(h, W + M.tile0 * bb, M.nt, Xd + off[i], (int64_t)M.nt * b, nrhs, true))) return rc;
+    }
+    // ||A_i||_inf once per factorization
+    if (max_refine > 0 && h->normA_infs[0] < 0) {
+        std::vector<double> o((size_t)ldmax, 1.0);
+        CK(cudaMemcpy(ones, o.data(), ldmax * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemsetAsync(sc, 0, count * sizeof(double), h->s));
+        for (int i = 0; i < count; ++i) {
+            const MatDesc &M = h->mats[i];
+            launch_symv_resid(M.A_dev, M.nt, b, M.n, ones, ldmax, nullptr, 0, rowsum, ldmax, 1, 1, h->s);
+            CK_LAUNCH();
+            launch_colmax_abs(rowsum, ldmax, M.n, 1, sc + i, h->s);
+            CK_LAUNCH();
+        }
+        CK(cudaMemcpyAsync(h->normA_infs.data(), sc, count * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+    }
+    std::vector<char> active(count, 1);
+    std::vector<double> berr(count, -1.0);
+    int it = 0;
+    for (; max_refine > 0; ++it) {
+        CK(cudaMemsetAsync(sc, 0, (size_t)3 * nrhs * count * sizeof(double), h->s));
+        for (int i = 0; i < count; ++i) {
+            if (!active[i]) continue;
+            const MatDesc &M = h->mats[i];
+            const int64_t ldr = (int64_t)M.nt * b;
+            for (int c0 = 0; c0 < nrhs; c0 += 16) {
+                const int nc = std::min(16, nrhs - c0);
+                launch_symv_resid(M.A_dev, M.nt, b, M.n, Xd + off[i] + c0 * ldr, ldr, Bd + off[i] + c0 * ldr, ldr,
+                                  Rd + off[i] + c0 * ldr, ldr, nc, 0, h->s);
+                CK_LAUNCH();
+            }
+            double *m3 = sc + (size_t)3 * nrhs * i;
+            launch_colmax_abs(Rd + off[i], ldr, M.n, nrhs, m3, h->s);
+            CK_LAUNCH();
+            launch_colmax_abs(Xd + off[i], ldr, M.n, nrhs, m3 + nrhs, h->s);
+            CK_LAUNCH();
+            launch_colmax_abs(Bd + off[i], ldr, M.n, nrhs, m3 + 2 * nrhs, h->s);
+            CK_LAUNCH();
+        }
+        std::vector<double> mx((size_t)3 * nrhs * count);
+        CK(cudaMemcpyAsync(mx.data(), sc, mx.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        bool any = false;
+        for (int i = 0; i < count; ++i) {
+            if (!active[i]) continue;
+            const double *m3 = mx.data() + (size_t)3 * nrhs * i;
+            double e = 0.0;
+            for (int c = 0; c < nrhs; ++c) {
+                const double den = h->normA_infs[i] * m3[nrhs + c] + m3[2 * nrhs + c];
+                e = std::max(e, den > 0 ? m3[c] / den : 0.0);
+            }
+            berr[i] = e;
+            if (e <= target_berr || it >= max_refine) active[i] = 0;
+            else any = true;
+        }
+        if (!any) break;
+        for (int i = 0; i < count; ++i) {
+            if (!active[i]) continue;
+            const MatDesc &M = h->mats[i];
+            const int64_t ldr = (int64_t)M.nt * b;
+            if ((rc = subst_w(h, W + M.tile0 * bb, M.nt, Rd + off[i], ldr, nrhs, true))) return rc;
+            launch_axpy_cols(Xd + off[i], ldr, Rd + off[i], ldr, M.n, nrhs, h->s);
+            CK_LAUNCH();
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        const MatDesc &M = h->mats[i];
+        CK(cudaMemcpy2DAsync(X[i], M.n * sizeof(double), Xd + off[i], (int64_t)M.nt * b * sizeof(double),
+                             M.n * sizeof(double), nrhs, cudaMemcpyDefault, h->s));
+    }
+    CK(cudaStreamSynchronize(h->s));
+    double worst = 0.0;
+    for (int i = 0; i < count; ++i) {
+        if (berr_out) berr_out[i] = berr[i];
+        worst = std::max(worst, berr[i]);
+    }
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->t_ms = now_ms() - t0;
+        stats->refine_iters = it;
+        stats->berr = max_refine > 0 ? worst : -1.0;
+        stats->kernel_launches = h->launches - launches0;
+    }
+    return TC_OK;
+}
+
+int tile_chol_loglik_batched(tc_handle h, const double *const *y, double *loglik_out) {
+    if (!h || !loglik_out) return TC_ERR_ARG;
+    if (!h->factored || h->ooc) return set_err(h, TC_ERR_STATE, "no successful in-core factorization");
+    CK(cudaSetDevice(h->device));
+    const int count = (int)h->mats.size(), b = h->b;
+    const int64_t bb = (int64_t)b * b;
+    std::vector<int64_t> off(count + 1, 0);
+    for (int i = 0; i < count; ++i) off[i + 1] = off[i] + (int64_t)h->mats[i].nt * b;
+    int rc = ensure(h, h->vec, (size_t)off[count] * sizeof(double));
+    if (rc) return rc;
+    if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, (size_t)count) * sizeof(double)))) return rc;
+    double *z = static_cast<double *>(h->vec.p), *sc = static_cast<double *>(h->scratch.p);
+    const double *W = static_cast<const double *>(h->W.p);
+    std::vector<double> quad(count, 0.0);
+    if (y) {
+        CK(cudaMemsetAsync(z, 0, off[count] * sizeof(double), h->s));
+        for (int i = 0; i < count; ++i) {
+            const MatDesc &M = h->mats[i];
+            if (!y[i]) return set_err(h, TC_ERR_ARG, "y entries must not be NULL");
+            CK(cudaMemcpyAsync(z + off[i], y[i], M.n * sizeof(double), cudaMemcpyDefault, h->s));
+            if ((rc = subst_w(h, W + M.tile0 * bb, M.nt, z + off[i], (int64_t)M.nt * b, 1, false))) return rc;
+            launch_dot_self(z + off[i], M.n, sc + i, h->s);
+            CK_LAUNCH();
+        }
+        CK(cudaMemcpyAsync(quad.data(), sc, count * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+    }
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int i = 0; i < count; ++i)
+        loglik_out[i] = -0.5 * (double)h->mats[i].n * std::log(two_pi) - 0.5 * h->logdets[i] - 0.5 * quad[i];
     return TC_OK;
 }
 

@@ -14,6 +14,16 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// One matrix of the current factorization (a single factor is a batch of one).
+struct MatDesc {
+    int64_t n = 0;
+    int nt = 0;
+    int64_t tile0 = 0;              // packed index of its tile (0, 0) in the concatenated W
+    const double *A_dev = nullptr;  // the caller's matrix on the device (refinement)
+    std::vector<uint8_t> map;       // nt x nt precision map (diagonal FP64)
+    bool mixed = false;
+};
+
 struct tc_handle_s {
     tc_config cfg{};
     int device = 0;
@@ -43,6 +53,15 @@ struct tc_handle_s {
     DevBuf pool_hi, pool_lo, pool16, pool8;
     DevBuf mxtab;
     CUtensorMap map_hi{}, map_lo{}, map16{}, map8{};
+    // matrices of the last (batched) factorization
+    std::vector<MatDesc> mats;
+    std::vector<double> logdets;
+    std::vector<int> infos;
+    std::vector<double> normA_infs;
+    // CUDA graph of the last batched factorization (replayed when the batch repeats)
+    cudaGraphExec_t graph = nullptr;
+    std::vector<int64_t> graph_key;
+    DevBuf bstage;     // device copies of host-resident batch inputs
     // out-of-core: the factor lives in the caller's host matrix
     bool ooc = false;
     double *host_factor = nullptr;

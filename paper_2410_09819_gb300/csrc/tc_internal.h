@@ -20,6 +20,7 @@ struct DJob {
     const double *X;
     const double *Y;
     int K, M, N, lower;
+    const int *status;   // info word of the matrix (skip when non-zero), or nullptr
 };
 
 // One CTA of the FP64 update: 64 x 64 output block (bi, bj) of job `job`, contraction
@@ -43,12 +44,29 @@ struct DRed {
 struct TStrip {
     double *C;          // tile (m, k) of the factor
     const double *L;    // L_kk
+    const int *status;  // info word of the matrix
     int r0;
+};
+
+// One diagonal tile's blocked POTRF step (batched over matrices): the 64-block at D,
+// its panel below (rows) and the matrix's info word; col0 = global column of the block.
+struct PEntry {
+    double *D;
+    int *status;
+    int col0, rows;
+};
+
+// A matrix of a batch for the batched log-determinant / padding kernels.
+struct LEntry {
+    double *W;          // first tile of this matrix in the concatenated tile array
+    int64_t n;
+    int nt;
 };
 
 // Tensor-core update of one 128 x 256 block (bm, bn) of output tile (m, k) (k_mxp.cu).
 struct QItem {
-    int m;
+    double *C;          // output tile (m, k)
+    int xoff, yoff;     // global packed index of tiles (m, 0) and (k, 0): sources are +n
     uint16_t bm, bn;
 };
 
@@ -67,10 +85,14 @@ void launch_dgemm_reduce(const DRed *reds, int nreds, int ld, const double *part
                          const int *status, cudaStream_t s);
 void launch_potrf_block(double *D, int ld, int col0, int *status, cudaStream_t s);
 void launch_trsm_rows(double *P, const double *L, int ld, int rows, const int *status, cudaStream_t s);
+void launch_potrf_blocks(const PEntry *e, int n, int ld, cudaStream_t s);
+void launch_trsm_rows_batched(const PEntry *e, int n, int max_rows, int ld, cudaStream_t s);
 void launch_trsm_strips(const TStrip *strips, int nstrips, int ld, int b, const int *status, cudaStream_t s);
 void launch_logdet(const double *W, int nt, int b, int64_t n, double *out, cudaStream_t s);
 void launch_fix_padding(double *W, int nt, int b, int64_t n, cudaStream_t s);
 void launch_zero_upper_diag(double *W, int nt, int b, int64_t n, cudaStream_t s);
+void launch_logdet_batched(const LEntry *e, int count, int b, double *out, cudaStream_t s);
+void launch_fix_padding_batched(const LEntry *e, int count, int ntmax, int b, cudaStream_t s);
 
 // tile-pointer variants (out-of-core executor)
 void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s);
@@ -101,8 +123,8 @@ void launch_tile_sumsq(const double *A, int nt, int b, int64_t n, double *out, c
 int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows);
 size_t qgemm_smem_bytes();
 void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
-                  const CUtensorMap &b1, double *W, const QItem *items, int nitems, const int *slot, const int *exps,
-                  int k, int b, int nt, int *err, cudaStream_t s);
+                  const CUtensorMap &b1, const QItem *items, int nitems, const int *slot, const int *exps,
+                  int k, int b, int *err, cudaStream_t s);
 void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, double *amax, cudaStream_t s);
 void launch_store_round(double *W, int b, const int *tiles, int ntiles, const uint8_t *prec, const double *amaxL,
                         double *amaxS, cudaStream_t s);

@@ -16,7 +16,8 @@ __all__ = [
     "TC_FP64", "TC_FP32", "TC_FP16", "TC_FP8", "TC_OK", "TileCholError", "tc_config", "tc_stats",
     "lib", "tc_config_default", "tc_create", "tc_destroy", "tc_last_error", "tc_matern_tiles",
     "tile_chol_precision_map", "tile_chol_factor", "tile_chol_factor_ooc", "tile_chol_solve", "tile_chol_logdet",
-    "tile_chol_loglik", "tile_chol_get_factor", "tile_chol_precision_map_noalloc", "Handle", "ntiles",
+    "tile_chol_loglik", "tile_chol_get_factor", "tile_chol_precision_map_noalloc", "tile_chol_factor_batched",
+    "tile_chol_solve_batched", "tile_chol_loglik_batched", "Handle", "ntiles",
     "tile_count",
 ]
 
@@ -86,6 +87,9 @@ def lib() -> ctypes.CDLL:
         "tile_chol_loglik": (ci, [H, vp, ctypes.POINTER(cd)]),
         "tile_chol_get_factor": (ci, [H, vp]),
         "tile_chol_precision_map_noalloc": (ci, [i64, ci, vp, cd, ci, ci, vp, vp]),
+        "tile_chol_factor_batched": (ci, [H, ci, vp, ci, vp, vp, vp, vp, ctypes.POINTER(tc_stats)]),
+        "tile_chol_solve_batched": (ci, [H, ci, vp, vp, ci, cd, vp, ctypes.POINTER(tc_stats)]),
+        "tile_chol_loglik_batched": (ci, [H, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -192,6 +196,49 @@ def tile_chol_loglik(h, y=None) -> float:
 
 def tile_chol_get_factor(h, L_tiles) -> None:
     _check(h, lib().tile_chol_get_factor(h, _ptr(L_tiles)))
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))(*[_ptr(x) for x in items])
+    return arr
+
+
+def tile_chol_factor_batched(h, ns, b, A_list, maps=None, stats: tc_stats | None = None):
+    """Factor every A_list[i] (order ns[i], tile b).  Returns (rc, info list, logdet list)."""
+    count = len(ns)
+    n_arr = (ctypes.c_int64 * count)(*ns)
+    a_arr = _ptr_array(A_list)
+    m_arr = _ptr_array(maps) if maps is not None else None
+    info = (ctypes.c_int * count)()
+    ld = (ctypes.c_double * count)()
+    rc = lib().tile_chol_factor_batched(h, count, ctypes.cast(n_arr, ctypes.c_void_p), b,
+                                        ctypes.cast(a_arr, ctypes.c_void_p),
+                                        ctypes.cast(m_arr, ctypes.c_void_p) if m_arr is not None else None,
+                                        ctypes.cast(info, ctypes.c_void_p), ctypes.cast(ld, ctypes.c_void_p),
+                                        ctypes.byref(stats) if stats is not None else None)
+    _check(h, rc, allow_positive=True)
+    return rc, list(info), list(ld)
+
+
+def tile_chol_solve_batched(h, nrhs, B_list, X_list, max_refine=0, target_berr=0.0,
+                            stats: tc_stats | None = None):
+    """Returns the per-matrix backward errors."""
+    count = len(B_list)
+    berr = (ctypes.c_double * count)()
+    _check(h, lib().tile_chol_solve_batched(h, nrhs, ctypes.cast(_ptr_array(B_list), ctypes.c_void_p),
+                                            ctypes.cast(_ptr_array(X_list), ctypes.c_void_p), max_refine,
+                                            target_berr, ctypes.cast(berr, ctypes.c_void_p),
+                                            ctypes.byref(stats) if stats is not None else None))
+    return list(berr)
+
+
+def tile_chol_loglik_batched(h, y_list, count=None):
+    count = len(y_list) if y_list is not None else count
+    out = (ctypes.c_double * count)()
+    _check(h, lib().tile_chol_loglik_batched(
+        h, ctypes.cast(_ptr_array(y_list), ctypes.c_void_p) if y_list is not None else None,
+        ctypes.cast(out, ctypes.c_void_p)))
+    return list(out)
 
 
 def tile_chol_precision_map_noalloc(n, b, A_tiles, eps_high, band, prec_set, map_out, stream=None) -> None:
