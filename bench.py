@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="fp64_n65536", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default="fp64_n65536", choices=sorted(inputs.WORKLOADS) + ["batched"])
+    ap.add_argument("--count", type=int, default=512, help="batched workload: number of matrices")
     ap.add_argument("--n", type=int, default=0, help="override n (smaller quick runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -298,6 +299,8 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     import oracle
+    if args.workload == "batched":
+        return run_reference_batched(args, ws)
     w = inputs.WORKLOADS[args.workload]
     n = args.n or w.n
     ns = min(args.cpu_sample, n)
@@ -321,6 +324,260 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def common_line(ws, args, value, t, metric_cfg, dtype):
+    return {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "impl": "ours",
+            "config": metric_cfg}
+
+
+def fp64_roofline(upd_flops, upd_ms, t):
+    pk, pk_kind = peaks()
+    fp64_peak = NSM * FP64_FLOPS_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = (upd_flops / (upd_ms / 1e3) / 1e12) if upd_ms > 0 else None
+    return {"kernel": "k_dgemm_update", "bound": "alu", "achieved": achieved, "peak": round(fp64_peak, 4),
+            "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+            "peak_source": f"ALU: 152 SMs x 4 FP64 flop/clk x {pk_kind} max SM clock",
+            "update_share_of_step": (upd_ms / 1e3) / t if t > 0 else None}
+
+
+def max_over_ranks(t, ws, dev):
+    if ws == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+# --------------------------------------------------------------------------- batched
+def run_batched(args, ws, rank, local):
+    """Many uneven SPD Matern matrices (n log-uniform in [64, 4096], range U[0.02, 0.2], nu in
+    {1/2, 3/2, 5/2}, nugget 1e-4): per-matrix precision maps (FP64 diagonal, FP16/FP8 off-diagonal
+    where the criterion at eps_high = 1e-7 allows, FP64 elsewhere), one graph-replayed batched
+    factorization, 16-RHS solves refined to backward error <= 1e-13, log-likelihoods."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_09819_gb300 import autotune
+    from paper_2410_09819_gb300 import tile_chol as tc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    H = tc.Handle(local, stream=stream.cuda_stream)
+    bw = inputs.batched_workload(args.count, 5 + 1000 * rank)
+    ns = bw.ns
+    pts = [torch.from_numpy(bw.points(i)).to(dev) for i in range(len(ns))]
+    eps, nrhs = 1e-7, bw.nrhs
+
+    def make_inputs(b):
+        A_list, maps = [], []
+        for i, n in enumerate(ns):
+            A = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=dev)
+            tc.tc_matern_tiles(H.h, n, b, pts[i], 1.0, bw.ranges[i], bw.nus[i], 1e-4, A)
+            A_list.append(A)
+            maps.append(torch.zeros(tc.ntiles(n, b) ** 2, dtype=torch.uint8, device=dev))
+        return A_list, maps
+
+    def compute_maps(A_list, maps, b):
+        for i, n in enumerate(ns):
+            tc.tile_chol_precision_map_noalloc(n, b, A_list[i], eps, 0, 4, maps[i], stream.cuda_stream)
+            maps[i][maps[i] == tc.TC_FP32] = tc.TC_FP64
+
+    best_b, tune = autotune.pick_batched_tile(H, ns, make_inputs)
+    b = best_b
+    A_list, maps = make_inputs(b)
+    B = [torch.from_numpy(np.ascontiguousarray(inputs.gaussian(n, nrhs, 77 + i).T)).to(dev) for i, n in enumerate(ns)]
+    X = [torch.empty_like(x) for x in B]
+    Y = [x[0].contiguous() for x in B]
+    flops = sum(n ** 3 / 3.0 for n in ns)
+
+    def step():
+        st, ss = tc.tc_stats(), tc.tc_stats()
+        compute_maps(A_list, maps, b)
+        rc, info, ld = tc.tile_chol_factor_batched(H.h, ns, b, A_list, maps, st)
+        if rc:
+            raise RuntimeError(f"batched factorization failed: {rc}")
+        berr = tc.tile_chol_solve_batched(H.h, nrhs, B, X, 10, 1e-13, ss)
+        ll = tc.tile_chol_loglik_batched(H.h, Y)
+        return st, ss, berr, ll
+
+    for _ in range(args.warmup):
+        step()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st, ss, berr, ll = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+    value = ws * flops * args.steps / t / 1e12
+    nlow = sum(int((m > 1).sum().item()) for m in maps)
+    if rank == 0:
+        line = common_line(ws, args, value, t, {
+            "workload": "batched", "count": len(ns), "n_range": [min(ns), max(ns)], "tile": b,
+            "tile_autotune_s": {str(k): v for k, v in tune.items()}, "nugget": 1e-4, "eps_high": eps,
+            "precision": "FP64 diagonal, FP16/FP8 off-diagonal where allowed, else FP64",
+            "nrhs": nrhs, "l2": "total inputs larger than L2", "parallelism": f"replicas x{ws}",
+            "step": "maps+graph-replayed batched factor+16-RHS refined solves+logliks"}, "f64+f16+e4m3")
+        line["roofline"] = None
+        line["e2e"] = None
+        line["cpu_baseline"] = None
+        line["clocks"] = clk
+        line["gpu_launches"] = None
+        line["detail"] = {"max_berr": max(berr), "refine_iters": ss.refine_iters, "low_precision_tiles": nlow,
+                          "t_factor_ms": st.t_ms, "t_solve_ms": ss.t_ms, "flops": flops}
+        print(json.dumps(line), flush=True)
+    H.close()
+
+
+def run_reference_batched(args, ws):
+    import oracle
+    bw = inputs.batched_workload(args.count, 5)
+    # bounded sample: the first matrices of the batch up to ~2e10 flops
+    idx, fl = [], 0.0
+    for i, n in enumerate(bw.ns):
+        if fl > 2e10:
+            break
+        idx.append(i)
+        fl += n ** 3 / 3.0
+    mats = [oracle.matern(bw.points(i), 1.0, bw.ranges[i], bw.nus[i], 1e-4) for i in idx]
+    for _ in range(args.warmup):
+        for A in mats:
+            oracle.cholesky(A)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for A in mats:
+            oracle.cholesky(A)
+    t = time.perf_counter() - t0
+    value = fl * args.steps / t / 1e12
+    sample = f"first {len(idx)} matrices of the batch ({fl:.2e} flops), oracle factorization each"
+    print(json.dumps({"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "impl": "reference", "config": {"workload": "batched", "count": args.count},
+                      "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.threads(),
+                                       "kind": "oracle", "sample": sample},
+                      "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+# ------------------------------------------------------------------------ out-of-core
+def measure_link(dev):
+    import torch
+    nb = 1 << 30
+    h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nb, dtype=torch.uint8, device=dev)
+    best = {}
+    for name, fn in (("h2d", lambda: d.copy_(h, non_blocking=True)), ("d2h", lambda: h.copy_(d, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        best[name] = nb / min(ts) / 1e9
+    del h, d
+    return best
+
+
+def run_ooc(args, ws, rank, local):
+    """Out-of-core FP64 factorization: the tiles live in pinned host memory, the device caches at
+    most OOC_CACHE_FRACTION of them.  Each step factors a fresh copy of A (restored, untimed,
+    before the step: the factorization overwrites A with L)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_09819_gb300 import tile_chol as tc
+
+    w = inputs.WORKLOADS[args.workload]
+    n = args.n or 65536
+    b = w.tile
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    T = tc.tile_count(n, b)
+    cap = int(inputs.OOC_CACHE_FRACTION * T * b * b * 8)
+    H = tc.Handle(local, stream=stream.cuda_stream, device_cap_bytes=cap)
+    link = measure_link(dev)
+    pts = inputs.uniform_points(n, w.seed + 1000 * rank, w.morton)
+    host0 = torch.empty(T * b * b, dtype=torch.float64, pin_memory=True)
+    # generate on the device tile-row by tile-row is not needed: n = 65536 fits; generate and move
+    A = torch.empty(T * b * b, dtype=torch.float64, device=dev)
+    tc.tc_matern_tiles(H.h, n, b, torch.from_numpy(pts).to(dev), w.sigma2, w.range_a, w.nu, w.nugget, A)
+    host0.copy_(A)
+    del A
+    torch.cuda.empty_cache()
+    work = torch.empty_like(host0).pin_memory()
+    y = torch.from_numpy(inputs.gaussian(n, 1, 9)[:, 0].copy()).pin_memory()
+    x = torch.empty_like(y).pin_memory()
+
+    def step(timed):
+        work.copy_(host0)                    # restore A (the factor overwrites it), untimed
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st, ss = tc.tc_stats(), tc.tc_stats()
+        e0.record(stream)
+        info = tc.tile_chol_factor_ooc(H.h, n, b, work, None, st)
+        if info:
+            raise RuntimeError(f"ooc factorization failed at column {info}")
+        tc.tile_chol_solve(H.h, 1, y, n, x, n, 0, 0.0, ss)
+        ll = tc.tile_chol_loglik(H.h, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, st, ss, ll
+
+    for _ in range(args.warmup):
+        step(False)
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t = 0.0
+    for _ in range(args.steps):
+        dt, st, ss, ll = step(True)
+        t += dt
+    clk = clocks.stop()
+    t = max_over_ranks(t, ws, dev)
+    flops = n ** 3 / 3.0
+    value = ws * flops * args.steps / t / 1e12
+    h2d, d2h = st.h2d_bytes, st.d2h_bytes
+    tf = st.t_ms / 1e3
+    if rank == 0:
+        line = common_line(ws, args, value, t, {
+            "workload": w.name + f"@n={n}", "n": n, "tile": b, "nu": w.nu, "range": w.range_a, "nugget": w.nugget,
+            "device_cache_bytes": cap, "matrix_bytes": T * b * b * 8, "host": "pinned",
+            "step": "ooc factor (A in host memory, overwritten by L)+streamed 1-RHS solve+loglik",
+            "l2": "inputs larger than L2", "parallelism": f"replicas x{ws}"}, "f64")
+        line["roofline"] = fp64_roofline(st.update_flops[0], st.t_update_ms[0], tf)
+        line["ooc_link"] = {"h2d_bytes": h2d, "d2h_bytes": d2h, "h2d_gbs": h2d / tf / 1e9, "d2h_gbs": d2h / tf / 1e9,
+                            "link_peak_gbs": link, "h2d_frac": (h2d / tf / 1e9) / link["h2d"],
+                            "cache_hits": st.cache_hits, "cache_misses": st.cache_misses,
+                            "evictions": st.evictions, "solve_h2d_note": "solve streams the factor again"}
+        line["e2e"] = {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "note": "the matrix is host-resident by construction: the device-timed step is end to end"}
+        line["cpu_baseline"] = None
+        line["clocks"] = clk
+        line["gpu_launches"] = st.kernel_launches + ss.kernel_launches
+        line["detail"] = {"t_factor_ms": st.t_ms, "t_update_ms": st.t_update_ms[0], "t_trsm_ms": st.t_trsm_ms,
+                          "t_potrf_ms": st.t_potrf_ms, "loglik": ll}
+        print(json.dumps(line), flush=True)
+    H.close()
+
+
 def main():
     args = parse_args()
     ws, rank, local = dist_info()
@@ -333,7 +590,12 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, ws, rank, local)
+        if args.workload == "batched":
+            run_batched(args, ws, rank, local)
+        elif args.workload.startswith("ooc"):
+            run_ooc(args, ws, rank, local)
+        else:
+            run_ours(args, ws, rank, local)
     finally:
         if ws > 1:
             import torch.distributed as dist

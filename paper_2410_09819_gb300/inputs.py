@@ -119,3 +119,9 @@ def batched_workload(count: int = 512, seed: int = 5, lo: int = 64, hi: int = 40
     seeds = [int(seed * 100003 + i) for i in range(count)]
     return BatchedWorkload(ns, ranges, nus, seeds)
 
+
+
+# Out-of-core workload actually run on a 199 GB host: n = 65536, tile 2048 (17.6 GB of tiles in
+# pinned host memory), device cache capped at 0.44 of it (the 120 GB / 275 GB ratio of the
+# n = 262144 configuration).
+OOC_CACHE_FRACTION = 120.0 / 275.0

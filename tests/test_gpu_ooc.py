@@ -114,3 +114,15 @@ def test_ooc_rejects_device_matrix_and_mixed_map():
         h = np.zeros(3 * 64 * 64)
         with pytest.raises(tc.TileCholError):
             tc.tile_chol_factor_ooc(H.h, 128, 64, h, np.array([0, 0, 2, 0], dtype=np.uint8))
+
+
+@pytest.mark.parametrize("n,b,cap", [(1536, 128, 12), (2048, 256, 9), (1000, 64, 40)])
+def test_ooc_counters_equal_the_schedule_simulator(n, b, cap):
+    from paper_2410_09819_gb300.ooc_sim import simulate
+    A = np.eye(n) * 3.0
+    H, info, host, st = ooc_factor(A, b, cap)
+    with H:
+        assert info == 0
+    r = simulate(n, b, cap)
+    assert (st.cache_hits, st.cache_misses, st.evictions) == (r.hits, r.misses, r.evictions)
+    assert (st.h2d_bytes, st.d2h_bytes) == (r.h2d_bytes, r.d2h_bytes)
