@@ -71,7 +71,12 @@ typedef struct {
     int prefetch_depth;         /* reserved: tile_chol_factor_ooc enqueues its whole static
                                    schedule, so copies run ahead as far as free slots allow */
     int lookahead;              /* reserved */
-    int reserved[8];
+    int fp64_mode;              /* FP64 SYRK/GEMM updates of all-FP64 factorizations:
+                                   0: the FP64 pipe (DFMA);
+                                   1: emulated on the FP8 tensor cores through 14 exact
+                                      base-16 digit planes per tile (normwise FP64 accuracy;
+                                      needs 14 b^2 extra bytes per lower tile) */
+    int reserved[7];
 } tc_config;
 
 /* Per-call statistics (any field a call does not produce is left 0). */

@@ -1,0 +1,356 @@
+// FP64 tile updates emulated on the FP8 tensor cores (GB300's FP64 pipe delivers only
+// ~1.25 TFLOP/s; its E4M3 tensor cores ~3.5 PFLOP/s).
+//
+// Splitting (the error-free slicing of Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 2012, with a per-tile exponent):
+// every final FP64 tile X with e = the smallest integer such that max|X| <= 2^e is written
+// as X = 2^e sum_{s=1..S} 16^-s D_s + R with S = 14 integer "digit planes" D_s
+// (D_1 in [-16, 16], the others in [-8, 8], |R| <= 2^(e-57)), each stored in E4M3, which
+// holds these integers exactly.  Then
+//     X Y^T = 2^(ex+ey) sum_{d=2..15} 16^-d G_d,   G_d = sum_{s+t=d} D_s(X) D_t(Y)^T,
+// dropping the pairs with s + t > 15 (below 2^-54 of the product's scale).  Each G_d over one
+// source tile (K <= 4096) is an integer below 2^24 in magnitude, so the tensor cores'
+// FP32 accumulation is exact; the drain recombines the 14 groups with int64 Horner steps
+// (exact) and adds 2^(ex+ey) (H1 16^-8 + H2 16^-15) to an FP64 running sum per element.
+// The result is the FP64 update up to FP64-level rounding relative to the tiles' scale
+// (a normwise bound, which is what the factorization's backward error needs).
+#include "tc_internal.h"
+
+#include <cuda.h>
+#include <cuda_fp8.h>
+
+namespace tc {
+
+constexpr int ZS = 14;                 // digit planes per tile
+constexpr int ZBM = 128, ZBN = 32;     // CTA block: 128 rows x 32 columns
+constexpr int ZKB = 128;               // K bytes (= E4M3 elements) per stage
+constexpr int ZXS = 6;                 // X-plane stages
+constexpr int ZX_BYTES = ZBM * ZKB;    // 16 KB: one X plane block
+constexpr int ZY_BYTES = ZBN * ZKB;    // 4 KB: one Y plane block
+constexpr int ZYSET = ZS * ZY_BYTES;   // 56 KB: all Y planes of a K block
+constexpr int ZTHREADS = 192;          // producer, MMA, 4 drain warps
+constexpr unsigned long long ZTIMEOUT_NS = 4000000000ull;
+
+// ------------------------------------------------------------------- digit planes
+// exps[t] = smallest e with amax[t] <= 2^e; planes of tile t at pool + (t*ZS + s) b^2,
+// each row-major (K-major) b x b.
+__global__ void __launch_bounds__(256)
+k_digits(const double *W, int b, const int *tiles, const double *amax, uint8_t *pool, int *exps) {
+    __shared__ double S[32][33];
+    const int t = tiles[blockIdx.y];
+    const double *T = W + (int64_t)t * b * b;
+    const double am = amax[t];
+    int e = 0;
+    if (am > 0.0) {
+        int ex;
+        const double f = frexp(am, &ex);
+        e = (f == 0.5) ? ex - 1 : ex;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) exps[t] = e;
+    const int nbc = b / 32;
+    const int64_t bb = (int64_t)b * b;
+    uint8_t *P = pool + (int64_t)t * ZS * bb;
+    for (int blk = blockIdx.x; blk < nbc * nbc; blk += gridDim.x) {
+        const int r0 = (blk % nbc) * 32, c0 = (blk / nbc) * 32;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 1024; idx += 256) {
+            const int r = idx & 31, c = idx >> 5;
+            S[r][c] = T[(int64_t)(c0 + c) * b + r0 + r];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 1024; idx += 256) {
+            const int c = idx & 31, r = idx >> 5;
+            double v = ldexp(S[r][c], -e);          // in [-1, 1]
+            const int64_t o = (int64_t)(r0 + r) * b + c0 + c;
+#pragma unroll
+            for (int s = 0; s < ZS; ++s) {
+                v = v * 16.0;                        // exact
+                const double d = rint(v);            // |d| <= 16 (s = 0), <= 8 after
+                v = v - d;                           // exact
+                P[(int64_t)s * bb + o] = (uint8_t)__nv_cvt_double_to_fp8(d, __NV_SATFINITE, __NV_E4M3);
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------- update kernel
+struct ZArgs {
+    const ZItem *items;
+    const int *exps;
+    int k, b;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t z_smem(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ uint64_t z_timer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void z_init(uint64_t *bar, uint32_t c) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(z_smem(bar)), "r"(c) : "memory");
+}
+__device__ __forceinline__ void z_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(z_smem(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void z_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(z_smem(bar)) : "memory");
+}
+__device__ __forceinline__ bool z_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(z_smem(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool z_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (z_try(bar, parity)) return true;
+    const uint64_t t0 = z_timer();
+    for (;;) {
+        if (z_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (z_timer() - t0 > ZTIMEOUT_NS) return false;
+    }
+}
+__device__ __forceinline__ void z_tma(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            z_smem(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z_smem(bar))
+        : "memory");
+}
+__device__ __forceinline__ void z_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(z_smem(bar))
+                 : "memory");
+}
+__device__ __forceinline__ uint64_t z_desc(uint32_t saddr) {   // K-major, 128-byte swizzle
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+__device__ __forceinline__ void z_mma(uint32_t d, uint64_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void z_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One CTA = one 128 x 32 block of one FP64 output tile: C -= sum_{n<k} X_n Y_n^T with X_n the
+// tiles (m, n) and Y_n the tiles (k, n), through their digit planes.
+__global__ void __launch_bounds__(ZTHREADS, 1)
+k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY, const ZArgs args) {
+    extern __shared__ __align__(1024) uint8_t zsmem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(zsmem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *xbuf = smem;                             // ZXS x 16 KB
+    uint8_t *ybuf = smem + ZXS * ZX_BYTES;            // 2 x 56 KB
+    uint64_t *xfull = reinterpret_cast<uint64_t *>(ybuf + 2 * ZYSET);
+    uint64_t *xempty = xfull + ZXS;
+    uint64_t *yfull = xempty + ZXS;
+    uint64_t *yempty = yfull + 2;
+    uint64_t *accf = yempty + 2;
+    uint64_t *acce = accf + 1;
+    uint64_t *done = acce + 1;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const ZItem it = args.items[blockIdx.x];
+    const int k = args.k, b = args.b;
+    const int kblocks = b / ZKB;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ZXS; ++s) {
+            z_init(xfull + s, 1);
+            z_init(xempty + s, 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            z_init(yfull + s, 1);
+            z_init(yempty + s, 1);
+        }
+        z_init(accf, 1);
+        z_init(acce, 4);
+        z_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(z_smem(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        // --------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int xi = 0, yi = 0, issued_x = 0, issued_y = 0;
+            bool ok = true;
+            for (int n = 0; n < k && ok; ++n) {
+                const int xt = it.xoff + n, yt = it.yoff + n;
+                for (int kb = 0; kb < kblocks && ok; ++kb, ++yi) {
+                    const int ys = yi & 1;
+                    if (!z_wait(yempty + ys, ((yi >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    z_expect(yfull + ys, ZYSET);
+                    for (int t = 0; t < ZS; ++t)
+                        z_tma(ybuf + ys * ZYSET + t * ZY_BYTES, &mapY, kb * ZKB, (yt * ZS + t) * b + it.bn * ZBN,
+                              yfull + ys);
+                    ++issued_y;
+                    for (int s = 0; s < ZS; ++s, ++xi) {
+                        const int st = xi % ZXS;
+                        if (!z_wait(xempty + st, ((xi / ZXS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                        z_expect(xfull + st, ZX_BYTES);
+                        z_tma(xbuf + st * ZX_BYTES, &mapX, kb * ZKB, (xt * ZS + s) * b + it.bm * ZBM, xfull + st);
+                        ++issued_x;
+                    }
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(args.err, 1);
+                static __shared__ int never;
+                never = 0;
+                for (int q = issued_x - ZXS < 0 ? 0 : issued_x - ZXS; q < issued_x; ++q)
+                    z_wait(xfull + q % ZXS, (q / ZXS) & 1, &never);
+                for (int q = issued_y - 2 < 0 ? 0 : issued_y - 2; q < issued_y; ++q)
+                    z_wait(yfull + (q & 1), (q >> 1) & 1, &never);
+            }
+        }
+    } else if (warp == 1) {
+        // --------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            // kind::f8f6f4, D F32, A/B E4M3, K-major, N = 32, M = 128
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(ZBN >> 3) << 17) | ((uint32_t)(ZBM >> 4) << 24);
+            int xi = 0, yi = 0;
+            bool ok = true;
+            for (int n = 0; n < k && ok; ++n) {
+                if (!z_wait(acce, (n & 1) ^ 1, abort_flag)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int kb = 0; kb < kblocks && ok; ++kb, ++yi) {
+                    const int ys = yi & 1;
+                    if (!z_wait(yfull + ys, (yi >> 1) & 1, abort_flag)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t ybase = z_smem(ybuf + ys * ZYSET);
+                    for (int s = 0; s < ZS; ++s, ++xi) {
+                        const int st = xi % ZXS;
+                        if (!z_wait(xfull + st, (xi / ZXS) & 1, abort_flag)) { ok = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t xa = z_smem(xbuf + st * ZX_BYTES);
+                        for (int t = 0; t + s < ZS; ++t) {
+                            const uint32_t dt = tmem + (uint32_t)((s + t) * ZBN);   // group d = s + t + 2
+#pragma unroll
+                            for (int kk = 0; kk < ZKB / 32; ++kk)
+                                z_mma(dt, z_desc(xa + kk * 32), z_desc(ybase + t * ZY_BYTES + kk * 32), idesc,
+                                      (kb > 0 || s > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        z_commit(xempty + st);
+                    }
+                    if (ok) z_commit(yempty + ys);
+                }
+                if (ok) z_commit(accf);
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(args.err, 1);
+            }
+            z_commit(done);
+            z_wait(done, 0, abort_flag);
+        }
+    } else {
+        // --------------------------------------------------------------- drain + epilogue
+        const int quarter = warp & 3;
+        double run[ZBN];
+#pragma unroll
+        for (int j = 0; j < ZBN; ++j) run[j] = 0.0;
+        bool ok = true;
+        for (int n = 0; n < k; ++n) {
+            if (!z_wait(accf, n & 1, abort_flag)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int E = args.exps[it.xoff + n] + args.exps[it.yoff + n];
+            const uint32_t lanebase = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+            for (int c = 0; c < ZBN / 16; ++c) {
+                long long hi[16], lo[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+                for (int g = 0; g < ZS; ++g) {
+                    float v[16];
+                    z_ld16(lanebase + (uint32_t)(g * ZBN + c * 16), v);
+                    if (g < 7) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) hi[j] = hi[j] * 16 + __float2ll_rn(v[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) lo[j] = lo[j] * 16 + __float2ll_rn(v[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    run[c * 16 + j] += ldexp((double)hi[j], E - 32) + ldexp((double)lo[j], E - 60);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) z_arrive(acce);
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(args.err, 1);
+        } else {
+            const int row = it.bm * ZBM + quarter * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < ZBN; ++j) {
+                const int col = it.bn * ZBN + j;
+                it.C[(int64_t)col * b + row] -= run[j];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+// ------------------------------------------------------------------------- host side
+// map over the digit pool: rows = tiles * 14 * b, b bytes each; box 128 bytes x box_rows
+int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_rows) {
+    return make_pool_map(map, pool, rows / b, b, 1, box_rows);
+}
+
+size_t zgemm_smem_bytes() { return (size_t)ZXS * ZX_BYTES + 2 * ZYSET + 1024 + 256; }
+
+void launch_digits(const double *W, int b, const int *tiles, int ntiles, const double *amax, uint8_t *pool, int *exps,
+                   cudaStream_t s) {
+    if (ntiles > 0) k_digits<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, amax, pool, exps);
+}
+
+void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
+                  int b, int *err, cudaStream_t s) {
+    if (nitems <= 0 || k <= 0) return;
+    static bool attr = false;
+    const size_t smem = zgemm_smem_bytes();
+    if (!attr) {
+        cudaFuncSetAttribute(k_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    ZArgs a{items, exps, k, b, err};
+    k_zgemm<<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
+}
+
+}  // namespace tc

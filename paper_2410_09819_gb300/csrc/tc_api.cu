@@ -34,6 +34,8 @@ struct PotrfStep {
 };
 
 struct ColPlan {
+    int z0 = 0, nz = 0;          // emulated-FP64 update items
+    int dg0 = 0, ndg = 0;        // tiles whose digit planes are made after the column's TRSMs
     int it0 = 0, nit = 0;        // FP64 update items
     int red0 = 0, nred = 0;      // split-K reductions
     int st0 = 0, nst = 0;        // TRSM strips
@@ -47,7 +49,10 @@ struct Plan {
     std::vector<TStrip> strips;
     std::vector<PEntry> pentries;
     std::vector<LEntry> lentries;
+    std::vector<ZItem> zitems;
+    std::vector<int> dtiles;
     std::vector<ColPlan> cols;
+    int64_t Ttot = 0;
     int max_parts = 0, ntmax = 0;
     double update_flops[4] = {0, 0, 0, 0};
     double trsm_flops = 0, potrf_flops = 0;
@@ -80,8 +85,12 @@ Plan build_plan(tc_handle h, double *W, int *status) {
     Plan P;
     const int b = h->b;
     const int64_t bb = (int64_t)b * b;
-    for (const MatDesc &M : h->mats) P.ntmax = std::max(P.ntmax, M.nt);
+    for (const MatDesc &M : h->mats) {
+        P.ntmax = std::max(P.ntmax, M.nt);
+        P.Ttot = std::max<int64_t>(P.Ttot, M.tile0 + tidx(M.nt, 0));
+    }
     P.cols.resize(P.ntmax);
+    const bool zmode = h->cfg.fp64_mode == 1;
     auto T = [&](const MatDesc &M, int i, int j) { return W + (M.tile0 + tidx(i, j)) * bb; };
     const int nmat = (int)h->mats.size();
     for (int mi = 0; mi < nmat; ++mi) {
@@ -93,6 +102,7 @@ Plan build_plan(tc_handle h, double *W, int *status) {
         // 1. updates of column k (FP64 output tiles here; low-precision ones in build_mxp)
         C.it0 = (int)P.items.size();
         C.red0 = (int)P.reds.size();
+        C.z0 = (int)P.zitems.size();
         if (k > 0) {
             const int K = k * b;
             std::vector<int> jobs_here;
@@ -103,6 +113,17 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 for (int m = k; m < M.nt; ++m) {
                     const bool fp64 = (m == k) || !M.mixed || M.map[(size_t)m * M.nt + k] == TC_FP64;
                     if (!fp64) continue;
+                    if (zmode && !M.mixed) {
+                        // emulated FP64: 128 x 32 blocks (the diagonal SYRK keeps blocks reaching the lower part)
+                        double *Cp = T(M, m, k);
+                        const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
+                        for (int bn = 0; bn < b / 32; ++bn)
+                            for (int bm = 0; bm < b / 128; ++bm)
+                                if (m != k || bm * 128 + 127 >= bn * 32)
+                                    P.zitems.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn});
+                        P.update_flops[TC_FP64] += (m == k ? 1.0 : 2.0) * (double)b * b * K;
+                        continue;
+                    }
                     jobs_here.push_back((int)P.jobs.size());
                     P.jobs.push_back({T(M, m, k), T(M, m, 0), T(M, k, 0), K, b, b, m == k ? 1 : 0, status + 2 + mi});
                     base += (m == k) ? (b / 64) * (b / 64 + 1) / 2 : (b / 64) * (b / 64);
@@ -118,6 +139,14 @@ Plan build_plan(tc_handle h, double *W, int *status) {
         }
         C.nit = (int)P.items.size() - C.it0;
         C.nred = (int)P.reds.size() - C.red0;
+        C.nz = (int)P.zitems.size() - C.z0;
+        // digit planes of the final tiles of this column (operands of later emulated updates)
+        C.dg0 = (int)P.dtiles.size();
+        if (zmode)
+            for (const MatDesc &M : h->mats)
+                if (!M.mixed && M.nt > k)
+                    for (int m = k + 1; m < M.nt; ++m) P.dtiles.push_back((int)(M.tile0 + tidx(m, k)));
+        C.ndg = (int)P.dtiles.size() - C.dg0;
         // 2. blocked POTRF of the diagonal tiles: per 64-panel, the block, its panel and the
         //    trailing update, each one launch over all matrices
         for (int jb = 0; jb < b / 64; ++jb) {
@@ -352,6 +381,10 @@ struct PlanDev {
     const TStrip *strips;
     const PEntry *pentries;
     const LEntry *lentries;
+    const ZItem *zitems = nullptr;
+    const int *dtiles = nullptr;
+    int *zexps = nullptr;
+    double *zamax = nullptr;
     MxpDev mx{};
     bool mixed = false;
 };
@@ -380,6 +413,27 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
     D.pentries = reinterpret_cast<const PEntry *>(base + op);
     D.lentries = reinterpret_cast<const LEntry *>(base + ol);
     if ((rc = ensure(h, h->partials, (size_t)std::max(1, P.max_parts) * 4096 * sizeof(double)))) return rc;
+    if (!P.zitems.empty() || !P.dtiles.empty()) {
+        // digit planes (14 per tile), exponents, amax, the Z items and the digit tile lists
+        const int64_t Tt = P.Ttot;
+        const size_t bb = (size_t)h->b * h->b;
+        if ((rc = ensure(h, h->dpool, (size_t)Tt * 14 * bb))) return rc;
+        const size_t oz = 0, od = align_up(P.zitems.size() * sizeof(ZItem)), oe = align_up(od + P.dtiles.size() * 4);
+        const size_t oa = align_up(oe + Tt * 4), zt = align_up(oa + Tt * 8);
+        if ((rc = ensure(h, h->ztab, zt))) return rc;
+        std::vector<char> zh(zt, 0);
+        if (!P.zitems.empty()) memcpy(zh.data() + oz, P.zitems.data(), P.zitems.size() * sizeof(ZItem));
+        if (!P.dtiles.empty()) memcpy(zh.data() + od, P.dtiles.data(), P.dtiles.size() * 4);
+        CK(cudaMemcpy(h->ztab.p, zh.data(), zt, cudaMemcpyHostToDevice));
+        char *zb = static_cast<char *>(h->ztab.p);
+        D.zitems = reinterpret_cast<const ZItem *>(zb + oz);
+        D.dtiles = reinterpret_cast<const int *>(zb + od);
+        D.zexps = reinterpret_cast<int *>(zb + oe);
+        D.zamax = reinterpret_cast<double *>(zb + oa);
+        if (make_digit_map(&h->map_zx, h->dpool.p, Tt * 14 * h->b, h->b, 128) ||
+            make_digit_map(&h->map_zy, h->dpool.p, Tt * 14 * h->b, h->b, 32))
+            return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the digit planes");
+    }
     D.mixed = M != nullptr;
     if (M && (rc = setup_mxp(h, *M, D.mx))) return rc;
     return TC_OK;
@@ -400,6 +454,7 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
     launch_fix_padding_batched(D.lentries, nmat, P.ntmax, b, h->s);
     CK_LAUNCH();
     CK(cudaMemsetAsync(status, 0, (2 + nmat) * sizeof(int), h->s));
+    if (D.zamax) CK(cudaMemsetAsync(D.zamax, 0, P.Ttot * sizeof(double), h->s));
     if (M) {
         CK(cudaMemsetAsync(D.mx.amaxL, 0, M->T * sizeof(double), h->s));
         CK(cudaMemsetAsync(D.mx.amaxS, 0, M->T * sizeof(double), h->s));
@@ -418,6 +473,13 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
         if (C.nred) {
             launch_dgemm_reduce(D.reds + C.red0, C.nred, b, parts, nullptr, h->s);
             CK_LAUNCH();
+        }
+        if (C.nz) {
+            const int sp = spans ? span_begin(h, CAT_UPD64) : -1;
+            launch_zgemm(h->map_zx, h->map_zy, D.zitems + C.z0, C.nz, D.zexps, k, b, status + 1, h->s);
+            span_end(h, sp);
+            CK_LAUNCH();
+            ++h->upd_launches[TC_FP64];
         }
         if (M) {
             const int rc = mxp_updates(h, *M, D.mx, k, spans);
@@ -444,6 +506,14 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
         if (M) {
             const int rc = mxp_convert(h, *M, D.mx, k, spans);
             if (rc) return rc;
+        }
+        if (C.ndg) {
+            const int sp = spans ? span_begin(h, CAT_CONVERT) : -1;
+            launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, D.zamax, h->s);
+            CK_LAUNCH();
+            launch_digits(W, b, D.dtiles + C.dg0, C.ndg, D.zamax, static_cast<uint8_t *>(h->dpool.p), D.zexps, h->s);
+            span_end(h, sp);
+            CK_LAUNCH();
         }
     }
     double *sc = static_cast<double *>(h->scratch.p);
@@ -608,7 +678,7 @@ void tc_destroy(tc_handle h) {
     cudaSetDevice(h->device);
     if (h->s) cudaStreamSynchronize(h->s);
     for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq,
-                      &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab, &h->logdiag})
+                      &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab, &h->logdiag, &h->dpool, &h->ztab})
         release(*d);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     release(h->bstage);
@@ -749,6 +819,8 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
     }
     for (uint8_t v : M.map) M.mixed |= (v != TC_FP64);
     if (M.mixed && b % 128) return set_err(h, TC_ERR_UNSUPPORTED, "mixed precision needs a tile size that is a multiple of 128");
+    if (h->cfg.fp64_mode == 1 && b % 128)
+        return set_err(h, TC_ERR_UNSUPPORTED, "emulated FP64 updates need a tile size that is a multiple of 128");
     if ((rc = ensure(h, h->W, bytes))) return rc;
     // the caller's A stays readable for refinement: reference it on the device or copy it
     if (on_device(A_tiles)) {

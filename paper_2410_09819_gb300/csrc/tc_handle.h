@@ -53,6 +53,9 @@ struct tc_handle_s {
     DevBuf pool_hi, pool_lo, pool16, pool8;
     DevBuf mxtab;
     CUtensorMap map_hi{}, map_lo{}, map16{}, map8{};
+    // emulated FP64 updates: digit planes, their tables and tensor maps
+    DevBuf dpool, ztab;
+    CUtensorMap map_zx{}, map_zy{};
     // matrices of the last (batched) factorization
     std::vector<MatDesc> mats;
     std::vector<double> logdets;

@@ -119,6 +119,21 @@ void launch_matern(double *A, int64_t n, int b, int nt, const double *pts, doubl
                    double a, int nu2, double nugget, cudaStream_t s);
 void launch_tile_sumsq(const double *A, int nt, int b, int64_t n, double *out, cudaStream_t s);
 
+// Emulated-FP64 update of one 128 x 32 block of an FP64 output tile (k_ozaki.cu).
+struct ZItem {
+    double *C;
+    int xoff, yoff;
+    uint16_t bm, bn;
+};
+
+// ------------------------------------------------------------------ launchers (k_ozaki.cu)
+size_t zgemm_smem_bytes();
+void launch_digits(const double *W, int b, const int *tiles, int ntiles, const double *amax, uint8_t *pool, int *exps,
+                   cudaStream_t s);
+void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
+                  int b, int *err, cudaStream_t s);
+int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_rows);
+
 // ------------------------------------------------------------------ launchers (k_mxp.cu)
 int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows);
 size_t qgemm_smem_bytes();

@@ -1,0 +1,102 @@
+"""GPU tests of the emulated FP64 updates (fp64_mode = 1: exact base-16 digit planes on the
+FP8 tensor cores) against exact cases, closed forms and the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_09819_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2410_09819_gb300 import tile_chol as tc  # noqa: E402
+
+from gpu_util import DEV, pack_padded, to_dev, unpack_lower  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def HZ():
+    with tc.Handle(0, fp64_mode=1) as h:
+        yield h
+
+
+def factor(H, A, b):
+    n = A.shape[0]
+    At = to_dev(pack_padded(A, b))
+    st = tc.tc_stats()
+    info = tc.tile_chol_factor(H.h, n, b, At, None, st)
+    L = torch.empty_like(At)
+    if info == 0:
+        tc.tile_chol_get_factor(H.h, L)
+    return info, unpack_lower(L, n, b), st
+
+
+@pytest.mark.parametrize("n,b", [(1024, 128), (2048, 256), (1000, 128), (1536, 512)])
+def test_integer_factor_bit_exact(HZ, n, b):
+    rng = np.random.default_rng(n + b)
+    L = np.tril(rng.integers(-1, 2, (n, n)).astype(np.float64), -1) + np.eye(n)
+    info, Lg, st = factor(HZ, L @ L.T, b)
+    assert info == 0
+    assert np.array_equal(Lg, L)
+    assert st.update_launches[0] > 0
+
+
+def test_pascal_exact(HZ):
+    n = 12
+    P = np.array([[math.comb(i + j, i) for j in range(n)] for i in range(n)], dtype=np.float64)
+    info, Lg, _ = factor(HZ, P, 128)
+    assert info == 0
+    assert np.array_equal(Lg, np.array([[math.comb(i, j) if j <= i else 0 for j in range(n)] for i in range(n)], float))
+
+
+def test_matern_config1_backward_error_and_logdet(HZ):
+    w = inputs.WORKLOADS["fp64_n2048"]
+    A = oracle.matern(w.points(), w.sigma2, w.range_a, w.nu, w.nugget)
+    Lo = oracle.cholesky(A)
+    info, Lg, _ = factor(HZ, A, w.tile)
+    assert info == 0
+    berr = np.linalg.norm(A - Lg @ Lg.T) / np.linalg.norm(A)
+    assert berr <= 1e-13
+    assert abs(tc.tile_chol_logdet(HZ.h) - oracle.logdet(Lo)) <= 1e-11 * abs(oracle.logdet(Lo))
+    kappa = np.linalg.cond(A)
+    bound = kappa * 2 * (berr + np.linalg.norm(A - Lo @ Lo.T) / np.linalg.norm(A)) * np.abs(Lo).max()
+    assert np.max(np.abs(Lg - Lo)) <= max(bound, 1e-14)
+    B = inputs.gaussian(A.shape[0], 2, seed=3)
+    X = torch.empty((2, A.shape[0]), dtype=torch.float64, device=DEV)
+    st = tc.tc_stats()
+    tc.tile_chol_solve(HZ.h, 2, to_dev(B.T.copy()), A.shape[0], X, A.shape[0], 4, 1e-14, st)
+    Xg = X.cpu().numpy().T
+    be = np.max(np.abs(B - A @ Xg).max(0) / (np.abs(A).sum(1).max() * np.abs(Xg).max(0) + np.abs(B).max(0)))
+    assert be <= 1e-13
+
+
+def test_ar1_closed_form(HZ):
+    n, b = 4096, 512
+    pts = inputs.line_points(n, seed=17)
+    a = 0.05
+    A = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=DEV)
+    tc.tc_matern_tiles(HZ.h, n, b, to_dev(pts), 1.0, a, 0.5, 0.0, A)
+    assert tc.tile_chol_factor(HZ.h, n, b, A) == 0
+    rho = np.exp(-np.diff(pts[:, 0]) / a)
+    ld = float(np.sum(np.log1p(-rho * rho)))
+    assert abs(tc.tile_chol_logdet(HZ.h) - ld) < 1e-10 * abs(ld)
+
+
+def test_emulated_and_dfma_factors_agree():
+    n, b = 2048, 256
+    A = oracle.matern(inputs.uniform_points(n, 8, morton=True), 1.0, 0.05, 1.5, 1e-4)
+    with tc.Handle(0, fp64_mode=1) as Hz, tc.Handle(0) as Hd:
+        _, Lz, _ = factor(Hz, A, b)
+        _, Ld, _ = factor(Hd, A, b)
+    assert np.max(np.abs(Lz - Ld)) <= 1e-12 * np.abs(Ld).max() * max(1.0, np.linalg.cond(A) * 1e-3)
+
+
+def test_tile_size_rule():
+    with tc.Handle(0, fp64_mode=1) as H:
+        with pytest.raises(tc.TileCholError):
+            tc.tile_chol_factor(H.h, 128, 64, to_dev(np.eye(128).reshape(-1)[: 3 * 64 * 64].copy()))
