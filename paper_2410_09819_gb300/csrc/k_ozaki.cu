@@ -236,8 +236,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
     } else if (warp == 1) {
         // --------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            // kind::f8f6f4, D F32, A/B E4M3, K-major, N = 32, M = 128
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(ZBN >> 3) << 17) | ((uint32_t)(ZBM >> 4) << 24);
+            // kind::f8f6f4, D F32, A/B E4M3, K-major, M = 128; N set per instruction
+            const uint32_t idesc0 = (1u << 4) | ((uint32_t)(ZBM >> 4) << 24);
             int xi = 0, yi = 0;
             bool ok = true;
             for (int n = 0; n < k && ok; ++n) {
@@ -253,12 +253,20 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                         if (!z_wait(xfull + st, (xi / ZXS) & 1, abort_flag)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t xa = z_smem(xbuf + st * ZX_BYTES);
-                        for (int t = 0; t + s < ZS; ++t) {
-                            const uint32_t dt = tmem + (uint32_t)((s + t) * ZBN);   // group d = s + t + 2
+                        // The Y planes sit back to back in shared memory (plane t at t * 32 rows),
+                        // so one MMA with N = 32 * cnt multiplies X_s by Y_t0 .. Y_t0+cnt-1 at once,
+                        // and column block j of its result lands on group s + t0 + j (the TMEM
+                        // columns of group g are g * 32 .. g * 32 + 31): the grouping by weight
+                        // comes from the accumulator address.  N is at most 256 per instruction.
 #pragma unroll
-                            for (int kk = 0; kk < ZKB / 32; ++kk)
-                                z_mma(dt, z_desc(xa + kk * 32), z_desc(ybase + t * ZY_BYTES + kk * 32), idesc,
+                        for (int kk = 0; kk < ZKB / 32; ++kk) {
+                            for (int t0 = 0; t0 + s < ZS; t0 += 8) {
+                                const int cnt = (ZS - s - t0) < 8 ? (ZS - s - t0) : 8;
+                                const uint32_t idesc = idesc0 | ((uint32_t)((cnt * ZBN) >> 3) << 17);
+                                z_mma(tmem + (uint32_t)((s + t0) * ZBN), z_desc(xa + kk * 32),
+                                      z_desc(ybase + t0 * ZY_BYTES + kk * 32), idesc,
                                       (kb > 0 || s > 0 || kk > 0) ? 1u : 0u);
+                            }
                         }
                         z_commit(xempty + st);
                     }

@@ -100,3 +100,27 @@ def test_tile_size_rule():
     with tc.Handle(0, fp64_mode=1) as H:
         with pytest.raises(tc.TileCholError):
             tc.tile_chol_factor(H.h, 128, 64, to_dev(np.eye(128).reshape(-1)[: 3 * 64 * 64].copy()))
+
+
+def test_full_size_ar1_closed_form_n65536_emulated(HZ):
+    n, b = 65536, 1024
+    pts = inputs.line_points(n, seed=2)
+    a = 0.05
+    A = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=DEV)
+    tc.tc_matern_tiles(HZ.h, n, b, to_dev(pts), 1.0, a, 0.5, 0.0, A)
+    assert tc.tile_chol_factor(HZ.h, n, b, A) == 0
+    rho = np.exp(-np.diff(pts[:, 0]) / a)
+    c = np.concatenate([[1.0], np.sqrt(1.0 - rho * rho)])
+    logcum = np.concatenate([[0.0], np.cumsum(np.log(rho))])
+    ld = float(np.sum(np.log1p(-rho * rho)))
+    assert abs(tc.tile_chol_logdet(HZ.h) - ld) <= 1e-9 * abs(ld)
+    del A
+    L = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=DEV)
+    tc.tile_chol_get_factor(HZ.h, L)
+    rng = np.random.default_rng(1)
+    cols = rng.integers(0, n, 20000)
+    rows = np.minimum(cols + rng.integers(0, 3000, 20000), n - 1)
+    ti, tj = rows // b, cols // b
+    idx = (ti * (ti + 1) // 2 + tj) * b * b + (cols % b) * b + (rows % b)
+    got = L[to_dev(idx)].cpu().numpy()
+    assert np.max(np.abs(got - np.exp(logcum[rows] - logcum[cols]) * c[cols])) < 1e-10
