@@ -71,11 +71,14 @@ typedef struct {
     int prefetch_depth;         /* reserved: tile_chol_factor_ooc enqueues its whole static
                                    schedule, so copies run ahead as far as free slots allow */
     int lookahead;              /* reserved */
-    int fp64_mode;              /* FP64 SYRK/GEMM updates of all-FP64 factorizations:
-                                   0: the FP64 pipe (DFMA);
-                                   1: emulated on the FP8 tensor cores through 14 exact
-                                      base-16 digit planes per tile (normwise FP64 accuracy;
-                                      needs 14 b^2 extra bytes per lower tile) */
+    int fp64_mode;              /* how SYRK/GEMM updates of FP64 (and FP32) output tiles run:
+                                   0: FP64 tiles on the FP64 pipe (DFMA), FP32 tiles as
+                                      3 x TF32 tensor-core products;
+                                   1: both on the FP8 tensor cores through exact base-16
+                                      digit planes of every final tile (14 planes for FP64
+                                      outputs: normwise FP64 accuracy; 8 for FP32 outputs:
+                                      below 2^-32 of the tile scale); needs 14 b^2 extra
+                                      bytes per lower tile and a tile size multiple of 128 */
     int reserved[7];
 } tc_config;
 

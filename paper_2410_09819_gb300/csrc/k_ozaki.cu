@@ -149,8 +149,11 @@ __device__ __forceinline__ void z_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// One CTA = one 128 x 32 block of one FP64 output tile: C -= sum_{n<k} X_n Y_n^T with X_n the
-// tiles (m, n) and Y_n the tiles (k, n), through their digit planes.
+// One CTA = one 128 x 32 block of one output tile: C -= sum_{n<k} X_n Y_n^T with X_n the
+// tiles (m, n) and Y_n the tiles (k, n), through their first SU digit planes (SU = 14 for FP64
+// outputs; SU = 8, i.e. pairs with s + t <= 9 and a truncation below 2^-32 of the tile scale,
+// for FP32 outputs).
+template <int SU>
 __global__ void __launch_bounds__(ZTHREADS, 1)
 k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY, const ZArgs args) {
     extern __shared__ __align__(1024) uint8_t zsmem_raw[];
@@ -208,12 +211,12 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 for (int kb = 0; kb < kblocks && ok; ++kb, ++yi) {
                     const int ys = yi & 1;
                     if (!z_wait(yempty + ys, ((yi >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                    z_expect(yfull + ys, ZYSET);
-                    for (int t = 0; t < ZS; ++t)
+                    z_expect(yfull + ys, SU * ZY_BYTES);
+                    for (int t = 0; t < SU; ++t)
                         z_tma(ybuf + ys * ZYSET + t * ZY_BYTES, &mapY, kb * ZKB, (yt * ZS + t) * b + it.bn * ZBN,
                               yfull + ys);
                     ++issued_y;
-                    for (int s = 0; s < ZS; ++s, ++xi) {
+                    for (int s = 0; s < SU; ++s, ++xi) {
                         const int st = xi % ZXS;
                         if (!z_wait(xempty + st, ((xi / ZXS) & 1) ^ 1, abort_flag)) { ok = false; break; }
                         z_expect(xfull + st, ZX_BYTES);
@@ -248,7 +251,7 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                     if (!z_wait(yfull + ys, (yi >> 1) & 1, abort_flag)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t ybase = z_smem(ybuf + ys * ZYSET);
-                    for (int s = 0; s < ZS; ++s, ++xi) {
+                    for (int s = 0; s < SU; ++s, ++xi) {
                         const int st = xi % ZXS;
                         if (!z_wait(xfull + st, (xi / ZXS) & 1, abort_flag)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -260,8 +263,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                         // comes from the accumulator address.  N is at most 256 per instruction.
 #pragma unroll
                         for (int kk = 0; kk < ZKB / 32; ++kk) {
-                            for (int t0 = 0; t0 + s < ZS; t0 += 8) {
-                                const int cnt = (ZS - s - t0) < 8 ? (ZS - s - t0) : 8;
+                            for (int t0 = 0; t0 + s < SU; t0 += 8) {
+                                const int cnt = (SU - s - t0) < 8 ? (SU - s - t0) : 8;
                                 const uint32_t idesc = idesc0 | ((uint32_t)((cnt * ZBN) >> 3) << 17);
                                 z_mma(tmem + (uint32_t)((s + t0) * ZBN), z_desc(xa + kk * 32),
                                       z_desc(ybase + t0 * ZY_BYTES + kk * 32), idesc,
@@ -298,7 +301,7 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 long long hi[16], lo[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
-                for (int g = 0; g < ZS; ++g) {
+                for (int g = 0; g < SU; ++g) {
                     float v[16];
                     z_ld16(lanebase + (uint32_t)(g * ZBN + c * 16), v);
                     if (g < 7) {
@@ -311,7 +314,7 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    run[c * 16 + j] += ldexp((double)hi[j], E - 32) + ldexp((double)lo[j], E - 60);
+                    run[c * 16 + j] += ldexp((double)hi[j], E - 32) + ldexp((double)lo[j], E - 4 * (SU + 1));
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -349,16 +352,18 @@ void launch_digits(const double *W, int b, const int *tiles, int ntiles, const d
 }
 
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
-                  int b, int *err, cudaStream_t s) {
+                  int b, int *err, cudaStream_t s, int planes) {
     if (nitems <= 0 || k <= 0) return;
     static bool attr = false;
     const size_t smem = zgemm_smem_bytes();
     if (!attr) {
-        cudaFuncSetAttribute(k_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<14>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     ZArgs a{items, exps, k, b, err};
-    k_zgemm<<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
+    if (planes == 8) k_zgemm<8><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
+    else k_zgemm<14><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
 }
 
 }  // namespace tc

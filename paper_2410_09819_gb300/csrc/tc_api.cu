@@ -35,6 +35,7 @@ struct PotrfStep {
 
 struct ColPlan {
     int z0 = 0, nz = 0;          // emulated-FP64 update items
+    int y0 = 0, ny = 0;          // emulated FP32-output update items (8 digit planes)
     int dg0 = 0, ndg = 0;        // tiles whose digit planes are made after the column's TRSMs
     int it0 = 0, nit = 0;        // FP64 update items
     int red0 = 0, nred = 0;      // split-K reductions
@@ -49,7 +50,7 @@ struct Plan {
     std::vector<TStrip> strips;
     std::vector<PEntry> pentries;
     std::vector<LEntry> lentries;
-    std::vector<ZItem> zitems;
+    std::vector<ZItem> zitems, zitems32;
     std::vector<int> dtiles;
     std::vector<ColPlan> cols;
     int64_t Ttot = 0;
@@ -103,6 +104,7 @@ Plan build_plan(tc_handle h, double *W, int *status) {
         C.it0 = (int)P.items.size();
         C.red0 = (int)P.reds.size();
         C.z0 = (int)P.zitems.size();
+        C.y0 = (int)P.zitems32.size();
         if (k > 0) {
             const int K = k * b;
             std::vector<int> jobs_here;
@@ -112,8 +114,18 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 if (M.nt <= k) continue;
                 for (int m = k; m < M.nt; ++m) {
                     const bool fp64 = (m == k) || !M.mixed || M.map[(size_t)m * M.nt + k] == TC_FP64;
+                    if (!fp64 && zmode && M.map[(size_t)m * M.nt + k] == TC_FP32) {
+                        // FP32 output: 8 digit planes of each operand, FP64 running sums
+                        double *Cp = T(M, m, k);
+                        const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
+                        for (int bn = 0; bn < b / 32; ++bn)
+                            for (int bm = 0; bm < b / 128; ++bm)
+                                P.zitems32.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn});
+                        P.update_flops[TC_FP32] += 2.0 * (double)b * b * K;
+                        continue;
+                    }
                     if (!fp64) continue;
-                    if (zmode && !M.mixed) {
+                    if (zmode) {
                         // emulated FP64: 128 x 32 blocks (the diagonal SYRK keeps blocks reaching the lower part)
                         double *Cp = T(M, m, k);
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
@@ -140,11 +152,12 @@ Plan build_plan(tc_handle h, double *W, int *status) {
         C.nit = (int)P.items.size() - C.it0;
         C.nred = (int)P.reds.size() - C.red0;
         C.nz = (int)P.zitems.size() - C.z0;
+        C.ny = (int)P.zitems32.size() - C.y0;
         // digit planes of the final tiles of this column (operands of later emulated updates)
         C.dg0 = (int)P.dtiles.size();
         if (zmode)
             for (const MatDesc &M : h->mats)
-                if (!M.mixed && M.nt > k)
+                if (M.nt > k)
                     for (int m = k + 1; m < M.nt; ++m) P.dtiles.push_back((int)(M.tile0 + tidx(m, k)));
         C.ndg = (int)P.dtiles.size() - C.dg0;
         // 2. blocked POTRF of the diagonal tiles: per 64-panel, the block, its panel and the
@@ -216,6 +229,7 @@ struct MxpPlan {
 
 MxpPlan build_mxp(tc_handle h, double *W) {
     MxpPlan X;
+    const bool zmode = h->cfg.fp64_mode == 1;   // FP32 outputs then run on digit planes
     const int b = h->b;
     const int64_t bb = (int64_t)b * b;
     int ntmax = 0;
@@ -236,6 +250,7 @@ MxpPlan build_mxp(tc_handle h, double *W) {
                 unsigned mask = 0;
                 for (int kk = j + 1; kk < i; ++kk) mask |= 1u << P(i, kk);
                 for (int m = i + 1; m < nt; ++m) mask |= 1u << P(m, i);
+                if (zmode) mask &= ~(1u << TC_FP32);
                 for (int q = 1; q <= 3; ++q)
                     if (mask & (1u << q)) X.slot[q - 1][g] = (int)X.nslots[q - 1]++;
             }
@@ -246,7 +261,7 @@ MxpPlan build_mxp(tc_handle h, double *W) {
         MxpPlan::Col &C = X.cols[k];
         for (int q = 1; q <= 3; ++q) {
             C.q0[q - 1] = (int)X.qitems.size();
-            if (k > 0)
+            if (k > 0 && !(zmode && q == TC_FP32))
                 for (const MatDesc &M : h->mats) {
                     if (!M.mixed || M.nt <= k) continue;
                     for (int m = k + 1; m < M.nt; ++m) {
@@ -381,7 +396,7 @@ struct PlanDev {
     const TStrip *strips;
     const PEntry *pentries;
     const LEntry *lentries;
-    const ZItem *zitems = nullptr;
+    const ZItem *zitems = nullptr, *zitems32 = nullptr;
     const int *dtiles = nullptr;
     int *zexps = nullptr;
     double *zamax = nullptr;
@@ -413,20 +428,23 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
     D.pentries = reinterpret_cast<const PEntry *>(base + op);
     D.lentries = reinterpret_cast<const LEntry *>(base + ol);
     if ((rc = ensure(h, h->partials, (size_t)std::max(1, P.max_parts) * 4096 * sizeof(double)))) return rc;
-    if (!P.zitems.empty() || !P.dtiles.empty()) {
+    if (!P.zitems.empty() || !P.zitems32.empty() || !P.dtiles.empty()) {
         // digit planes (14 per tile), exponents, amax, the Z items and the digit tile lists
         const int64_t Tt = P.Ttot;
         const size_t bb = (size_t)h->b * h->b;
         if ((rc = ensure(h, h->dpool, (size_t)Tt * 14 * bb))) return rc;
-        const size_t oz = 0, od = align_up(P.zitems.size() * sizeof(ZItem)), oe = align_up(od + P.dtiles.size() * 4);
+        const size_t oz = 0, oy = align_up(P.zitems.size() * sizeof(ZItem));
+        const size_t od = align_up(oy + P.zitems32.size() * sizeof(ZItem)), oe = align_up(od + P.dtiles.size() * 4);
         const size_t oa = align_up(oe + Tt * 4), zt = align_up(oa + Tt * 8);
         if ((rc = ensure(h, h->ztab, zt))) return rc;
         std::vector<char> zh(zt, 0);
         if (!P.zitems.empty()) memcpy(zh.data() + oz, P.zitems.data(), P.zitems.size() * sizeof(ZItem));
+        if (!P.zitems32.empty()) memcpy(zh.data() + oy, P.zitems32.data(), P.zitems32.size() * sizeof(ZItem));
         if (!P.dtiles.empty()) memcpy(zh.data() + od, P.dtiles.data(), P.dtiles.size() * 4);
         CK(cudaMemcpy(h->ztab.p, zh.data(), zt, cudaMemcpyHostToDevice));
         char *zb = static_cast<char *>(h->ztab.p);
         D.zitems = reinterpret_cast<const ZItem *>(zb + oz);
+        D.zitems32 = reinterpret_cast<const ZItem *>(zb + oy);
         D.dtiles = reinterpret_cast<const int *>(zb + od);
         D.zexps = reinterpret_cast<int *>(zb + oe);
         D.zamax = reinterpret_cast<double *>(zb + oa);
@@ -476,10 +494,17 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
         }
         if (C.nz) {
             const int sp = spans ? span_begin(h, CAT_UPD64) : -1;
-            launch_zgemm(h->map_zx, h->map_zy, D.zitems + C.z0, C.nz, D.zexps, k, b, status + 1, h->s);
+            launch_zgemm(h->map_zx, h->map_zy, D.zitems + C.z0, C.nz, D.zexps, k, b, status + 1, h->s, 14);
             span_end(h, sp);
             CK_LAUNCH();
             ++h->upd_launches[TC_FP64];
+        }
+        if (C.ny) {
+            const int sp = spans ? span_begin(h, CAT_UPD32) : -1;
+            launch_zgemm(h->map_zx, h->map_zy, D.zitems32 + C.y0, C.ny, D.zexps, k, b, status + 1, h->s, 8);
+            span_end(h, sp);
+            CK_LAUNCH();
+            ++h->upd_launches[TC_FP32];
         }
         if (M) {
             const int rc = mxp_updates(h, *M, D.mx, k, spans);
@@ -549,6 +574,7 @@ void fill_stats(tc_handle h, const Plan &P, const MxpPlan *M, tc_stats *stats, d
     stats->update_flops[0] = P.update_flops[0];
     if (M)
         for (int p = 1; p < 4; ++p) stats->update_flops[p] = M->flops[p];
+    stats->update_flops[1] += P.update_flops[1];
     stats->trsm_flops = P.trsm_flops;
     stats->potrf_flops = P.potrf_flops;
     stats->kernel_launches = h->launches - launches0;

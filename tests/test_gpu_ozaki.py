@@ -124,3 +124,51 @@ def test_full_size_ar1_closed_form_n65536_emulated(HZ):
     idx = (ti * (ti + 1) // 2 + tj) * b * b + (cols % b) * b + (rows % b)
     got = L[to_dev(idx)].cpu().numpy()
     assert np.max(np.abs(got - np.exp(logcum[rows] - logcum[cols]) * c[cols])) < 1e-10
+
+
+@pytest.mark.parametrize("n,b,seed", [(1024, 128, 1), (2048, 256, 2)])
+def test_mixed_precision_integer_factor_exact_emulated(n, b, seed):
+    rng = np.random.default_rng(seed + 50)
+    L = np.tril(rng.integers(-1, 2, (n, n)).astype(np.float64), -1) + np.eye(n)
+    nt = n // b
+    pm = np.zeros((nt, nt), dtype=np.uint8)
+    for i in range(nt):
+        for j in range(i):
+            pm[i, j] = rng.integers(0, 4)
+    with tc.Handle(0, fp64_mode=1) as H:
+        At = to_dev(pack_padded(L @ L.T, b))
+        st = tc.tc_stats()
+        assert tc.tile_chol_factor(H.h, n, b, At, pm.reshape(-1), st) == 0
+        Lg = torch.empty_like(At)
+        tc.tile_chol_get_factor(H.h, Lg)
+    assert np.array_equal(unpack_lower(Lg, n, b), L)
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_mixed_precision_emulated_matches_emulation_oracle(eps):
+    n, b = 2048, 256
+    A = oracle.matern(inputs.uniform_points(n, 31, morton=True), 1.0, 0.03, 1.5, 1e-4)
+    nt = n // b
+    with tc.Handle(0, fp64_mode=1) as H:
+        At = to_dev(pack_padded(A, b))
+        pm = np.empty(nt * nt, dtype=np.uint8)
+        tc.tile_chol_precision_map(H.h, n, b, At, eps, 1, 4, pm)
+        st = tc.tc_stats()
+        assert tc.tile_chol_factor(H.h, n, b, At, pm, st) == 0
+        Lt = torch.empty_like(At)
+        tc.tile_chol_get_factor(H.h, Lt)
+        ld = tc.tile_chol_logdet(H.h)
+    pm = pm.reshape(nt, nt)
+    Lg = unpack_lower(Lt, n, b)
+    Lo, _ = oracle.mxp_cholesky(A, b, pm)
+    normA = np.linalg.norm(A)
+    for i in range(nt):
+        for j in range(i + 1):
+            p = int(pm[i, j]) if i != j else 0
+            d = np.abs(Lg[i*b:(i+1)*b, j*b:(j+1)*b] - Lo[i*b:(i+1)*b, j*b:(j+1)*b]).max()
+            ref = np.abs(Lo[i*b:(i+1)*b, j*b:(j+1)*b]).max()
+            assert d <= 2.0 * oracle.UNIT_ROUNDOFF[p] * ref + 8 * eps * normA / nt, (i, j, p, d, ref)
+    be_g = np.linalg.norm(A - Lg @ Lg.T) / normA
+    be_o = np.linalg.norm(A - Lo @ Lo.T) / normA
+    assert be_g <= 10 * eps and be_g <= 4 * be_o + 1e-13
+    assert abs(ld - oracle.logdet(Lo)) <= 1e-6 * abs(oracle.logdet(Lo)) + n * eps
