@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fp64_n65536", choices=sorted(inputs.WORKLOADS) + ["batched"])
     ap.add_argument("--count", type=int, default=512, help="batched workload: number of matrices")
-    ap.add_argument("--fp64-mode", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1],
                     help="FP64 updates: 0 DFMA pipe, 1 emulated on FP8 tensor cores (exact digit planes)")
     ap.add_argument("--n", type=int, default=0, help="override n (smaller quick runs)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -389,7 +389,7 @@ def run_batched(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    H = tc.Handle(local, stream=stream.cuda_stream)
+    H = tc.Handle(local, stream=stream.cuda_stream, fp64_mode=args.fp64_mode)
     bw = inputs.batched_workload(args.count, 5 + 1000 * rank)
     ns = bw.ns
     pts = [torch.from_numpy(bw.points(i)).to(dev) for i in range(len(ns))]
