@@ -76,8 +76,8 @@ typedef struct {
                                       3 x TF32 tensor-core products;
                                    1: both on the FP8 tensor cores through exact base-16
                                       digit planes of every final tile (14 planes for FP64
-                                      outputs: normwise FP64 accuracy; 8 for FP32 outputs:
-                                      below 2^-32 of the tile scale); needs 14 b^2 extra
+                                      outputs: normwise FP64 accuracy; 10 for FP32 outputs:
+                                      below 2^-40 of the tile scale); needs 14 b^2 extra
                                       bytes per lower tile and a tile size multiple of 128 */
     int reserved[7];
 } tc_config;

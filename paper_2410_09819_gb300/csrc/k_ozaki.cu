@@ -151,8 +151,9 @@ __device__ __forceinline__ void z_ld16(uint32_t taddr, float (&v)[16]) {
 
 // One CTA = one 128 x 32 block of one output tile: C -= sum_{n<k} X_n Y_n^T with X_n the
 // tiles (m, n) and Y_n the tiles (k, n), through their first SU digit planes (SU = 14 for FP64
-// outputs; SU = 8, i.e. pairs with s + t <= 9 and a truncation below 2^-32 of the tile scale,
-// for FP32 outputs).
+// outputs; SU = 10, i.e. pairs with s + t <= 11 and a truncation below 2^-40 of the tile scale,
+// for FP32 outputs: with 8 planes the truncation, which is relative to the operand tile's largest
+// entry, cost 50x in the factor's backward error at eps_high = 1e-9 on Matern matrices).
 template <int SU>
 __global__ void __launch_bounds__(ZTHREADS, 1)
 k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY, const ZArgs args) {
@@ -358,11 +359,11 @@ void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *ite
     const size_t smem = zgemm_smem_bytes();
     if (!attr) {
         cudaFuncSetAttribute(k_zgemm<14>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     ZArgs a{items, exps, k, b, err};
-    if (planes == 8) k_zgemm<8><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
+    if (planes == 10) k_zgemm<10><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
     else k_zgemm<14><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
 }
 

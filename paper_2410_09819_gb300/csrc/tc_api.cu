@@ -115,7 +115,7 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 for (int m = k; m < M.nt; ++m) {
                     const bool fp64 = (m == k) || !M.mixed || M.map[(size_t)m * M.nt + k] == TC_FP64;
                     if (!fp64 && zmode && M.map[(size_t)m * M.nt + k] == TC_FP32) {
-                        // FP32 output: 8 digit planes of each operand, FP64 running sums
+                        // FP32 output: 10 digit planes of each operand, FP64 running sums
                         double *Cp = T(M, m, k);
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
                         for (int bn = 0; bn < b / 32; ++bn)
@@ -501,7 +501,7 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
         }
         if (C.ny) {
             const int sp = spans ? span_begin(h, CAT_UPD32) : -1;
-            launch_zgemm(h->map_zx, h->map_zy, D.zitems32 + C.y0, C.ny, D.zexps, k, b, status + 1, h->s, 8);
+            launch_zgemm(h->map_zx, h->map_zy, D.zitems32 + C.y0, C.ny, D.zexps, k, b, status + 1, h->s, 10);
             span_end(h, sp);
             CK_LAUNCH();
             ++h->upd_launches[TC_FP32];
