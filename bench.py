@@ -223,6 +223,13 @@ def run_ours(args, ws, rank, local):
                 "peak_source": f"ALU: 152 SMs x 4 FP64 flop/clk x {pk_kind} max SM clock",
                 "update_share_of_step": (upd_ms / 1e3) / t if t > 0 else None}
 
+    # accuracy of a mixed-precision factorization against the FP64 one (outside the timed region)
+    accuracy = None
+    if w.mixed:
+        ld_mxp = tc.tile_chol_logdet(H.h)
+        ll_ref_mxp, berr_mxp = tc.tile_chol_loglik_refined(H.h, y, 5, 1e-14)
+        stash = (ld_mxp, ll, ll_ref_mxp, berr_mxp)
+
     # end to end: the same step through host (pinned) buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -256,6 +263,21 @@ def run_ours(args, ws, rank, local):
                "d2h_bytes_per_step": d2h, "loglik_matches_device": bool(abs(ll_h - ll) <= 1e-9 * abs(ll))}
         del Ah
 
+    if w.mixed:
+        # FP64 reference: the same matrix factored with every tile in FP64 (emulated updates)
+        src = Ah if not args.no_e2e else A
+        info = tc.tile_chol_factor(H.h, n, b, src, None, None)
+        if info == 0:
+            ld64 = tc.tile_chol_logdet(H.h)
+            ll64, berr64 = tc.tile_chol_loglik_refined(H.h, y, 5, 1e-14)
+            ld_mxp, ll_plain, ll_ref_mxp, berr_mxp = stash
+            accuracy = {"loglik_fp64": ll64, "loglik_mxp": ll_plain, "loglik_mxp_refined": ll_ref_mxp,
+                        "loglik_rel_err": abs(ll_plain - ll64) / abs(ll64),
+                        "loglik_refined_rel_err": abs(ll_ref_mxp - ll64) / abs(ll64),
+                        "logdet_fp64": ld64, "logdet_mxp": ld_mxp, "kl_divergence": 0.5 * (ld_mxp - ld64),
+                        "solve_berr_mxp": berr_mxp, "solve_berr_fp64": berr64,
+                        "reference": "same matrix, all-FP64 map, emulated FP64 updates, refined solve"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, min(args.cpu_sample, n), pts)
@@ -275,6 +297,7 @@ def run_ours(args, ws, rank, local):
                        "step": "map+factor+solve(1 RHS, <=2 refinement)+loglik" if w.mixed
                        else "factor+solve(1 RHS, <=2 refinement)+loglik"},
             "roofline": roofline,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

@@ -207,6 +207,16 @@ int tile_chol_logdet(tc_handle h, double *logdet_out);
 int tile_chol_loglik(tc_handle h, const double *y, double *loglik_out);
 
 /*
+ * Eq. 1 with the quadratic form taken from a refined solve: y^T Sigma^{-1} y = y^T x where
+ * A x = y is solved as tile_chol_solve does (up to max_refine FP64 refinement steps until the
+ * normwise backward error is <= target_berr), so a mixed-precision factor still gives the
+ * quadratic term to FP64 accuracy; log|A| comes from the factor.  y: n doubles, host or
+ * device.  berr_out (optional): the solve's final backward error.
+ */
+int tile_chol_loglik_refined(tc_handle h, const double *y, int max_refine, double target_berr,
+                             double *loglik_out, double *berr_out);
+
+/*
  * Copy the last factor out as FP64 values of the stored tiles (tile layout; upper
  * triangles of diagonal tiles and padding are written as 0).  L_tiles: host or device.
  */

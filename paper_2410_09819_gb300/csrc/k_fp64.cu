@@ -673,6 +673,23 @@ void launch_colmax_abs(const double *V, int64_t ld, int64_t n, int ncols, double
 void launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n, int ncols, cudaStream_t s) {
     k_axpy_cols<<<dim3(64, ncols), 256, 0, s>>>(X, ldx, D, ldd, n);
 }
+__global__ void __launch_bounds__(1024) k_dot(const double *u, const double *v, int64_t n, double *out) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) s = fma(u[i], v[i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+void launch_dot(const double *u, const double *v, int64_t n, double *out, cudaStream_t s) {
+    k_dot<<<1, 1024, 0, s>>>(u, v, n, out);
+}
+
 void launch_dot_self(const double *v, int64_t n, double *out, cudaStream_t s) {
     k_dot_self<<<1, 1024, 0, s>>>(v, n, out);
 }

@@ -1029,6 +1029,35 @@ int tile_chol_loglik(tc_handle h, const double *y, double *loglik_out) {
     return TC_OK;
 }
 
+int tile_chol_loglik_refined(tc_handle h, const double *y, int max_refine, double target_berr, double *loglik_out,
+                             double *berr_out) {
+    if (!h || !y || !loglik_out) return TC_ERR_ARG;
+    if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");
+    CK(cudaSetDevice(h->device));
+    const int64_t n = h->n;
+    DevBuf xy;
+    int rc = ensure(h, xy, (size_t)2 * n * sizeof(double));
+    if (rc) return rc;
+    double *x = static_cast<double *>(xy.p), *yd = x + n;
+    CK(cudaMemcpyAsync(yd, y, n * sizeof(double), cudaMemcpyDefault, h->s));
+    tc_stats st;
+    if ((rc = tile_chol_solve(h, 1, yd, n, x, n, max_refine, target_berr, &st))) {
+        release(xy);
+        return rc;
+    }
+    double *sc = static_cast<double *>(h->scratch.p);
+    launch_dot(yd, x, n, sc, h->s);
+    CK_LAUNCH();
+    double quad = 0.0;
+    CK(cudaMemcpyAsync(&quad, sc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    release(xy);
+    const double two_pi = 6.283185307179586476925286766559;
+    *loglik_out = -0.5 * (double)n * std::log(two_pi) - 0.5 * h->logdet - 0.5 * quad;
+    if (berr_out) *berr_out = st.berr;
+    return TC_OK;
+}
+
 int tile_chol_get_factor(tc_handle h, double *L_tiles) {
     if (!h || !L_tiles) return TC_ERR_ARG;
     if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");

@@ -113,6 +113,7 @@ void launch_symv_resid(const double *A, int nt, int b, int64_t n, const double *
 void launch_colmax_abs(const double *V, int64_t ld, int64_t n, int ncols, double *out, cudaStream_t s);
 void launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
 void launch_dot_self(const double *v, int64_t n, double *out, cudaStream_t s);
+void launch_dot(const double *u, const double *v, int64_t n, double *out, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers (k_gen.cu)
 void launch_matern(double *A, int64_t n, int b, int nt, const double *pts, double sigma2,

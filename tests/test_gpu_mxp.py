@@ -157,3 +157,26 @@ def test_mxp_solve_refines_to_fp64_accuracy(H):
     # the log-likelihood of the MxP factor: relative error of order eps_high
     assert abs(ll - ref) <= 1e-5 * abs(ref)
     assert math.isfinite(ll)
+
+
+def test_refined_loglik_recovers_fp64_quadratic_form(H):
+    n, b = 1024, 128
+    pts = inputs.uniform_points(n, 31, morton=True)
+    A = oracle.matern(pts, 1.0, 0.02, 0.5, 1e-4)
+    nt = n // b
+    At = to_dev(pack_padded(A, b))
+    pm = np.empty(nt * nt, dtype=np.uint8)
+    tc.tile_chol_precision_map(H.h, n, b, At, 1e-5, 1, 4, pm)
+    assert tc.tile_chol_factor(H.h, n, b, At, pm) == 0
+    y = inputs.gaussian(n, 1, seed=12)[:, 0].copy()
+    ll_plain = tc.tile_chol_loglik(H.h, to_dev(y))
+    ll_ref, berr = tc.tile_chol_loglik_refined(H.h, to_dev(y), 10, 1e-14)
+    ld = tc.tile_chol_logdet(H.h)
+    Lo = oracle.cholesky(A)
+    ll64 = oracle.loglik(Lo, y)
+    # the quadratic term of Eq. 1: -2 (ll + n/2 log 2 pi + logdet/2)
+    quad = lambda ll, l: -2.0 * (ll + 0.5 * n * math.log(2 * math.pi) + 0.5 * l)
+    q64 = quad(ll64, oracle.logdet(Lo))
+    assert abs(quad(ll_ref, ld) - q64) <= 1e-10 * abs(q64)
+    assert berr <= 1e-14
+    assert abs(quad(ll_plain, ld) - q64) > abs(quad(ll_ref, ld) - q64)
