@@ -261,11 +261,10 @@ def run_ours(args, ws, rank, local):
         d2h = n * 8 + 8
         e2e = {"value": ws * flops / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "loglik_matches_device": bool(abs(ll_h - ll) <= 1e-9 * abs(ll))}
-        del Ah
 
     if w.mixed:
         # FP64 reference: the same matrix factored with every tile in FP64 (emulated updates)
-        src = Ah if not args.no_e2e else A
+        src = Ah if not args.no_e2e else A          # the e2e leg moved A to pinned host memory
         info = tc.tile_chol_factor(H.h, n, b, src, None, None)
         if info == 0:
             ld64 = tc.tile_chol_logdet(H.h)
@@ -277,6 +276,9 @@ def run_ours(args, ws, rank, local):
                         "logdet_fp64": ld64, "logdet_mxp": ld_mxp, "kl_divergence": 0.5 * (ld_mxp - ld64),
                         "solve_berr_mxp": berr_mxp, "solve_berr_fp64": berr64,
                         "reference": "same matrix, all-FP64 map, emulated FP64 updates, refined solve"}
+
+    if not args.no_e2e:
+        del Ah
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
