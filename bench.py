@@ -46,8 +46,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fp64_n65536", choices=sorted(inputs.WORKLOADS) + ["batched"])
     ap.add_argument("--count", type=int, default=512, help="batched workload: number of matrices")
-    ap.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1],
-                    help="FP64 updates: 0 DFMA pipe, 1 emulated on FP8 tensor cores (exact digit planes)")
+    ap.add_argument("--fp64-mode", type=int, default=2, choices=[0, 1, 2],
+                    help="FP64 updates: 0 DFMA pipe, 1 emulated on FP8 tensor cores (exact digit planes), "
+                         "2 as 1 plus inverse-based TRSM in mixed precision")
     ap.add_argument("--n", type=int, default=0, help="override n (smaller quick runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -215,7 +216,7 @@ def run_ours(args, ws, rank, local):
     achieved = (upd_flops / (upd_ms / 1e3) / 1e12) if upd_ms > 0 else None
     sha = kernel_source_sha()
     traffic = profiled_traffic("dgemm_update_fp64_n65536", sha) if (n == 65536 and not w.mixed) else None
-    if args.fp64_mode == 1:
+    if args.fp64_mode >= 1:
         roofline = zgemm_roofline(upd_flops, upd_ms, t)
     else:
         roofline = {"kernel": "k_dgemm_update", "bound": "alu", "achieved": achieved, "peak": round(fp64_peak, 4),

@@ -78,7 +78,12 @@ typedef struct {
                                       digit planes of every final tile (14 planes for FP64
                                       outputs: normwise FP64 accuracy; 10 for FP32 outputs:
                                       below 2^-40 of the tile scale); needs 14 b^2 extra
-                                      bytes per lower tile and a tile size multiple of 128 */
+                                      bytes per lower tile and a tile size multiple of 128;
+                                   2: as 1, and in a mixed-precision factorization of one
+                                      matrix the TRSMs run as L_mk = C_mk L_kk^{-T} on the
+                                      emulated engine (L_kk^{-T} by FP64 substitution on the
+                                      identity); the error kappa(L_kk) u of that form is far
+                                      below a mixed-precision factor's accuracy level */
     int reserved[7];
 } tc_config;
 

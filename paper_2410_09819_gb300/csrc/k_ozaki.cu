@@ -80,6 +80,7 @@ struct ZArgs {
     const int *exps;
     int k, b;
     int *err;
+    int assign;         // 0: C -= sum X Y^T;  1: C = sum X Y^T
 };
 
 __device__ __forceinline__ uint32_t z_smem(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -329,7 +330,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
 #pragma unroll
             for (int j = 0; j < ZBN; ++j) {
                 const int col = it.bn * ZBN + j;
-                it.C[(int64_t)col * b + row] -= run[j];
+                double *c = it.C + (int64_t)col * b + row;
+                *c = args.assign ? run[j] : *c - run[j];
             }
         }
     }
@@ -338,6 +340,70 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
+
+
+// Digit planes of one b x b matrix at src (column-major; row-major when transpose != 0)
+// into slot dst of the pool, exponent from *amax.
+__global__ void __launch_bounds__(256)
+k_digits_src(const double *src, int b, int transpose, int dst, const double *amax, uint8_t *pool, int *exps) {
+    __shared__ double S[32][33];
+    const double am = *amax;
+    int e = 0;
+    if (am > 0.0) {
+        int ex;
+        const double f = frexp(am, &ex);
+        e = (f == 0.5) ? ex - 1 : ex;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) exps[dst] = e;
+    const int nbc = b / 32;
+    const int64_t bb = (int64_t)b * b;
+    uint8_t *P = pool + (int64_t)dst * ZS * bb;
+    for (int blk = blockIdx.x; blk < nbc * nbc; blk += gridDim.x) {
+        const int r0 = (blk % nbc) * 32, c0 = (blk / nbc) * 32;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 1024; idx += 256) {
+            const int r = idx & 31, c = idx >> 5;
+            S[r][c] = transpose ? src[(int64_t)(r0 + r) * b + c0 + c] : src[(int64_t)(c0 + c) * b + r0 + r];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 1024; idx += 256) {
+            const int c = idx & 31, r = idx >> 5;
+            double v = ldexp(S[r][c], -e);
+            const int64_t o = (int64_t)(r0 + r) * b + c0 + c;
+#pragma unroll
+            for (int s = 0; s < ZS; ++s) {
+                v = v * 16.0;
+                const double d = rint(v);
+                v = v - d;
+                P[(int64_t)s * bb + o] = (uint8_t)__nv_cvt_double_to_fp8(d, __NV_SATFINITE, __NV_E4M3);
+            }
+        }
+    }
+}
+
+__global__ void k_amax_ptr(const double *src, int64_t count, double *out) {
+    double m = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(src[e]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long *>(out), (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_set_identity(double *T, int b) {
+    const int64_t bb = (int64_t)b * b;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb; e += (int64_t)gridDim.x * blockDim.x)
+        T[e] = (e % b == e / b) ? 1.0 : 0.0;
+}
+
+void launch_digits_src(const double *src, int b, int transpose, int dst, const double *amax, uint8_t *pool, int *exps,
+                       cudaStream_t s) {
+    k_digits_src<<<64, 256, 0, s>>>(src, b, transpose, dst, amax, pool, exps);
+}
+void launch_amax_ptr(const double *src, int64_t count, double *out, cudaStream_t s) {
+    k_amax_ptr<<<64, 256, 0, s>>>(src, count, out);
+}
+void launch_set_identity(double *T, int b, cudaStream_t s) { k_set_identity<<<64, 256, 0, s>>>(T, b); }
 
 // ------------------------------------------------------------------------- host side
 // map over the digit pool: rows = tiles * 14 * b, b bytes each; box 128 bytes x box_rows
@@ -353,7 +419,7 @@ void launch_digits(const double *W, int b, const int *tiles, int ntiles, const d
 }
 
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
-                  int b, int *err, cudaStream_t s, int planes) {
+                  int b, int *err, cudaStream_t s, int planes, int assign) {
     if (nitems <= 0 || k <= 0) return;
     static bool attr = false;
     const size_t smem = zgemm_smem_bytes();
@@ -362,7 +428,7 @@ void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *ite
         cudaFuncSetAttribute(k_zgemm<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    ZArgs a{items, exps, k, b, err};
+    ZArgs a{items, exps, k, b, err, assign};
     if (planes == 10) k_zgemm<10><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
     else k_zgemm<14><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
 }

@@ -35,7 +35,8 @@ struct PotrfStep {
 
 struct ColPlan {
     int z0 = 0, nz = 0;          // emulated-FP64 update items
-    int y0 = 0, ny = 0;          // emulated FP32-output update items (8 digit planes)
+    int y0 = 0, ny = 0;          // emulated FP32-output update items (10 digit planes)
+    int v0 = 0, nv = 0;          // TRSM as an emulated product with L_kk^{-1} (assign mode)
     int dg0 = 0, ndg = 0;        // tiles whose digit planes are made after the column's TRSMs
     int it0 = 0, nit = 0;        // FP64 update items
     int red0 = 0, nred = 0;      // split-K reductions
@@ -50,7 +51,8 @@ struct Plan {
     std::vector<TStrip> strips;
     std::vector<PEntry> pentries;
     std::vector<LEntry> lentries;
-    std::vector<ZItem> zitems, zitems32;
+    std::vector<ZItem> zitems, zitems32, zinv;
+    bool inv_trsm = false;
     std::vector<int> dtiles;
     std::vector<ColPlan> cols;
     int64_t Ttot = 0;
@@ -91,7 +93,10 @@ Plan build_plan(tc_handle h, double *W, int *status) {
         P.Ttot = std::max<int64_t>(P.Ttot, M.tile0 + tidx(M.nt, 0));
     }
     P.cols.resize(P.ntmax);
-    const bool zmode = h->cfg.fp64_mode == 1;
+    const bool zmode = h->cfg.fp64_mode >= 1;
+    // explicit-inverse TRSM (fp64_mode 2): mixed precision only (its error, kappa(L_kk) u, is far
+    // below the accuracy level of a mixed-precision factorization), single matrix (one scratch)
+    P.inv_trsm = h->cfg.fp64_mode == 2 && h->mats.size() == 1 && h->mats[0].mixed;
     auto T = [&](const MatDesc &M, int i, int j) { return W + (M.tile0 + tidx(i, j)) * bb; };
     const int nmat = (int)h->mats.size();
     for (int mi = 0; mi < nmat; ++mi) {
@@ -160,6 +165,19 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 if (M.nt > k)
                     for (int m = k + 1; m < M.nt; ++m) P.dtiles.push_back((int)(M.tile0 + tidx(m, k)));
         C.ndg = (int)P.dtiles.size() - C.dg0;
+        // TRSM of a mixed-precision column as C_mk L_kk^{-T} on the emulated engine (one matrix)
+        C.v0 = (int)P.zinv.size();
+        if (P.inv_trsm) {
+            const MatDesc &M = h->mats[0];
+            for (int m = k + 1; m < M.nt; ++m) {
+                double *Cp = T(M, m, k);
+                for (int bn = 0; bn < b / 32; ++bn)
+                    for (int bm = 0; bm < b / 128; ++bm)
+                        P.zinv.push_back({Cp, (int)(M.tile0 + tidx(m, k)), (int)(M.tile0 + tidx(k, k)), (uint16_t)bm,
+                                          (uint16_t)bn});
+            }
+        }
+        C.nv = (int)P.zinv.size() - C.v0;
         // 2. blocked POTRF of the diagonal tiles: per 64-panel, the block, its panel and the
         //    trailing update, each one launch over all matrices
         for (int jb = 0; jb < b / 64; ++jb) {
@@ -196,7 +214,8 @@ Plan build_plan(tc_handle h, double *W, int *status) {
             if (M.nt <= k) continue;
             P.potrf_flops += (double)b * b * b / 3.0;
             for (int m = k + 1; m < M.nt; ++m) {
-                for (int r0 = 0; r0 < b; r0 += 64) P.strips.push_back({T(M, m, k), T(M, k, k), status + 2 + mi, r0});
+                if (!P.inv_trsm)
+                    for (int r0 = 0; r0 < b; r0 += 64) P.strips.push_back({T(M, m, k), T(M, k, k), status + 2 + mi, r0});
                 P.trsm_flops += (double)b * b * b;
             }
         }
@@ -229,7 +248,7 @@ struct MxpPlan {
 
 MxpPlan build_mxp(tc_handle h, double *W) {
     MxpPlan X;
-    const bool zmode = h->cfg.fp64_mode == 1;   // FP32 outputs then run on digit planes
+    const bool zmode = h->cfg.fp64_mode >= 1;   // FP32 outputs then run on digit planes
     const int b = h->b;
     const int64_t bb = (int64_t)b * b;
     int ntmax = 0;
@@ -396,7 +415,8 @@ struct PlanDev {
     const TStrip *strips;
     const PEntry *pentries;
     const LEntry *lentries;
-    const ZItem *zitems = nullptr, *zitems32 = nullptr;
+    const ZItem *zitems = nullptr, *zitems32 = nullptr, *zinv = nullptr;
+    double *zamax2 = nullptr;
     const int *dtiles = nullptr;
     int *zexps = nullptr;
     double *zamax = nullptr;
@@ -428,23 +448,28 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
     D.pentries = reinterpret_cast<const PEntry *>(base + op);
     D.lentries = reinterpret_cast<const LEntry *>(base + ol);
     if ((rc = ensure(h, h->partials, (size_t)std::max(1, P.max_parts) * 4096 * sizeof(double)))) return rc;
-    if (!P.zitems.empty() || !P.zitems32.empty() || !P.dtiles.empty()) {
+    if (!P.zitems.empty() || !P.zitems32.empty() || !P.zinv.empty() || !P.dtiles.empty()) {
         // digit planes (14 per tile), exponents, amax, the Z items and the digit tile lists
         const int64_t Tt = P.Ttot;
         const size_t bb = (size_t)h->b * h->b;
         if ((rc = ensure(h, h->dpool, (size_t)Tt * 14 * bb))) return rc;
         const size_t oz = 0, oy = align_up(P.zitems.size() * sizeof(ZItem));
-        const size_t od = align_up(oy + P.zitems32.size() * sizeof(ZItem)), oe = align_up(od + P.dtiles.size() * 4);
-        const size_t oa = align_up(oe + Tt * 4), zt = align_up(oa + Tt * 8);
+        const size_t ov = align_up(oy + P.zitems32.size() * sizeof(ZItem));
+        const size_t od = align_up(ov + P.zinv.size() * sizeof(ZItem)), oe = align_up(od + P.dtiles.size() * 4);
+        const size_t oa = align_up(oe + Tt * 4), oa2 = align_up(oa + Tt * 8), zt = align_up(oa2 + Tt * 8);
+        if (P.inv_trsm && (rc = ensure(h, h->invbuf, bb * sizeof(double)))) return rc;
         if ((rc = ensure(h, h->ztab, zt))) return rc;
         std::vector<char> zh(zt, 0);
         if (!P.zitems.empty()) memcpy(zh.data() + oz, P.zitems.data(), P.zitems.size() * sizeof(ZItem));
         if (!P.zitems32.empty()) memcpy(zh.data() + oy, P.zitems32.data(), P.zitems32.size() * sizeof(ZItem));
+        if (!P.zinv.empty()) memcpy(zh.data() + ov, P.zinv.data(), P.zinv.size() * sizeof(ZItem));
         if (!P.dtiles.empty()) memcpy(zh.data() + od, P.dtiles.data(), P.dtiles.size() * 4);
         CK(cudaMemcpy(h->ztab.p, zh.data(), zt, cudaMemcpyHostToDevice));
         char *zb = static_cast<char *>(h->ztab.p);
         D.zitems = reinterpret_cast<const ZItem *>(zb + oz);
         D.zitems32 = reinterpret_cast<const ZItem *>(zb + oy);
+        D.zinv = reinterpret_cast<const ZItem *>(zb + ov);
+        D.zamax2 = reinterpret_cast<double *>(zb + oa2);
         D.dtiles = reinterpret_cast<const int *>(zb + od);
         D.zexps = reinterpret_cast<int *>(zb + oe);
         D.zamax = reinterpret_cast<double *>(zb + oa);
@@ -473,6 +498,7 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
     CK_LAUNCH();
     CK(cudaMemsetAsync(status, 0, (2 + nmat) * sizeof(int), h->s));
     if (D.zamax) CK(cudaMemsetAsync(D.zamax, 0, P.Ttot * sizeof(double), h->s));
+    if (D.zamax2) CK(cudaMemsetAsync(D.zamax2, 0, P.Ttot * sizeof(double), h->s));
     if (M) {
         CK(cudaMemsetAsync(D.mx.amaxL, 0, M->T * sizeof(double), h->s));
         CK(cudaMemsetAsync(D.mx.amaxS, 0, M->T * sizeof(double), h->s));
@@ -522,6 +548,30 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
             }
         }
         span_end(h, sp_potrf);
+        if (C.nv) {
+            // L_mk = C_mk L_kk^{-T}: L_kk^{-T} by substitution on the identity (FP64), then digit
+            // planes of L_kk^{-1} and of every C_mk, and one emulated product per tile
+            const int sp = spans ? span_begin(h, CAT_TRSM) : -1;
+            const MatDesc &Md = h->mats[0];
+            const int gkk = (int)(Md.tile0 + tidx(k, k));
+            double *inv = static_cast<double *>(h->invbuf.p);
+            uint8_t *pool = static_cast<uint8_t *>(h->dpool.p);
+            launch_set_identity(inv, b, h->s);
+            CK_LAUNCH();
+            launch_trsm_tile(inv, W + tidx(k, k) * bb, b, b, nullptr, h->s);
+            CK_LAUNCH();
+            launch_amax_ptr(inv, bb, D.zamax2 + gkk, h->s);
+            CK_LAUNCH();
+            launch_digits_src(inv, b, 1, gkk, D.zamax2 + gkk, pool, D.zexps, h->s);
+            CK_LAUNCH();
+            launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, D.zamax2, h->s);
+            CK_LAUNCH();
+            launch_digits(W, b, D.dtiles + C.dg0, C.ndg, D.zamax2, pool, D.zexps, h->s);
+            CK_LAUNCH();
+            launch_zgemm(h->map_zx, h->map_zy, D.zinv + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1);
+            CK_LAUNCH();
+            span_end(h, sp);
+        }
         if (C.nst) {
             const int sp = spans ? span_begin(h, CAT_TRSM) : -1;
             launch_trsm_strips(D.strips + C.st0, C.nst, b, b, nullptr, h->s);
@@ -704,7 +754,8 @@ void tc_destroy(tc_handle h) {
     cudaSetDevice(h->device);
     if (h->s) cudaStreamSynchronize(h->s);
     for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq,
-                      &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab, &h->logdiag, &h->dpool, &h->ztab})
+                      &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab, &h->logdiag, &h->dpool, &h->ztab,
+                      &h->invbuf})
         release(*d);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     release(h->bstage);
@@ -845,7 +896,7 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
     }
     for (uint8_t v : M.map) M.mixed |= (v != TC_FP64);
     if (M.mixed && b % 128) return set_err(h, TC_ERR_UNSUPPORTED, "mixed precision needs a tile size that is a multiple of 128");
-    if (h->cfg.fp64_mode == 1 && b % 128)
+    if (h->cfg.fp64_mode >= 1 && b % 128)
         return set_err(h, TC_ERR_UNSUPPORTED, "emulated FP64 updates need a tile size that is a multiple of 128");
     if ((rc = ensure(h, h->W, bytes))) return rc;
     // the caller's A stays readable for refinement: reference it on the device or copy it

@@ -54,7 +54,7 @@ struct tc_handle_s {
     DevBuf mxtab;
     CUtensorMap map_hi{}, map_lo{}, map16{}, map8{};
     // emulated FP64 updates: digit planes, their tables and tensor maps
-    DevBuf dpool, ztab;
+    DevBuf dpool, ztab, invbuf;
     CUtensorMap map_zx{}, map_zy{};
     // matrices of the last (batched) factorization
     std::vector<MatDesc> mats;

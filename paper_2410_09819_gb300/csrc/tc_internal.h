@@ -132,7 +132,11 @@ size_t zgemm_smem_bytes();
 void launch_digits(const double *W, int b, const int *tiles, int ntiles, const double *amax, uint8_t *pool, int *exps,
                    cudaStream_t s);
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
-                  int b, int *err, cudaStream_t s, int planes = 14);
+                  int b, int *err, cudaStream_t s, int planes = 14, int assign = 0);
+void launch_digits_src(const double *src, int b, int transpose, int dst, const double *amax, uint8_t *pool, int *exps,
+                       cudaStream_t s);
+void launch_amax_ptr(const double *src, int64_t count, double *out, cudaStream_t s);
+void launch_set_identity(double *T, int b, cudaStream_t s);
 int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_rows);
 
 // ------------------------------------------------------------------ launchers (k_mxp.cu)

@@ -172,3 +172,37 @@ def test_mixed_precision_emulated_matches_emulation_oracle(eps):
     be_o = np.linalg.norm(A - Lo @ Lo.T) / normA
     assert be_g <= 10 * eps and be_g <= 4 * be_o + 1e-13
     assert abs(ld - oracle.logdet(Lo)) <= 1e-6 * abs(oracle.logdet(Lo)) + n * eps
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_mixed_precision_inverse_trsm_mode(eps):
+    n, b = 2048, 256
+    A = oracle.matern(inputs.uniform_points(n, 31, morton=True), 1.0, 0.03, 1.5, 1e-4)
+    nt = n // b
+    with tc.Handle(0, fp64_mode=2) as H:
+        At = to_dev(pack_padded(A, b))
+        pm = np.empty(nt * nt, dtype=np.uint8)
+        tc.tile_chol_precision_map(H.h, n, b, At, eps, 1, 4, pm)
+        st = tc.tc_stats()
+        assert tc.tile_chol_factor(H.h, n, b, At, pm, st) == 0
+        Lt = torch.empty_like(At)
+        tc.tile_chol_get_factor(H.h, Lt)
+        y = inputs.gaussian(n, 1, seed=4)[:, 0].copy()
+        ll_ref, berr = tc.tile_chol_loglik_refined(H.h, to_dev(y), 10, 1e-14)
+    pm = pm.reshape(nt, nt)
+    Lg = unpack_lower(Lt, n, b)
+    Lo, _ = oracle.mxp_cholesky(A, b, pm)
+    normA = np.linalg.norm(A)
+    for i in range(nt):
+        for j in range(i + 1):
+            p = int(pm[i, j]) if i != j else 0
+            d = np.abs(Lg[i*b:(i+1)*b, j*b:(j+1)*b] - Lo[i*b:(i+1)*b, j*b:(j+1)*b]).max()
+            ref = np.abs(Lo[i*b:(i+1)*b, j*b:(j+1)*b]).max()
+            assert d <= 2.0 * oracle.UNIT_ROUNDOFF[p] * ref + 8 * eps * normA / nt, (i, j, p, d, ref)
+    be_g = np.linalg.norm(A - Lg @ Lg.T) / normA
+    be_o = np.linalg.norm(A - Lo @ Lo.T) / normA
+    assert be_g <= 10 * eps and be_g <= 4 * be_o + 1e-12
+    Lf = oracle.cholesky(A)
+    ll64 = oracle.loglik(Lf, y)
+    assert berr <= 1e-14
+    assert abs(ll_ref - ll64) <= 10 * eps * abs(ll64)
