@@ -421,19 +421,25 @@ def run_batched(args, ws, rank, local):
     pts = [torch.from_numpy(bw.points(i)).to(dev) for i in range(len(ns))]
     eps, nrhs = 1e-7, bw.nrhs
 
+    map_store = {}
+
     def make_inputs(b):
-        A_list, maps = [], []
+        A_list = []
+        sizes = [tc.ntiles(n, b) ** 2 for n in ns]
+        flat = torch.zeros(sum(sizes), dtype=torch.uint8, device=dev)
+        map_store[b] = flat
+        maps = list(torch.split(flat, sizes))
         for i, n in enumerate(ns):
             A = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=dev)
             tc.tc_matern_tiles(H.h, n, b, pts[i], 1.0, bw.ranges[i], bw.nus[i], 1e-4, A)
             A_list.append(A)
-            maps.append(torch.zeros(tc.ntiles(n, b) ** 2, dtype=torch.uint8, device=dev))
         return A_list, maps
 
     def compute_maps(A_list, maps, b):
         for i, n in enumerate(ns):
             tc.tile_chol_precision_map_noalloc(n, b, A_list[i], eps, 0, 4, maps[i], stream.cuda_stream)
-            maps[i][maps[i] == tc.TC_FP32] = tc.TC_FP64
+        flat = map_store[b]
+        flat[flat == tc.TC_FP32] = tc.TC_FP64
 
     best_b, tune = autotune.pick_batched_tile(H, ns, make_inputs)
     b = best_b

@@ -246,9 +246,11 @@ int tile_chol_factor_batched(tc_handle h, int count, const int64_t *n, int b, co
 
 /*
  * Solve A_i X_i = B_i for every matrix of the last batched factorization, with up to
- * max_refine refinement steps per matrix (FP64 residuals with the caller's A_i) until its
- * normwise backward error is <= target_berr.  B[i], X[i]: n_i x nrhs column-major with
- * leading dimension n_i, host or device.  berr_out[count] (optional): final backward errors.
+ * max_refine refinement steps (FP64 residuals with the caller's A_i, every matrix refined
+ * together) until every normwise backward error is <= target_berr.  1 <= nrhs <= 16.
+ * B[i], X[i]: n_i x nrhs column-major with leading dimension n_i, host or device.
+ * berr_out[count] (optional): final backward errors.  Each substitution step is one grouped
+ * launch over all matrices.
  */
 int tile_chol_solve_batched(tc_handle h, int nrhs, const double *const *B, double *const *X, int max_refine,
                             double target_berr, double *berr_out, tc_stats *stats);

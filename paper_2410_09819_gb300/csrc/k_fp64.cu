@@ -613,6 +613,251 @@ void launch_fix_padding_batched(const LEntry *e, int count, int ntmax, int b, cu
     if (count > 0) k_fix_padding_batched<<<dim3(16, ntmax, count), 256, 0, s>>>(e, b);
 }
 
+
+// ------------------------------------------------------------ grouped (batched) solves
+__global__ void __launch_bounds__(256) k_fwd_diag_g(const SDiag *__restrict__ e, double *R, int b) {
+    const SDiag E = e[blockIdx.y];
+    __shared__ double z[4096];
+    __shared__ double red[4][64];
+    __shared__ double blk[64];
+    const double *L = E.L;
+    double *r = R + E.off + blockIdx.x * E.ldr;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < b; i += 256) z[i] = r[i];
+    __syncthreads();
+    const int rr = tid & 63, part = tid >> 6;
+    for (int jb = 0; jb < b / 64; ++jb) {
+        double s = 0.0;
+        for (int l = part; l < jb * 64; l += 4) s += L[(int64_t)l * b + jb * 64 + rr] * z[l];
+        red[part][rr] = s;
+        __syncthreads();
+        if (tid < 64) blk[tid] = z[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+        __syncthreads();
+        for (int jj = 0; jj < 64; ++jj) {
+            if (tid == jj) blk[jj] = blk[jj] / L[(int64_t)(jb * 64 + jj) * b + jb * 64 + jj];
+            __syncthreads();
+            if (tid > jj && tid < 64) blk[tid] -= L[(int64_t)(jb * 64 + jj) * b + jb * 64 + tid] * blk[jj];
+            __syncthreads();
+        }
+        if (tid < 64) z[jb * 64 + tid] = blk[tid];
+        __syncthreads();
+    }
+    for (int i = tid; i < b; i += 256) r[i] = z[i];
+}
+
+__global__ void __launch_bounds__(256) k_fwd_update_g(const SUpd *__restrict__ u, double *R, int b, int nrhs) {
+    const SUpd U = u[blockIdx.x];
+    __shared__ double zs[128][16];
+    __shared__ double red[64][17];
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int c0 = 0; c0 < b; c0 += 128) {
+        __syncthreads();
+        for (int e = tid; e < 128 * nrhs; e += 256) {
+            const int c = e % 128, q = e / 128;
+            zs[c][q] = R[U.src + q * U.ldr + c0 + c];
+        }
+        __syncthreads();
+        for (int c = part; c < 128; c += 4) {
+            const double l = U.L[(int64_t)(c0 + c) * b + U.r0 + rr];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q < nrhs) acc[q] = fma(l, zs[c][q], acc[q]);
+        }
+    }
+    part_reduce_sub(red, acc, nrhs, R + U.dst, U.ldr, 0);
+}
+
+__global__ void __launch_bounds__(256) k_bwd_diag_g(const SDiag *__restrict__ e, double *R, int b) {
+    const SDiag E = e[blockIdx.y];
+    __shared__ double S[64][65];
+    __shared__ double red[4][64];
+    __shared__ double blk[64];
+    const double *L = E.L;
+    double *x = R + E.off + blockIdx.x * E.ldr;
+    const int tid = threadIdx.x;
+    const int rr = tid & 63, part = tid >> 6;
+    for (int jb = b / 64 - 1; jb >= 0; --jb) {
+        double s = 0.0;
+        for (int l0 = (jb + 1) * 64; l0 < b; l0 += 64) {
+            __syncthreads();
+            for (int idx = tid; idx < 4096; idx += 256) {
+                const int lr = idx & 63, rc = idx >> 6;
+                S[rc][lr] = L[(int64_t)(jb * 64 + rc) * b + l0 + lr];
+            }
+            __syncthreads();
+            for (int lr = part; lr < 64; lr += 4) s += S[rr][lr] * x[l0 + lr];
+        }
+        red[part][rr] = s;
+        __syncthreads();
+        if (tid < 64) blk[tid] = x[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int lr = idx & 63, rc = idx >> 6;
+            S[rc][lr] = L[(int64_t)(jb * 64 + rc) * b + jb * 64 + lr];
+        }
+        __syncthreads();
+        for (int jj = 63; jj >= 0; --jj) {
+            if (tid == jj) blk[jj] = blk[jj] / S[jj][jj];
+            __syncthreads();
+            if (tid < jj) blk[tid] -= S[tid][jj] * blk[jj];
+            __syncthreads();
+        }
+        if (tid < 64) x[jb * 64 + tid] = blk[tid];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bwd_update_g(const SUpd *__restrict__ u, double *R, int b, int nrhs) {
+    const SUpd U = u[blockIdx.x];
+    __shared__ double xs[64][16];
+    __shared__ double S[64][65];
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int c0 = 0; c0 < b; c0 += 64) {
+        __syncthreads();
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int c = idx & 63, r = idx >> 6;
+            S[r][c] = U.L[(int64_t)(U.r0 + r) * b + c0 + c];
+        }
+        for (int e = tid; e < 64 * nrhs; e += 256) {
+            const int c = e % 64, q = e / 64;
+            xs[c][q] = R[U.src + q * U.ldr + c0 + c];
+        }
+        __syncthreads();
+        for (int c = part; c < 64; c += 4) {
+            const double l = S[rr][c];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
+        }
+    }
+    part_reduce_sub(reinterpret_cast<double(*)[17]>(&S[0][0]), acc, nrhs, R + U.dst, U.ldr, 0);
+}
+
+__global__ void __launch_bounds__(256)
+k_symv_g(const SRes *__restrict__ rs, int b, const double *X, const double *B, double *R, int nrhs, int absmode) {
+    const SRes Q = rs[blockIdx.x];
+    __shared__ double xs[64][16];
+    __shared__ double S[64][65];
+    const int i = Q.i, r0 = Q.r0;
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    const int64_t bb = (int64_t)b * b;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int j = 0; j < Q.nt; ++j) {
+        const bool lower = j <= i;
+        const double *T = lower ? Q.A + ((int64_t)i * (i + 1) / 2 + j) * bb : Q.A + ((int64_t)j * (j + 1) / 2 + i) * bb;
+        for (int c0 = 0; c0 < b; c0 += 64) {
+            __syncthreads();
+            for (int idx = tid; idx < 4096; idx += 256) {
+                const int lo = idx & 63, hi = idx >> 6;
+                double v;
+                int64_t gr, gc;
+                if (lower) {
+                    v = T[(int64_t)(c0 + hi) * b + r0 + lo];
+                    gr = (int64_t)i * b + r0 + lo; gc = (int64_t)j * b + c0 + hi;
+                    if (gr >= Q.n || gc >= Q.n) v = 0.0;
+                    S[lo][hi] = absmode ? fabs(v) : v;
+                } else {
+                    v = T[(int64_t)(r0 + hi) * b + c0 + lo];
+                    gr = (int64_t)i * b + r0 + hi; gc = (int64_t)j * b + c0 + lo;
+                    if (gr >= Q.n || gc >= Q.n) v = 0.0;
+                    S[hi][lo] = absmode ? fabs(v) : v;
+                }
+            }
+            for (int e = tid; e < 64 * nrhs; e += 256) {
+                const int c = e % 64, q = e / 64;
+                const int64_t g = (int64_t)j * b + c0 + c;
+                xs[c][q] = (g < Q.n) ? (X ? X[Q.xo + q * Q.ldr + g] : 1.0) : 0.0;
+            }
+            __syncthreads();
+            for (int c = part; c < 64; c += 4) {
+                const double l = S[rr][c];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
+            }
+        }
+    }
+    double(*red)[17] = reinterpret_cast<double(*)[17]>(&S[0][0]);
+    for (int p = 0; p < 4; ++p) {
+        __syncthreads();
+        if (part == p)
+            for (int q = 0; q < nrhs; ++q) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < 64 * nrhs; e += 256) {
+        const int r = e % 64, q = e / 64;
+        const int64_t g = (int64_t)i * b + r0 + r;
+        double out = 0.0;
+        if (g < Q.n) out = absmode ? red[r][q] : B[Q.bo + q * Q.ldr + g] - red[r][q];
+        R[Q.ro + q * Q.ldr + g] = out;
+    }
+}
+
+__global__ void k_colmax_g(const SMax *__restrict__ m, const double *V, int nrhs, double *out) {
+    const SMax M = m[blockIdx.y];
+    for (int c = 0; c < nrhs; ++c) {
+        double mx = 0.0;
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < M.n; r += (int64_t)gridDim.x * blockDim.x)
+            mx = fmax(mx, fabs(V[M.off + c * M.ldr + r]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0)
+            atomicMax(reinterpret_cast<unsigned long long *>(out + M.out + c), (unsigned long long)__double_as_longlong(mx));
+    }
+}
+
+__global__ void k_axpy_flat(double *X, const double *D, int64_t count) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        X[e] += D[e];
+}
+
+// one CTA per matrix: out[M.out] = u . v over its n entries (fixed order)
+__global__ void __launch_bounds__(256) k_dots_g(const SMax *__restrict__ m, const double *u, const double *v, double *out) {
+    const SMax M = m[blockIdx.x];
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < M.n; r += 256) s = fma(u[M.off + r], v[M.off + r], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[M.out] = red[0];
+}
+
+void launch_fwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaStream_t s) {
+    if (ne > 0) k_fwd_diag_g<<<dim3(nrhs, ne), 256, 0, s>>>(e, R, b);
+}
+void launch_fwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s) {
+    if (nu > 0) k_fwd_update_g<<<nu, 256, 0, s>>>(u, R, b, nrhs);
+}
+void launch_bwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaStream_t s) {
+    if (ne > 0) k_bwd_diag_g<<<dim3(nrhs, ne), 256, 0, s>>>(e, R, b);
+}
+void launch_bwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s) {
+    if (nu > 0) k_bwd_update_g<<<nu, 256, 0, s>>>(u, R, b, nrhs);
+}
+void launch_symv_g(const SRes *r, int nr, int b, const double *X, const double *B, double *R, int nrhs, int absmode,
+                   cudaStream_t s) {
+    if (nr > 0) k_symv_g<<<nr, 256, 0, s>>>(r, b, X, B, R, nrhs, absmode);
+}
+void launch_colmax_g(const SMax *m, int nm, const double *V, int nrhs, double *out, cudaStream_t s) {
+    if (nm > 0) k_colmax_g<<<dim3(8, nm), 256, 0, s>>>(m, V, nrhs, out);
+}
+void launch_axpy_flat(double *X, const double *D, int64_t count, cudaStream_t s) {
+    k_axpy_flat<<<1024, 256, 0, s>>>(X, D, count);
+}
+void launch_dots_g(const SMax *m, int nm, const double *u, const double *v, double *out, cudaStream_t s) {
+    if (nm > 0) k_dots_g<<<nm, 256, 0, s>>>(m, u, v, out);
+}
+
 // ---------------------------------------------------------------------------- launchers
 void launch_dgemm_update(const DJob *jobs, const DItem *items, int nitems, int ld, double *partials,
                          const int *status, cudaStream_t s) {

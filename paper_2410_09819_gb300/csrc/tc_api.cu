@@ -755,7 +755,7 @@ void tc_destroy(tc_handle h) {
     if (h->s) cudaStreamSynchronize(h->s);
     for (DevBuf *d : {&h->W, &h->Acopy, &h->status, &h->scratch, &h->tables, &h->partials, &h->vec, &h->sumsq,
                       &h->pool_hi, &h->pool_lo, &h->pool16, &h->pool8, &h->mxtab, &h->logdiag, &h->dpool, &h->ztab,
-                      &h->invbuf})
+                      &h->invbuf, &h->stab})
         release(*d);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     release(h->bstage);
@@ -1222,109 +1222,191 @@ int tile_chol_factor_batched(tc_handle h, int count, const int64_t *n, int b, co
     return TC_OK;
 }
 
+// Grouped substitution plan over every matrix of the last batched factorization: per tile
+// column step one launch for all diagonal blocks and one for all off-diagonal updates.
+struct BatchSolvePlan {
+    std::vector<int64_t> off;            // RHS block of matrix i in a buffer (elements)
+    int64_t total = 0;
+    std::vector<SDiag> diag;             // forward steps, then backward steps
+    std::vector<SUpd> upd;
+    std::vector<std::pair<int, int>> fd, fu, bd, bu;   // (first, count) per step
+    std::vector<SRes> res;
+    std::vector<SMax> mx;
+};
+
+static BatchSolvePlan plan_batch_solve(tc_handle h, int nrhs) {
+    BatchSolvePlan S;
+    const int count = (int)h->mats.size(), b = h->b;
+    const int64_t bb = (int64_t)b * b;
+    const double *W = static_cast<const double *>(h->W.p);
+    S.off.assign(count + 1, 0);
+    int ntmax = 0;
+    for (int i = 0; i < count; ++i) {
+        S.off[i + 1] = S.off[i] + (int64_t)h->mats[i].nt * b * nrhs;
+        ntmax = std::max(ntmax, h->mats[i].nt);
+    }
+    S.total = S.off[count];
+    auto tile = [&](const MatDesc &M, int r, int c) { return W + (M.tile0 + tidx(r, c)) * bb; };
+    for (int j = 0; j < ntmax; ++j) {
+        const int d0 = (int)S.diag.size(), u0 = (int)S.upd.size();
+        for (int i = 0; i < count; ++i) {
+            const MatDesc &M = h->mats[i];
+            if (M.nt <= j) continue;
+            const int64_t ldr = (int64_t)M.nt * b;
+            S.diag.push_back({tile(M, j, j), S.off[i] + (int64_t)j * b, ldr});
+            for (int r = j + 1; r < M.nt; ++r)
+                for (int r0 = 0; r0 < b; r0 += 64)
+                    S.upd.push_back({tile(M, r, j), S.off[i] + (int64_t)j * b, S.off[i] + (int64_t)r * b + r0, ldr, r0});
+        }
+        S.fd.push_back({d0, (int)S.diag.size() - d0});
+        S.fu.push_back({u0, (int)S.upd.size() - u0});
+    }
+    for (int j = ntmax - 1; j >= 0; --j) {
+        const int d0 = (int)S.diag.size(), u0 = (int)S.upd.size();
+        for (int i = 0; i < count; ++i) {
+            const MatDesc &M = h->mats[i];
+            if (M.nt <= j) continue;
+            const int64_t ldr = (int64_t)M.nt * b;
+            S.diag.push_back({tile(M, j, j), S.off[i] + (int64_t)j * b, ldr});
+            for (int r = 0; r < j; ++r)
+                for (int r0 = 0; r0 < b; r0 += 64)
+                    S.upd.push_back({tile(M, j, r), S.off[i] + (int64_t)j * b, S.off[i] + (int64_t)r * b + r0, ldr, r0});
+        }
+        S.bd.push_back({d0, (int)S.diag.size() - d0});
+        S.bu.push_back({u0, (int)S.upd.size() - u0});
+    }
+    for (int i = 0; i < count; ++i) {
+        const MatDesc &M = h->mats[i];
+        const int64_t ldr = (int64_t)M.nt * b;
+        for (int r = 0; r < M.nt; ++r)
+            for (int r0 = 0; r0 < b; r0 += 64)
+                S.res.push_back({M.A_dev, M.n, M.nt, r, r0, S.off[i], S.off[i], S.off[i], ldr});
+        S.mx.push_back({S.off[i], ldr, M.n, i * nrhs});
+    }
+    return S;
+}
+
+struct BatchSolveDev {
+    const SDiag *diag;
+    const SUpd *upd;
+    const SRes *res;
+    const SMax *mx;
+};
+
+static int upload_batch_solve(tc_handle h, const BatchSolvePlan &S, BatchSolveDev &D) {
+    const size_t od = 0, ou = align_up(S.diag.size() * sizeof(SDiag)), orr = align_up(ou + S.upd.size() * sizeof(SUpd));
+    const size_t om = align_up(orr + S.res.size() * sizeof(SRes)), total = align_up(om + S.mx.size() * sizeof(SMax));
+    int rc = ensure(h, h->stab, total);
+    if (rc) return rc;
+    std::vector<char> host(total, 0);
+    if (!S.diag.empty()) memcpy(host.data() + od, S.diag.data(), S.diag.size() * sizeof(SDiag));
+    if (!S.upd.empty()) memcpy(host.data() + ou, S.upd.data(), S.upd.size() * sizeof(SUpd));
+    if (!S.res.empty()) memcpy(host.data() + orr, S.res.data(), S.res.size() * sizeof(SRes));
+    if (!S.mx.empty()) memcpy(host.data() + om, S.mx.data(), S.mx.size() * sizeof(SMax));
+    CK(cudaMemcpy(h->stab.p, host.data(), total, cudaMemcpyHostToDevice));
+    char *base = static_cast<char *>(h->stab.p);
+    D.diag = reinterpret_cast<const SDiag *>(base + od);
+    D.upd = reinterpret_cast<const SUpd *>(base + ou);
+    D.res = reinterpret_cast<const SRes *>(base + orr);
+    D.mx = reinterpret_cast<const SMax *>(base + om);
+    return TC_OK;
+}
+
+static int batch_subst(tc_handle h, const BatchSolvePlan &S, const BatchSolveDev &D, double *R, int nrhs, bool back) {
+    const int b = h->b;
+    for (size_t j = 0; j < S.fd.size(); ++j) {
+        launch_fwd_diag_g(D.diag + S.fd[j].first, S.fd[j].second, R, b, nrhs, h->s);
+        CK_LAUNCH();
+        if (S.fu[j].second) {
+            launch_fwd_update_g(D.upd + S.fu[j].first, S.fu[j].second, R, b, nrhs, h->s);
+            CK_LAUNCH();
+        }
+    }
+    if (!back) return TC_OK;
+    for (size_t j = 0; j < S.bd.size(); ++j) {
+        launch_bwd_diag_g(D.diag + S.bd[j].first, S.bd[j].second, R, b, nrhs, h->s);
+        CK_LAUNCH();
+        if (S.bu[j].second) {
+            launch_bwd_update_g(D.upd + S.bu[j].first, S.bu[j].second, R, b, nrhs, h->s);
+            CK_LAUNCH();
+        }
+    }
+    return TC_OK;
+}
+
 int tile_chol_solve_batched(tc_handle h, int nrhs, const double *const *B, double *const *X, int max_refine,
                             double target_berr, double *berr_out, tc_stats *stats) {
     if (!h) return TC_ERR_ARG;
     if (!h->factored || h->ooc) return set_err(h, TC_ERR_STATE, "no successful in-core factorization");
-    if (nrhs < 1 || !B || !X || max_refine < 0) return set_err(h, TC_ERR_ARG, "bad batched solve arguments");
+    if (nrhs < 1 || nrhs > 16 || !B || !X || max_refine < 0)
+        return set_err(h, TC_ERR_ARG, "bad batched solve arguments (1 <= nrhs <= 16)");
     CK(cudaSetDevice(h->device));
     const double t0 = now_ms();
     const int64_t launches0 = h->launches;
     const int count = (int)h->mats.size(), b = h->b;
-    const int64_t bb = (int64_t)b * b;
-    std::vector<int64_t> off(count + 1, 0);
-    int64_t ldmax = 0;
-    for (int i = 0; i < count; ++i) {
-        const int64_t ldr = (int64_t)h->mats[i].nt * b;
-        off[i + 1] = off[i] + ldr * nrhs;
-        ldmax = std::max(ldmax, ldr);
-    }
-    int rc = ensure(h, h->vec, (size_t)(3 * off[count] + 2 * ldmax) * sizeof(double));
+    BatchSolvePlan S = plan_batch_solve(h, nrhs);
+    BatchSolveDev D{};
+    int rc = upload_batch_solve(h, S, D);
     if (rc) return rc;
+    if ((rc = ensure(h, h->vec, (size_t)3 * S.total * sizeof(double)))) return rc;
     if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, (size_t)(3 * nrhs + 1) * count) * sizeof(double)))) return rc;
-    double *Bd = static_cast<double *>(h->vec.p), *Xd = Bd + off[count], *Rd = Xd + off[count];
-    double *ones = Rd + off[count], *rowsum = ones + ldmax;
+    double *Bd = static_cast<double *>(h->vec.p), *Xd = Bd + S.total, *Rd = Xd + S.total;
     double *sc = static_cast<double *>(h->scratch.p);
-    const double *W = static_cast<const double *>(h->W.p);
-    CK(cudaMemsetAsync(Bd, 0, off[count] * sizeof(double), h->s));
+    CK(cudaMemsetAsync(Bd, 0, S.total * sizeof(double), h->s));
     for (int i = 0; i < count; ++i) {
         const MatDesc &M = h->mats[i];
-        const int64_t ldr = (int64_t)M.nt * b;
-        CK(cudaMemcpy2DAsync(Bd + off[i], ldr * sizeof(double), B[i], M.n * sizeof(double), M.n * sizeof(double),
-                             nrhs, cudaMemcpyDefault, h->s));
+        CK(cudaMemcpy2DAsync(Bd + S.off[i], (size_t)M.nt * b * sizeof(double), B[i], M.n * sizeof(double),
+                             M.n * sizeof(double), nrhs, cudaMemcpyDefault, h->s));
     }
-    CK(cudaMemcpyAsync(Xd, Bd, off[count] * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-    for (int i = 0; i < count; ++i) {
-        const MatDesc &M = h->mats[i];
-        if ((rc = subst_w(h, W + M.tile0 * bb, M.nt, Xd + off[i], (int64_t)M.nt * b, nrhs, true))) return rc;
-    }
-    // ||A_i||_inf once per factorization
+    CK(cudaMemcpyAsync(Xd, Bd, S.total * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    if ((rc = batch_subst(h, S, D, Xd, nrhs, true))) return rc;
+    // ||A_i||_inf once per factorization: max row sum of |A_i| (X = nullptr reads ones)
     if (max_refine > 0 && h->normA_infs[0] < 0) {
-        std::vector<double> o((size_t)ldmax, 1.0);
-        CK(cudaMemcpy(ones, o.data(), ldmax * sizeof(double), cudaMemcpyHostToDevice));
-        CK(cudaMemsetAsync(sc, 0, count * sizeof(double), h->s));
-        for (int i = 0; i < count; ++i) {
-            const MatDesc &M = h->mats[i];
-            launch_symv_resid(M.A_dev, M.nt, b, M.n, ones, ldmax, nullptr, 0, rowsum, ldmax, 1, 1, h->s);
-            CK_LAUNCH();
-            launch_colmax_abs(rowsum, ldmax, M.n, 1, sc + i, h->s);
-            CK_LAUNCH();
-        }
-        CK(cudaMemcpyAsync(h->normA_infs.data(), sc, count * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaMemsetAsync(sc, 0, (size_t)count * nrhs * sizeof(double), h->s));
+        launch_symv_g(D.res, (int)S.res.size(), b, nullptr, nullptr, Rd, 1, 1, h->s);
+        CK_LAUNCH();
+        launch_colmax_g(D.mx, count, Rd, 1, sc, h->s);
+        CK_LAUNCH();
+        std::vector<double> nm((size_t)count * nrhs);
+        CK(cudaMemcpyAsync(nm.data(), sc, nm.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
         CK(cudaStreamSynchronize(h->s));
+        for (int i = 0; i < count; ++i) h->normA_infs[i] = nm[(size_t)i * nrhs];
     }
-    std::vector<char> active(count, 1);
     std::vector<double> berr(count, -1.0);
     int it = 0;
     for (; max_refine > 0; ++it) {
+        launch_symv_g(D.res, (int)S.res.size(), b, Xd, Bd, Rd, nrhs, 0, h->s);
+        CK_LAUNCH();
         CK(cudaMemsetAsync(sc, 0, (size_t)3 * nrhs * count * sizeof(double), h->s));
-        for (int i = 0; i < count; ++i) {
-            if (!active[i]) continue;
-            const MatDesc &M = h->mats[i];
-            const int64_t ldr = (int64_t)M.nt * b;
-            for (int c0 = 0; c0 < nrhs; c0 += 16) {
-                const int nc = std::min(16, nrhs - c0);
-                launch_symv_resid(M.A_dev, M.nt, b, M.n, Xd + off[i] + c0 * ldr, ldr, Bd + off[i] + c0 * ldr, ldr,
-                                  Rd + off[i] + c0 * ldr, ldr, nc, 0, h->s);
-                CK_LAUNCH();
-            }
-            double *m3 = sc + (size_t)3 * nrhs * i;
-            launch_colmax_abs(Rd + off[i], ldr, M.n, nrhs, m3, h->s);
-            CK_LAUNCH();
-            launch_colmax_abs(Xd + off[i], ldr, M.n, nrhs, m3 + nrhs, h->s);
-            CK_LAUNCH();
-            launch_colmax_abs(Bd + off[i], ldr, M.n, nrhs, m3 + 2 * nrhs, h->s);
-            CK_LAUNCH();
-        }
+        launch_colmax_g(D.mx, count, Rd, nrhs, sc, h->s);
+        CK_LAUNCH();
+        launch_colmax_g(D.mx, count, Xd, nrhs, sc + (size_t)nrhs * count, h->s);
+        CK_LAUNCH();
+        launch_colmax_g(D.mx, count, Bd, nrhs, sc + (size_t)2 * nrhs * count, h->s);
+        CK_LAUNCH();
         std::vector<double> mx((size_t)3 * nrhs * count);
         CK(cudaMemcpyAsync(mx.data(), sc, mx.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
         CK(cudaStreamSynchronize(h->s));
-        bool any = false;
+        double worst = 0.0;
         for (int i = 0; i < count; ++i) {
-            if (!active[i]) continue;
-            const double *m3 = mx.data() + (size_t)3 * nrhs * i;
             double e = 0.0;
             for (int c = 0; c < nrhs; ++c) {
-                const double den = h->normA_infs[i] * m3[nrhs + c] + m3[2 * nrhs + c];
-                e = std::max(e, den > 0 ? m3[c] / den : 0.0);
+                const size_t k0 = (size_t)i * nrhs + c;
+                const double den = h->normA_infs[i] * mx[(size_t)nrhs * count + k0] + mx[(size_t)2 * nrhs * count + k0];
+                e = std::max(e, den > 0 ? mx[k0] / den : 0.0);
             }
             berr[i] = e;
-            if (e <= target_berr || it >= max_refine) active[i] = 0;
-            else any = true;
+            worst = std::max(worst, e);
         }
-        if (!any) break;
-        for (int i = 0; i < count; ++i) {
-            if (!active[i]) continue;
-            const MatDesc &M = h->mats[i];
-            const int64_t ldr = (int64_t)M.nt * b;
-            if ((rc = subst_w(h, W + M.tile0 * bb, M.nt, Rd + off[i], ldr, nrhs, true))) return rc;
-            launch_axpy_cols(Xd + off[i], ldr, Rd + off[i], ldr, M.n, nrhs, h->s);
-            CK_LAUNCH();
-        }
+        if (worst <= target_berr || it >= max_refine) break;
+        // one refinement step for every matrix (already-accurate ones stay accurate)
+        if ((rc = batch_subst(h, S, D, Rd, nrhs, true))) return rc;
+        launch_axpy_flat(Xd, Rd, S.total, h->s);
+        CK_LAUNCH();
     }
     for (int i = 0; i < count; ++i) {
         const MatDesc &M = h->mats[i];
-        CK(cudaMemcpy2DAsync(X[i], M.n * sizeof(double), Xd + off[i], (int64_t)M.nt * b * sizeof(double),
+        CK(cudaMemcpy2DAsync(X[i], M.n * sizeof(double), Xd + S.off[i], (size_t)M.nt * b * sizeof(double),
                              M.n * sizeof(double), nrhs, cudaMemcpyDefault, h->s));
     }
     CK(cudaStreamSynchronize(h->s));
@@ -1348,29 +1430,28 @@ int tile_chol_loglik_batched(tc_handle h, const double *const *y, double *loglik
     if (!h->factored || h->ooc) return set_err(h, TC_ERR_STATE, "no successful in-core factorization");
     CK(cudaSetDevice(h->device));
     const int count = (int)h->mats.size(), b = h->b;
-    const int64_t bb = (int64_t)b * b;
-    std::vector<int64_t> off(count + 1, 0);
-    for (int i = 0; i < count; ++i) off[i + 1] = off[i] + (int64_t)h->mats[i].nt * b;
-    int rc = ensure(h, h->vec, (size_t)off[count] * sizeof(double));
-    if (rc) return rc;
-    if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, (size_t)count) * sizeof(double)))) return rc;
-    double *z = static_cast<double *>(h->vec.p), *sc = static_cast<double *>(h->scratch.p);
-    const double *W = static_cast<const double *>(h->W.p);
     std::vector<double> quad(count, 0.0);
     if (y) {
-        CK(cudaMemsetAsync(z, 0, off[count] * sizeof(double), h->s));
+        BatchSolvePlan S = plan_batch_solve(h, 1);
+        BatchSolveDev D{};
+        int rc = upload_batch_solve(h, S, D);
+        if (rc) return rc;
+        if ((rc = ensure(h, h->vec, (size_t)S.total * sizeof(double)))) return rc;
+        if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, (size_t)count) * sizeof(double)))) return rc;
+        double *z = static_cast<double *>(h->vec.p), *sc = static_cast<double *>(h->scratch.p);
+        CK(cudaMemsetAsync(z, 0, S.total * sizeof(double), h->s));
         for (int i = 0; i < count; ++i) {
-            const MatDesc &M = h->mats[i];
             if (!y[i]) return set_err(h, TC_ERR_ARG, "y entries must not be NULL");
-            CK(cudaMemcpyAsync(z + off[i], y[i], M.n * sizeof(double), cudaMemcpyDefault, h->s));
-            if ((rc = subst_w(h, W + M.tile0 * bb, M.nt, z + off[i], (int64_t)M.nt * b, 1, false))) return rc;
-            launch_dot_self(z + off[i], M.n, sc + i, h->s);
-            CK_LAUNCH();
+            CK(cudaMemcpyAsync(z + S.off[i], y[i], h->mats[i].n * sizeof(double), cudaMemcpyDefault, h->s));
         }
+        if ((rc = batch_subst(h, S, D, z, 1, false))) return rc;
+        launch_dots_g(D.mx, count, z, z, sc, h->s);
+        CK_LAUNCH();
         CK(cudaMemcpyAsync(quad.data(), sc, count * sizeof(double), cudaMemcpyDeviceToHost, h->s));
         CK(cudaStreamSynchronize(h->s));
     }
     const double two_pi = 6.283185307179586476925286766559;
+    (void)b;
     for (int i = 0; i < count; ++i)
         loglik_out[i] = -0.5 * (double)h->mats[i].n * std::log(two_pi) - 0.5 * h->logdets[i] - 0.5 * quad[i];
     return TC_OK;

@@ -55,6 +55,7 @@ struct tc_handle_s {
     CUtensorMap map_hi{}, map_lo{}, map16{}, map8{};
     // emulated FP64 updates: digit planes, their tables and tensor maps
     DevBuf dpool, ztab, invbuf;
+    DevBuf stab;       // grouped batched-solve task tables
     CUtensorMap map_zx{}, map_zy{};
     // matrices of the last (batched) factorization
     std::vector<MatDesc> mats;

@@ -56,6 +56,28 @@ struct PEntry {
     int col0, rows;
 };
 
+// Grouped (batched) substitution tasks.  Offsets are element offsets into one RHS buffer
+// holding every matrix's padded right-hand sides (column stride ldr of that matrix).
+struct SDiag {          // diagonal block solve: L_jj, rows of block j
+    const double *L;
+    int64_t off, ldr;
+};
+struct SUpd {           // off-diagonal update of a 64-row chunk: dst -= op(L) src
+    const double *L;    // tile (i, j) for forward, (j, i) for back substitution
+    int64_t src, dst, ldr;
+    int r0;             // chunk's first row inside the destination tile row
+};
+struct SRes {           // residual / |A| x of one 64-row chunk of one matrix
+    const double *A;    // the matrix's tiles
+    int64_t n;
+    int nt, i, r0;
+    int64_t xo, bo, ro, ldr;
+};
+struct SMax {           // column maxima of one matrix's block of a buffer
+    int64_t off, ldr, n;
+    int out;            // output index of column 0
+};
+
 // A matrix of a batch for the batched log-determinant / padding kernels.
 struct LEntry {
     double *W;          // first tile of this matrix in the concatenated tile array
@@ -114,6 +136,15 @@ void launch_colmax_abs(const double *V, int64_t ld, int64_t n, int ncols, double
 void launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
 void launch_dot_self(const double *v, int64_t n, double *out, cudaStream_t s);
 void launch_dot(const double *u, const double *v, int64_t n, double *out, cudaStream_t s);
+void launch_fwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaStream_t s);
+void launch_fwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s);
+void launch_bwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaStream_t s);
+void launch_bwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s);
+void launch_symv_g(const SRes *r, int nr, int b, const double *X, const double *B, double *R, int nrhs, int absmode,
+                   cudaStream_t s);
+void launch_colmax_g(const SMax *m, int nm, const double *V, int nrhs, double *out, cudaStream_t s);
+void launch_axpy_flat(double *X, const double *D, int64_t count, cudaStream_t s);
+void launch_dots_g(const SMax *m, int nm, const double *u, const double *v, double *out, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers (k_gen.cu)
 void launch_matern(double *A, int64_t n, int b, int nt, const double *pts, double sigma2,
