@@ -36,6 +36,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_FLOPS_PER_CLK_SM = 4.0   # GB300: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / 152 SMs / 2.07 GHz)
 NSM = 152
 CPU_SAMPLE_N = 8192
+OOC_MXP_EPS, OOC_MXP_BAND = 1e-9, 2
 
 
 def parse_args():
@@ -53,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_N)
+    ap.add_argument("--ooc-mxp", action="store_true",
+                    help="out-of-core workload in four precisions (map at eps_high 1e-9, FP64 band 2)")
     return ap.parse_args()
 
 
@@ -550,7 +553,8 @@ def measure_link(dev):
 
 def run_ooc(args, ws, rank, local):
     """Out-of-core FP64 factorization: the tiles live in pinned host memory, the device caches at
-    most OOC_CACHE_FRACTION of them.  Each step factors a fresh copy of A (restored, untimed,
+    most OOC_CACHE_FRACTION of them (in bytes: with emulated updates a slot also holds the
+    tile's digit planes, so fewer tiles fit).  Each step factors a fresh copy of A (restored, untimed,
     before the step: the factorization overwrites A with L)."""
     import torch
     import torch.distributed as dist
@@ -565,13 +569,19 @@ def run_ooc(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     T = tc.tile_count(n, b)
     cap = int(inputs.OOC_CACHE_FRACTION * T * b * b * 8)
-    H = tc.Handle(local, stream=stream.cuda_stream, device_cap_bytes=cap)
+    H = tc.Handle(local, stream=stream.cuda_stream, device_cap_bytes=cap, fp64_mode=args.fp64_mode)
     link = measure_link(dev)
     pts = inputs.uniform_points(n, w.seed + 1000 * rank, w.morton)
     host0 = torch.empty(T * b * b, dtype=torch.float64, pin_memory=True)
     # generate on the device tile-row by tile-row is not needed: n = 65536 fits; generate and move
     A = torch.empty(T * b * b, dtype=torch.float64, device=dev)
     tc.tc_matern_tiles(H.h, n, b, torch.from_numpy(pts).to(dev), w.sigma2, w.range_a, w.nu, w.nugget, A)
+    nt = tc.ntiles(n, b)
+    pmap = None
+    if args.ooc_mxp:
+        # four-precision map from the tile-norm criterion (computed once; the matrix is fixed)
+        pmap = torch.zeros(nt * nt, dtype=torch.uint8)
+        tc.tile_chol_precision_map(H.h, n, b, A, OOC_MXP_EPS, OOC_MXP_BAND, 4, pmap)
     host0.copy_(A)
     del A
     torch.cuda.empty_cache()
@@ -585,7 +595,7 @@ def run_ooc(args, ws, rank, local):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st, ss = tc.tc_stats(), tc.tc_stats()
         e0.record(stream)
-        info = tc.tile_chol_factor_ooc(H.h, n, b, work, None, st)
+        info = tc.tile_chol_factor_ooc(H.h, n, b, work, pmap, st)
         if info:
             raise RuntimeError(f"ooc factorization failed at column {info}")
         tc.tile_chol_solve(H.h, 1, y, n, x, n, 0, 0.0, ss)
@@ -610,13 +620,34 @@ def run_ooc(args, ws, rank, local):
     value = ws * flops * args.steps / t / 1e12
     h2d, d2h = st.h2d_bytes, st.d2h_bytes
     tf = st.t_ms / 1e3
+    ld_run = tc.tile_chol_logdet(H.h)
+    accuracy = None
+    if args.ooc_mxp:
+        # FP64 reference (untimed): the same matrix out of core with an all-FP64 map
+        work.copy_(host0)
+        s64 = tc.tc_stats()
+        if tc.tile_chol_factor_ooc(H.h, n, b, work, None, s64) == 0:
+            ll64 = tc.tile_chol_loglik(H.h, y)
+            ld64 = tc.tile_chol_logdet(H.h)
+            accuracy = {"loglik_fp64": ll64, "loglik_mxp": ll, "loglik_rel_err": abs(ll - ll64) / abs(ll64),
+                        "logdet_fp64": ld64, "logdet_mxp": ld_run, "kl_divergence": 0.5 * (ld_run - ld64),
+                        "fp64_ooc_h2d_bytes": s64.h2d_bytes, "fp64_ooc_t_factor_ms": s64.t_ms,
+                        "reference": "same matrix, out of core, all-FP64 map"}
     if rank == 0:
         line = common_line(ws, args, value, t, {
             "workload": w.name + f"@n={n}", "n": n, "tile": b, "nu": w.nu, "range": w.range_a, "nugget": w.nugget,
             "device_cache_bytes": cap, "matrix_bytes": T * b * b * 8, "host": "pinned",
             "step": "ooc factor (A in host memory, overwritten by L)+streamed 1-RHS solve+loglik",
-            "l2": "inputs larger than L2", "parallelism": f"replicas x{ws}"}, "f64")
-        line["roofline"] = fp64_roofline(st.update_flops[0], st.t_update_ms[0], tf)
+            "l2": "inputs larger than L2", "parallelism": f"replicas x{ws}",
+            "precision": (f"per-tile map, eps_high {OOC_MXP_EPS}, FP64 band {OOC_MXP_BAND}" if args.ooc_mxp
+                          else "FP64")},
+            ("f64+f32+f16+e4m3" if args.ooc_mxp else
+             "f64" if args.fp64_mode == 0 else "f64 (updates emulated on e4m3 tensor cores)"))
+        rf = zgemm_roofline if args.fp64_mode >= 1 else fp64_roofline
+        line["roofline"] = rf(st.update_flops[0], st.t_update_ms[0], tf)
+        if args.fp64_mode >= 1:
+            line["roofline"]["kernel"] = "k_zgemm (grouped out-of-core form)"
+        line["config"]["fp64_updates"] = "emulated (E4M3 digit planes)" if args.fp64_mode >= 1 else "DFMA"
         line["ooc_link"] = {"h2d_bytes": h2d, "d2h_bytes": d2h, "h2d_gbs": h2d / tf / 1e9, "d2h_gbs": d2h / tf / 1e9,
                             "link_peak_gbs": link, "h2d_frac": (h2d / tf / 1e9) / link["h2d"],
                             "cache_hits": st.cache_hits, "cache_misses": st.cache_misses,
@@ -626,8 +657,12 @@ def run_ooc(args, ws, rank, local):
         line["cpu_baseline"] = None
         line["clocks"] = clk
         line["gpu_launches"] = st.kernel_launches + ss.kernel_launches
-        line["detail"] = {"t_factor_ms": st.t_ms, "t_update_ms": st.t_update_ms[0], "t_trsm_ms": st.t_trsm_ms,
-                          "t_potrf_ms": st.t_potrf_ms, "loglik": ll}
+        line["detail"] = {"t_factor_ms": st.t_ms, "t_update_ms": list(st.t_update_ms), "t_trsm_ms": st.t_trsm_ms,
+                          "t_potrf_ms": st.t_potrf_ms, "t_convert_ms": st.t_convert_ms, "loglik": ll,
+                          "update_launches": list(st.update_launches), "tiles_by_prec": list(st.tiles),
+                          "update_tflops_by_prec": [st.update_flops[p] / st.t_update_ms[p] / 1e9
+                                                    if st.t_update_ms[p] > 0 else None for p in range(4)]}
+        line["accuracy"] = accuracy
         print(json.dumps(line), flush=True)
     H.close()
 

@@ -9,6 +9,16 @@
 
 namespace tc {
 
+// Right-hand-side kernels are compiled for 1, 4 and 16 columns: GB300 issues a DFMA for every
+// unrolled column even when its predicate is off, and FP64 is its scarce pipe.
+#define NQ_DISPATCH(nrhs, kern, grid, block, smem, stream, ...)                             \
+    do {                                                                                  \
+        if ((nrhs) <= 1) kern<1><<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);      \
+        else if ((nrhs) <= 4) kern<4><<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__); \
+        else kern<16><<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                \
+    } while (0)
+
+
 // acc (rows tx + 16 i, columns ty + 16 j of a 64 x 64 block) += X[:, k0:k1] Y[:, k0:k1]^T.
 // X and Y point at the block's first row/column; column l of each is at l * ld.
 __device__ __forceinline__ void dgemm_block(double (&acc)[4][4], const double *__restrict__ X,
@@ -256,13 +266,16 @@ __global__ void k_zero_upper_diag(double *W, int nt, int b, int64_t n) {
 
 // Sum the four per-part accumulators of each row in a fixed order and subtract them from
 // R[q * ldr + g0 + r] (rows r of a 64-row chunk, RHS q < nrhs).
-__device__ __forceinline__ void part_reduce_sub(double (*red)[17], const double (&acc)[16], int nrhs,
+template <int NQ>
+__device__ __forceinline__ void part_reduce_sub(double (*red)[17], const double (&acc)[NQ], int nrhs,
                                                 double *R, int64_t ldr, int64_t g0) {
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
     for (int p = 0; p < 4; ++p) {
         __syncthreads();
         if (part == p)
-            for (int q = 0; q < nrhs; ++q) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nrhs) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
     }
     __syncthreads();
     for (int e = tid; e < 64 * nrhs; e += 256) {
@@ -272,36 +285,106 @@ __device__ __forceinline__ void part_reduce_sub(double (*red)[17], const double 
 }
 
 // -------------------------------------------------------------------------------- solves
-// Forward substitution with one diagonal tile: L_jj z = r for each RHS column.
-__global__ void __launch_bounds__(256) k_fwd_diag(const double *L, int b, double *R, int64_t ldr) {
-    __shared__ double z[4096];
+// One warp solves the 64 x 64 triangle held in S (S[r][c] = L[r][c], r >= c) against the 64
+// values in blk: forward (L x = blk) or backward (L^T x = blk).  Each lane owns rows lane and
+// lane + 32; the solved value travels by shuffle, so the 64 steps need no block barrier, and
+// the pivots' reciprocals are formed up front (x * (1/d): one extra rounding, off the chain).
+__device__ __forceinline__ void warp_tri64(double (*S)[65], double *blk, bool forward) {
+    const int lane = threadIdx.x & 31;
+    double x0 = blk[lane], x1 = blk[lane + 32];
+    const double r0 = 1.0 / S[lane][lane], r1 = 1.0 / S[lane + 32][lane + 32];
+    if (forward) {
+        for (int j = 0; j < 32; ++j) {
+            if (lane == j) x0 *= r0;
+            const double xj = __shfl_sync(0xffffffffu, x0, j);
+            if (lane > j) x0 = fma(-S[lane][j], xj, x0);
+            x1 = fma(-S[lane + 32][j], xj, x1);
+        }
+        for (int j = 0; j < 32; ++j) {
+            if (lane == j) x1 *= r1;
+            const double xj = __shfl_sync(0xffffffffu, x1, j);
+            if (lane > j) x1 = fma(-S[lane + 32][32 + j], xj, x1);
+        }
+    } else {
+        for (int j = 31; j >= 0; --j) {
+            if (lane == j) x1 *= r1;
+            const double xj = __shfl_sync(0xffffffffu, x1, j);
+            if (lane < j) x1 = fma(-S[32 + j][lane + 32], xj, x1);
+            x0 = fma(-S[32 + j][lane], xj, x0);
+        }
+        for (int j = 31; j >= 0; --j) {
+            if (lane == j) x0 *= r0;
+            const double xj = __shfl_sync(0xffffffffu, x0, j);
+            if (lane < j) x0 = fma(-S[j][lane], xj, x0);
+        }
+    }
+    blk[lane] = x0;
+    blk[lane + 32] = x1;
+}
+
+// Forward substitution with one diagonal tile, one right-hand side r (in place): per 64-row
+// block, the product with the solved part (256 threads, 4 partial sums per row, fixed order)
+// and the warp solve of the diagonal block.
+__device__ __forceinline__ void fwd_diag_body(const double *L, int b, double *r) {
     __shared__ double red[4][64];
     __shared__ double blk[64];
-    double *r = R + blockIdx.x * ldr;
+    __shared__ double S[64][65];
+    double *z = r;                       // solved in place (block barriers order the accesses)
     const int tid = threadIdx.x;
-    for (int i = tid; i < b; i += 256) z[i] = r[i];
-    __syncthreads();
     const int rr = tid & 63, part = tid >> 6;
     for (int jb = 0; jb < b / 64; ++jb) {
-        double s = 0.0;
-        for (int l = part; l < jb * 64; l += 4) s += L[(int64_t)l * b + jb * 64 + rr] * z[l];
-        red[part][rr] = s;
+        double acc = 0.0;
+        for (int l = part; l < jb * 64; l += 4) acc = fma(L[(int64_t)l * b + jb * 64 + rr], z[l], acc);
+        red[part][rr] = acc;
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int lr = idx & 63, lc = idx >> 6;
+            S[lr][lc] = (lr >= lc) ? L[(int64_t)(jb * 64 + lc) * b + jb * 64 + lr] : 0.0;
+        }
         __syncthreads();
         if (tid < 64) blk[tid] = z[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
         __syncthreads();
-        for (int jj = 0; jj < 64; ++jj) {
-            if (tid == jj) blk[jj] = blk[jj] / L[(int64_t)(jb * 64 + jj) * b + jb * 64 + jj];
-            __syncthreads();
-            if (tid > jj && tid < 64) blk[tid] -= L[(int64_t)(jb * 64 + jj) * b + jb * 64 + tid] * blk[jj];
-            __syncthreads();
-        }
+        if (tid < 32) warp_tri64(S, blk, true);
+        __syncthreads();
         if (tid < 64) z[jb * 64 + tid] = blk[tid];
         __syncthreads();
     }
-    for (int i = tid; i < b; i += 256) r[i] = z[i];
+}
+
+// Back substitution with one diagonal tile: L_jj^T x = z, one right-hand side (in place).
+__device__ __forceinline__ void bwd_diag_body(const double *L, int b, double *x) {
+    __shared__ double S[64][65];
+    __shared__ double red[4][64];
+    __shared__ double blk[64];
+    const int tid = threadIdx.x;
+    const int rr = tid & 63, part = tid >> 6;
+    for (int jb = b / 64 - 1; jb >= 0; --jb) {
+        // acc[r] = sum_{l >= (jb+1)*64} L[l][jb*64 + r] x[l]: rows of the tile's column block,
+        // read along l (column-major L: contiguous in l for a fixed column)
+        double acc = 0.0;
+        const double *Lc = L + (int64_t)(jb * 64 + rr) * b;
+        for (int l = (jb + 1) * 64 + part; l < b; l += 4) acc = fma(Lc[l], x[l], acc);
+        red[part][rr] = acc;
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int lr = idx & 63, lc = idx >> 6;
+            S[lr][lc] = (lr >= lc) ? L[(int64_t)(jb * 64 + lc) * b + jb * 64 + lr] : 0.0;
+        }
+        __syncthreads();
+        if (tid < 64) blk[tid] = x[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+        __syncthreads();
+        if (tid < 32) warp_tri64(S, blk, false);
+        __syncthreads();
+        if (tid < 64) x[jb * 64 + tid] = blk[tid];
+        __syncthreads();
+    }
+}
+
+// Forward substitution with one diagonal tile: L_jj z = r for each RHS column (one CTA each).
+__global__ void __launch_bounds__(256) k_fwd_diag(const double *L, int b, double *R, int64_t ldr) {
+    fwd_diag_body(L, b, R + blockIdx.x * ldr);
 }
 
 // r_i -= L_ij z_j for every tile row i > j; one CTA per 64-row chunk of a tile row.
+template <int NQ>
 __global__ void __launch_bounds__(256)
 k_fwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
     __shared__ double zs[128][16];
@@ -310,9 +393,9 @@ k_fwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
     const int i = j + 1 + blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * 64;
     const double *L = W + ((int64_t)i * (i + 1) / 2 + j) * (int64_t)b * b;
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
-    double acc[16];
+    double acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int c0 = 0; c0 < b; c0 += 128) {
         __syncthreads();
         for (int e = tid; e < 128 * nrhs; e += 256) {
@@ -323,53 +406,20 @@ k_fwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
         for (int c = part; c < 128; c += 4) {
             const double l = L[(int64_t)(c0 + c) * b + r0 + rr];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < NQ; ++q)
                 if (q < nrhs) acc[q] = fma(l, zs[c][q], acc[q]);
         }
     }
     part_reduce_sub(red, acc, nrhs, R, ldr, (int64_t)i * b + r0);
 }
 
-// Back substitution with one diagonal tile: L_jj^T x = z for each RHS column (in place).
+// Back substitution with one diagonal tile: L_jj^T x = z for each RHS column (one CTA each).
 __global__ void __launch_bounds__(256) k_bwd_diag(const double *L, int b, double *R, int64_t ldr) {
-    __shared__ double S[64][65];
-    __shared__ double red[4][64];
-    __shared__ double blk[64];
-    double *x = R + blockIdx.x * ldr;
-    const int tid = threadIdx.x;
-    const int rr = tid & 63, part = tid >> 6;
-    for (int jb = b / 64 - 1; jb >= 0; --jb) {
-        // s[r] = z[jb*64 + r] - sum_{l >= (jb+1)*64} L[l][jb*64 + r] x[l]
-        double s = 0.0;
-        for (int l0 = (jb + 1) * 64; l0 < b; l0 += 64) {
-            __syncthreads();
-            for (int idx = tid; idx < 4096; idx += 256) {
-                const int lr = idx & 63, rc = idx >> 6;
-                S[rc][lr] = L[(int64_t)(jb * 64 + rc) * b + l0 + lr];
-            }
-            __syncthreads();
-            for (int lr = part; lr < 64; lr += 4) s += S[rr][lr] * x[l0 + lr];
-        }
-        red[part][rr] = s;
-        __syncthreads();
-        if (tid < 64) blk[tid] = x[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
-        for (int idx = tid; idx < 4096; idx += 256) {
-            const int lr = idx & 63, rc = idx >> 6;
-            S[rc][lr] = L[(int64_t)(jb * 64 + rc) * b + jb * 64 + lr];  // S[r][l] = L[l][r]
-        }
-        __syncthreads();
-        for (int jj = 63; jj >= 0; --jj) {
-            if (tid == jj) blk[jj] = blk[jj] / S[jj][jj];
-            __syncthreads();
-            if (tid < jj) blk[tid] -= S[tid][jj] * blk[jj];
-            __syncthreads();
-        }
-        if (tid < 64) x[jb * 64 + tid] = blk[tid];
-        __syncthreads();
-    }
+    bwd_diag_body(L, b, R + blockIdx.x * ldr);
 }
 
 // z_i -= L_ji^T x_j for every tile row i < j; one CTA per 64-row chunk of tile row i.
+template <int NQ>
 __global__ void __launch_bounds__(256)
 k_bwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
     __shared__ double xs[64][16];
@@ -378,9 +428,9 @@ k_bwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
     const int i = blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * 64;
     const double *L = W + ((int64_t)j * (j + 1) / 2 + i) * (int64_t)b * b;   // tile (j, i)
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
-    double acc[16];
+    double acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int c0 = 0; c0 < b; c0 += 64) {
         __syncthreads();
         for (int idx = tid; idx < 4096; idx += 256) {
@@ -395,7 +445,7 @@ k_bwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
         for (int c = part; c < 64; c += 4) {
             const double l = S[rr][c];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < NQ; ++q)
                 if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
         }
     }
@@ -404,6 +454,7 @@ k_bwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
 
 // R = B - A X (absmode 0) or R = |A| X (absmode 1, B unused) for the symmetric A held as
 // lower tiles; rows and columns >= n (padding) contribute nothing and R's padding is 0.
+template <int NQ>
 __global__ void __launch_bounds__(256)
 k_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t ldx,
              const double *B, int64_t ldb, double *R, int64_t ldr, int nrhs, int absmode) {
@@ -413,9 +464,9 @@ k_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t
     const int i = blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * 64;
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
     const int64_t bb = (int64_t)b * b;
-    double acc[16];
+    double acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int j = 0; j < nt; ++j) {
         const bool lower = j <= i;
         const double *T = lower ? A + ((int64_t)i * (i + 1) / 2 + j) * bb : A + ((int64_t)j * (j + 1) / 2 + i) * bb;
@@ -446,7 +497,7 @@ k_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t
             for (int c = part; c < 64; c += 4) {
                 const double l = S[rr][c];
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
+                for (int q = 0; q < NQ; ++q)
                     if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
             }
         }
@@ -455,7 +506,9 @@ k_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t
     for (int p = 0; p < 4; ++p) {
         __syncthreads();
         if (part == p)
-            for (int q = 0; q < nrhs; ++q) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nrhs) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
     }
     __syncthreads();
     for (int e = tid; e < 64 * nrhs; e += 256) {
@@ -617,42 +670,18 @@ void launch_fix_padding_batched(const LEntry *e, int count, int ntmax, int b, cu
 // ------------------------------------------------------------ grouped (batched) solves
 __global__ void __launch_bounds__(256) k_fwd_diag_g(const SDiag *__restrict__ e, double *R, int b) {
     const SDiag E = e[blockIdx.y];
-    __shared__ double z[4096];
-    __shared__ double red[4][64];
-    __shared__ double blk[64];
-    const double *L = E.L;
-    double *r = R + E.off + blockIdx.x * E.ldr;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < b; i += 256) z[i] = r[i];
-    __syncthreads();
-    const int rr = tid & 63, part = tid >> 6;
-    for (int jb = 0; jb < b / 64; ++jb) {
-        double s = 0.0;
-        for (int l = part; l < jb * 64; l += 4) s += L[(int64_t)l * b + jb * 64 + rr] * z[l];
-        red[part][rr] = s;
-        __syncthreads();
-        if (tid < 64) blk[tid] = z[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
-        __syncthreads();
-        for (int jj = 0; jj < 64; ++jj) {
-            if (tid == jj) blk[jj] = blk[jj] / L[(int64_t)(jb * 64 + jj) * b + jb * 64 + jj];
-            __syncthreads();
-            if (tid > jj && tid < 64) blk[tid] -= L[(int64_t)(jb * 64 + jj) * b + jb * 64 + tid] * blk[jj];
-            __syncthreads();
-        }
-        if (tid < 64) z[jb * 64 + tid] = blk[tid];
-        __syncthreads();
-    }
-    for (int i = tid; i < b; i += 256) r[i] = z[i];
+    fwd_diag_body(E.L, b, R + E.off + blockIdx.x * E.ldr);
 }
 
+template <int NQ>
 __global__ void __launch_bounds__(256) k_fwd_update_g(const SUpd *__restrict__ u, double *R, int b, int nrhs) {
     const SUpd U = u[blockIdx.x];
     __shared__ double zs[128][16];
     __shared__ double red[64][17];
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
-    double acc[16];
+    double acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int c0 = 0; c0 < b; c0 += 128) {
         __syncthreads();
         for (int e = tid; e < 128 * nrhs; e += 256) {
@@ -663,7 +692,7 @@ __global__ void __launch_bounds__(256) k_fwd_update_g(const SUpd *__restrict__ u
         for (int c = part; c < 128; c += 4) {
             const double l = U.L[(int64_t)(c0 + c) * b + U.r0 + rr];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < NQ; ++q)
                 if (q < nrhs) acc[q] = fma(l, zs[c][q], acc[q]);
         }
     }
@@ -672,51 +701,18 @@ __global__ void __launch_bounds__(256) k_fwd_update_g(const SUpd *__restrict__ u
 
 __global__ void __launch_bounds__(256) k_bwd_diag_g(const SDiag *__restrict__ e, double *R, int b) {
     const SDiag E = e[blockIdx.y];
-    __shared__ double S[64][65];
-    __shared__ double red[4][64];
-    __shared__ double blk[64];
-    const double *L = E.L;
-    double *x = R + E.off + blockIdx.x * E.ldr;
-    const int tid = threadIdx.x;
-    const int rr = tid & 63, part = tid >> 6;
-    for (int jb = b / 64 - 1; jb >= 0; --jb) {
-        double s = 0.0;
-        for (int l0 = (jb + 1) * 64; l0 < b; l0 += 64) {
-            __syncthreads();
-            for (int idx = tid; idx < 4096; idx += 256) {
-                const int lr = idx & 63, rc = idx >> 6;
-                S[rc][lr] = L[(int64_t)(jb * 64 + rc) * b + l0 + lr];
-            }
-            __syncthreads();
-            for (int lr = part; lr < 64; lr += 4) s += S[rr][lr] * x[l0 + lr];
-        }
-        red[part][rr] = s;
-        __syncthreads();
-        if (tid < 64) blk[tid] = x[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
-        for (int idx = tid; idx < 4096; idx += 256) {
-            const int lr = idx & 63, rc = idx >> 6;
-            S[rc][lr] = L[(int64_t)(jb * 64 + rc) * b + jb * 64 + lr];
-        }
-        __syncthreads();
-        for (int jj = 63; jj >= 0; --jj) {
-            if (tid == jj) blk[jj] = blk[jj] / S[jj][jj];
-            __syncthreads();
-            if (tid < jj) blk[tid] -= S[tid][jj] * blk[jj];
-            __syncthreads();
-        }
-        if (tid < 64) x[jb * 64 + tid] = blk[tid];
-        __syncthreads();
-    }
+    bwd_diag_body(E.L, b, R + E.off + blockIdx.x * E.ldr);
 }
 
+template <int NQ>
 __global__ void __launch_bounds__(256) k_bwd_update_g(const SUpd *__restrict__ u, double *R, int b, int nrhs) {
     const SUpd U = u[blockIdx.x];
     __shared__ double xs[64][16];
     __shared__ double S[64][65];
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
-    double acc[16];
+    double acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int c0 = 0; c0 < b; c0 += 64) {
         __syncthreads();
         for (int idx = tid; idx < 4096; idx += 256) {
@@ -731,13 +727,14 @@ __global__ void __launch_bounds__(256) k_bwd_update_g(const SUpd *__restrict__ u
         for (int c = part; c < 64; c += 4) {
             const double l = S[rr][c];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < NQ; ++q)
                 if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
         }
     }
     part_reduce_sub(reinterpret_cast<double(*)[17]>(&S[0][0]), acc, nrhs, R + U.dst, U.ldr, 0);
 }
 
+template <int NQ>
 __global__ void __launch_bounds__(256)
 k_symv_g(const SRes *__restrict__ rs, int b, const double *X, const double *B, double *R, int nrhs, int absmode) {
     const SRes Q = rs[blockIdx.x];
@@ -746,9 +743,9 @@ k_symv_g(const SRes *__restrict__ rs, int b, const double *X, const double *B, d
     const int i = Q.i, r0 = Q.r0;
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
     const int64_t bb = (int64_t)b * b;
-    double acc[16];
+    double acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int j = 0; j < Q.nt; ++j) {
         const bool lower = j <= i;
         const double *T = lower ? Q.A + ((int64_t)i * (i + 1) / 2 + j) * bb : Q.A + ((int64_t)j * (j + 1) / 2 + i) * bb;
@@ -779,7 +776,7 @@ k_symv_g(const SRes *__restrict__ rs, int b, const double *X, const double *B, d
             for (int c = part; c < 64; c += 4) {
                 const double l = S[rr][c];
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
+                for (int q = 0; q < NQ; ++q)
                     if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
             }
         }
@@ -788,7 +785,9 @@ k_symv_g(const SRes *__restrict__ rs, int b, const double *X, const double *B, d
     for (int p = 0; p < 4; ++p) {
         __syncthreads();
         if (part == p)
-            for (int q = 0; q < nrhs; ++q) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nrhs) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
     }
     __syncthreads();
     for (int e = tid; e < 64 * nrhs; e += 256) {
@@ -836,17 +835,17 @@ void launch_fwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaS
     if (ne > 0) k_fwd_diag_g<<<dim3(nrhs, ne), 256, 0, s>>>(e, R, b);
 }
 void launch_fwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s) {
-    if (nu > 0) k_fwd_update_g<<<nu, 256, 0, s>>>(u, R, b, nrhs);
+    if (nu > 0) NQ_DISPATCH(nrhs, k_fwd_update_g, nu, 256, 0, s, u, R, b, nrhs);
 }
 void launch_bwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaStream_t s) {
     if (ne > 0) k_bwd_diag_g<<<dim3(nrhs, ne), 256, 0, s>>>(e, R, b);
 }
 void launch_bwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s) {
-    if (nu > 0) k_bwd_update_g<<<nu, 256, 0, s>>>(u, R, b, nrhs);
+    if (nu > 0) NQ_DISPATCH(nrhs, k_bwd_update_g, nu, 256, 0, s, u, R, b, nrhs);
 }
 void launch_symv_g(const SRes *r, int nr, int b, const double *X, const double *B, double *R, int nrhs, int absmode,
                    cudaStream_t s) {
-    if (nr > 0) k_symv_g<<<nr, 256, 0, s>>>(r, b, X, B, R, nrhs, absmode);
+    if (nr > 0) NQ_DISPATCH(nrhs, k_symv_g, nr, 256, 0, s, r, b, X, B, R, nrhs, absmode);
 }
 void launch_colmax_g(const SMax *m, int nm, const double *V, int nrhs, double *out, cudaStream_t s) {
     if (nm > 0) k_colmax_g<<<dim3(8, nm), 256, 0, s>>>(m, V, nrhs, out);
@@ -859,6 +858,7 @@ void launch_dots_g(const SMax *m, int nm, const double *u, const double *v, doub
 }
 
 // ---------------------------------------------------------------------------- launchers
+
 void launch_dgemm_update(const DJob *jobs, const DItem *items, int nitems, int ld, double *partials,
                          const int *status, cudaStream_t s) {
     if (nitems > 0) k_dgemm_update<<<nitems, 256, 0, s>>>(jobs, items, ld, partials, status);
@@ -898,19 +898,19 @@ void launch_fwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs,
 }
 void launch_fwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
     const int ntiles = nt - 1 - j;
-    if (ntiles > 0) k_fwd_update<<<ntiles * (b / 64), 256, 0, s>>>(W, b, j, R, ldr, nrhs);
+    if (ntiles > 0) NQ_DISPATCH(nrhs, k_fwd_update, ntiles * (b / 64), 256, 0, s, W, b, j, R, ldr, nrhs);
 }
 void launch_bwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
     k_bwd_diag<<<nrhs, 256, 0, s>>>(Ljj, b, R, ldr);
 }
 void launch_bwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
     (void)nt;
-    if (j > 0) k_bwd_update<<<j * (b / 64), 256, 0, s>>>(W, b, j, R, ldr, nrhs);
+    if (j > 0) NQ_DISPATCH(nrhs, k_bwd_update, j * (b / 64), 256, 0, s, W, b, j, R, ldr, nrhs);
 }
 void launch_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t ldx,
                        const double *B, int64_t ldb, double *R, int64_t ldr, int nrhs, int absmode,
                        cudaStream_t s) {
-    k_symv_resid<<<nt * (b / 64), 256, 0, s>>>(A, nt, b, n, X, ldx, B, ldb, R, ldr, nrhs, absmode);
+    NQ_DISPATCH(nrhs, k_symv_resid, nt * (b / 64), 256, 0, s, A, nt, b, n, X, ldx, B, ldb, R, ldr, nrhs, absmode);
 }
 void launch_colmax_abs(const double *V, int64_t ld, int64_t n, int ncols, double *out, cudaStream_t s) {
     k_colmax_abs<<<dim3(64, ncols), 256, 0, s>>>(V, ld, n, out);
@@ -956,9 +956,15 @@ __global__ void __launch_bounds__(256, 2) k_dgemm_tile(const DJob job, int ld) {
         for (int i = 0; i < 4; ++i) C[(int64_t)(ty + 16 * j) * ld + tx + 16 * i] -= acc[i][j];
 }
 
-// TRSM of one tile held at C with L_kk at L (one CTA per 64-row strip).
-__global__ void __launch_bounds__(256, 2) k_trsm_tile(double *C, const double *L, int ld, int b, const int *status) {
+// TRSM of up to TG_MAX tiles at C[0..] with the same L_kk at L (one CTA per 64-row strip;
+// grid b/64 x tiles).
+struct TGroup {
+    double *C[TG_MAX];
+};
+__global__ void __launch_bounds__(256, 2)
+k_trsm_tile(const __grid_constant__ TGroup g, const double *L, int ld, int b, const int *status) {
     if (failed(status)) return;
+    double *C = g.C[blockIdx.y];
     extern __shared__ double smem[];
     double(*Xs)[64] = reinterpret_cast<double(*)[64]>(smem);
     double(*Ys)[64] = reinterpret_cast<double(*)[64]>(smem + 16 * 64);
@@ -985,6 +991,53 @@ __global__ void __launch_bounds__(256, 2) k_trsm_tile(double *C, const double *L
             X[(int64_t)(jb * 64 + c) * ld + r] = Ss[r][c];
         }
         __syncthreads();
+    }
+}
+
+// Y = L^{-1} for a lower-triangular b x b tile L (column-major, ld = b), by forward
+// substitution L y_c = e_c column by column: CTA x owns columns 8x .. 8x+7, whose entries
+// above the diagonal block are zero; for each 64-row block the product with the already
+// solved rows (kept in shared memory) is followed by the 64 x 64 diagonal solve.
+constexpr int TRINV_COLS = 8;
+__global__ void __launch_bounds__(256) k_trinv(const double *__restrict__ L, int b, double *__restrict__ Y) {
+    extern __shared__ double tsm[];
+    double *Ys = tsm;                               // b x 8: the CTA's columns, row-major by row
+    double(*Ld)[65] = reinterpret_cast<double(*)[65]>(tsm + (size_t)b * TRINV_COLS);
+    double(*Acc)[TRINV_COLS] = reinterpret_cast<double(*)[TRINV_COLS]>(tsm + (size_t)b * TRINV_COLS + 64 * 65);
+    const int tid = threadIdx.x, c0 = blockIdx.x * TRINV_COLS;
+    const int ib0 = c0 / 64;
+    const int r = tid & 63, cg = tid >> 6;          // row in block, column pair
+    for (int i = tid; i < ib0 * 64 * TRINV_COLS; i += 256) Ys[i] = 0.0;
+    for (int ib = ib0; ib < b / 64; ++ib) {
+        const int row = ib * 64 + r;
+        double a0 = (row == c0 + 2 * cg) ? 1.0 : 0.0, a1 = (row == c0 + 2 * cg + 1) ? 1.0 : 0.0;
+        for (int l = ib0 * 64; l < ib * 64; ++l) {
+            const double lv = L[(int64_t)l * b + row];
+            a0 = fma(-lv, Ys[l * TRINV_COLS + 2 * cg], a0);
+            a1 = fma(-lv, Ys[l * TRINV_COLS + 2 * cg + 1], a1);
+        }
+        Acc[r][2 * cg] = a0;
+        Acc[r][2 * cg + 1] = a1;
+        for (int i = tid; i < 4096; i += 256) {
+            const int rr = i & 63, cc = i >> 6;
+            Ld[rr][cc] = (rr >= cc) ? L[(int64_t)(ib * 64 + cc) * b + ib * 64 + rr] : 0.0;
+        }
+        __syncthreads();
+        for (int j = 0; j < 64; ++j) {
+            if (tid < TRINV_COLS) Acc[j][tid] = Acc[j][tid] / Ld[j][j];
+            __syncthreads();
+            for (int i = tid; i < 64 * TRINV_COLS; i += 256) {
+                const int rr = i / TRINV_COLS, cc = i % TRINV_COLS;
+                if (rr > j) Acc[rr][cc] = fma(-Ld[rr][j], Acc[j][cc], Acc[rr][cc]);
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < 64 * TRINV_COLS; i += 256) Ys[(ib * 64 + i / TRINV_COLS) * TRINV_COLS + i % TRINV_COLS] = Acc[i / TRINV_COLS][i % TRINV_COLS];
+        __syncthreads();
+    }
+    for (int i = tid; i < b * TRINV_COLS; i += 256) {
+        const int rr = i % b, cc = i / b;
+        Y[(int64_t)(c0 + cc) * b + rr] = Ys[rr * TRINV_COLS + cc];
     }
 }
 
@@ -1017,15 +1070,16 @@ __global__ void k_fix_padding_tile(double *T, int b, int nv, int diag) {
 }
 
 // r_i -= L_ij z_j for one tile L_ij (ptr), rows of tile row i; grid = b/64 chunks
+template <int NQ>
 __global__ void __launch_bounds__(256)
 k_fwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs) {
     __shared__ double zs[128][16];
     __shared__ double red[64][17];
     const int r0 = blockIdx.x * 64;
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
-    double acc[16];
+    double acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int c0 = 0; c0 < b; c0 += 128) {
         __syncthreads();
         for (int e = tid; e < 128 * nrhs; e += 256) {
@@ -1036,7 +1090,7 @@ k_fwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, 
         for (int c = part; c < 128; c += 4) {
             const double l = L[(int64_t)(c0 + c) * b + r0 + rr];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < NQ; ++q)
                 if (q < nrhs) acc[q] = fma(l, zs[c][q], acc[q]);
         }
     }
@@ -1044,15 +1098,16 @@ k_fwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, 
 }
 
 // z_i -= L_ji^T x_j for one tile L_ji (ptr); grid = b/64 chunks of tile row i
+template <int NQ>
 __global__ void __launch_bounds__(256)
 k_bwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs) {
     __shared__ double xs[64][16];
     __shared__ double S[64][65];
     const int r0 = blockIdx.x * 64;
     const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
-    double acc[16];
+    double acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int c0 = 0; c0 < b; c0 += 64) {
         __syncthreads();
         for (int idx = tid; idx < 4096; idx += 256) {
@@ -1067,7 +1122,7 @@ k_bwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, 
         for (int c = part; c < 64; c += 4) {
             const double l = S[rr][c];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < NQ; ++q)
                 if (q < nrhs) acc[q] = fma(l, xs[c][q], acc[q]);
         }
     }
@@ -1077,14 +1132,34 @@ k_bwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, 
 void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s) {
     k_dgemm_tile<<<dim3(job.M / 64, job.N / 64), 256, 0, s>>>(job, ld);
 }
-void launch_trsm_tile(double *C, const double *L, int ld, int b, const int *status, cudaStream_t s) {
+static size_t trsm_tile_smem() {
     const size_t smem = (32 * 64 + 2 * 64 * 65) * sizeof(double);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_trsm_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_trsm_tile<<<b / 64, 256, smem, s>>>(C, L, ld, b, status);
+    return smem;
+}
+void launch_trsm_tile(double *C, const double *L, int ld, int b, const int *status, cudaStream_t s) {
+    launch_trsm_group(&C, 1, L, ld, b, status, s);
+}
+void launch_trsm_group(double *const *C, int ntiles, const double *L, int ld, int b, const int *status,
+                       cudaStream_t s) {
+    if (ntiles <= 0) return;
+    const size_t smem = trsm_tile_smem();
+    TGroup g{};
+    for (int t = 0; t < ntiles; ++t) g.C[t] = C[t];
+    k_trsm_tile<<<dim3(b / 64, ntiles), 256, smem, s>>>(g, L, ld, b, status);
+}
+void launch_trinv(const double *L, int b, double *Y, cudaStream_t s) {
+    const size_t smem = ((size_t)b * TRINV_COLS + 64 * 65 + 64 * TRINV_COLS) * sizeof(double);
+    static int attr_b = 0;
+    if (attr_b < b) {
+        cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_b = b;
+    }
+    k_trinv<<<b / TRINV_COLS, 256, smem, s>>>(L, b, Y);
 }
 void launch_logdiag_tile(const double *D, int b, int nv, double *out, cudaStream_t s) {
     k_logdiag_tile<<<1, 256, 0, s>>>(D, b, nv, out);
@@ -1093,10 +1168,10 @@ void launch_fix_padding_tile(double *T, int b, int nv, int diag, cudaStream_t s)
     k_fix_padding_tile<<<64, 256, 0, s>>>(T, b, nv, diag);
 }
 void launch_fwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
-    k_fwd_update_tile<<<b / 64, 256, 0, s>>>(L, b, i, j, R, ldr, nrhs);
+    NQ_DISPATCH(nrhs, k_fwd_update_tile, b / 64, 256, 0, s, L, b, i, j, R, ldr, nrhs);
 }
 void launch_bwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
-    k_bwd_update_tile<<<b / 64, 256, 0, s>>>(L, b, i, j, R, ldr, nrhs);
+    NQ_DISPATCH(nrhs, k_bwd_update_tile, b / 64, 256, 0, s, L, b, i, j, R, ldr, nrhs);
 }
 
 }  // namespace tc

@@ -13,6 +13,8 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <cstring>
+
 namespace tc {
 
 // ----------------------------------------------------------------------- rounding
@@ -55,15 +57,15 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
 }
 
 // amax of every listed tile (atomic max of non-negative doubles on their bit patterns)
-__global__ void k_tile_amax(const double *W, int b, const int *tiles, double *amax) {
+__global__ void k_tile_amax(const double *W, int b, const int *tiles, double *amax, const double *alt) {
     const int t = tiles[blockIdx.y];
-    const double *T = W + (int64_t)t * b * b;
+    const double *T = alt ? alt + (int64_t)blockIdx.y * b * b : W + (int64_t)t * b * b;
     const int64_t bb = (int64_t)b * b;
-    double m = 0.0;
+    unsigned long long m = 0;           // sign-cleared bit patterns order like |x|
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb; e += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs(T[e]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(amax + t, m);
+        m = max(m, (unsigned long long)__double_as_longlong(T[e]) & 0x7FFFFFFFFFFFFFFFull);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long *>(amax + t), m);
 }
 
 // W tile <- its value stored in precision prec[t] (Section IV-C), and amax of the result
@@ -91,9 +93,9 @@ __global__ void k_store_round(double *W, int b, const int *tiles, const uint8_t 
 // transposed into its pool slot (row-major).  32 x 32 blocks through shared memory.
 __global__ void __launch_bounds__(256)
 k_make_copies(const double *W, int b, const CopyJob *jobs, const double *amaxS, float *pool_hi, float *pool_lo,
-              __half *pool16, uint8_t *pool8, int *exps16, int *exps8) {
+              __half *pool16, uint8_t *pool8, int *exps16, int *exps8, CopyJob one) {
     __shared__ double S[32][33];
-    const CopyJob J = jobs[blockIdx.y];
+    const CopyJob J = jobs ? jobs[blockIdx.y] : one;
     const double *T = W + (int64_t)J.tile * b * b;
     const int nbc = b / 32;
     const int e = (J.q >= 2) ? scale_exp(amaxS[J.tile], fmt_max(J.q)) : 0;
@@ -144,12 +146,44 @@ constexpr int QA_BYTES = QBM * QKB, QB_BYTES = QBN * QKB, QSTAGE_BYTES = QA_BYTE
 constexpr int QTHREADS = 320;
 constexpr unsigned long long QTIMEOUT_NS = 4000000000ull;  // 4 s per wait, then give up
 
+// In-core form: one CTA per QItem; operand n of item `it` is the packed tile it.xoff + n
+// (X) / it.yoff + n (Y), found in the pool through slot[] and scaled by exps[tile].
 struct QArgs {
     const QItem *items;
     const int *slot;      // slot of each (global) packed tile in this precision's pool (-1: none)
     const int *exps;      // scale exponents of the copies (FP16/FP8), nullptr for TF32
     int k, b;
     int *err;             // error word: set on a timed-out wait or a missing operand slot
+    __device__ void tile(QItem &it) const { it = items[blockIdx.x]; }
+    __device__ int xslot(const QItem &it, int n) const { return slot[it.xoff + n]; }
+    __device__ int yslot(const QItem &it, int n) const { return slot[it.yoff + n]; }
+    __device__ int xexp(const QItem &it, int n) const { return exps[it.xoff + n]; }
+    __device__ int yexp(const QItem &it, int n) const { return exps[it.yoff + n]; }
+};
+
+// Out-of-core form: up to QG_MAX output tiles of one tile column whose operands sit in
+// arbitrary cache slots (lists in the launch parameters; exps indexed by slot).  Grid:
+// ntiles x (b/QBM) x (b/QBN).
+struct QGroupArgs {
+    double *C[QG_MAX];
+    uint16_t xs[QG_MAX][QK_MAX];
+    uint16_t ys[QK_MAX];
+    const int *exps;
+    int k, b;
+    int *err;
+    __device__ void tile(QItem &it) const {
+        const int nbm = b / QBM, per = nbm * (b / QBN);
+        const int g = blockIdx.x / per, r = blockIdx.x % per;
+        it.C = C[g];
+        it.xoff = g;
+        it.yoff = 0;
+        it.bm = (uint16_t)(r % nbm);
+        it.bn = (uint16_t)(r / nbm);
+    }
+    __device__ int xslot(const QItem &it, int n) const { return xs[it.xoff][n]; }
+    __device__ int yslot(const QItem &, int n) const { return ys[n]; }
+    __device__ int xexp(const QItem &it, int n) const { return exps[xs[it.xoff][n]]; }
+    __device__ int yexp(const QItem &, int n) const { return exps[ys[n]]; }
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -257,10 +291,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // KIND 1: TF32 x3 (maps: A_hi, A_lo, B_hi, B_lo); 2: FP16; 3: FP8 E4M3 (maps: A, -, B, -)
-template <int KIND>
+template <int KIND, class Args>
 __global__ void __launch_bounds__(QTHREADS, 1)
 k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
-        const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1, const QArgs args) {
+        const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
+        const __grid_constant__ Args args) {
     extern __shared__ __align__(1024) uint8_t qsmem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(qsmem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + QSTAGES * QSTAGE_BYTES);
@@ -272,7 +307,8 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const QItem it = args.items[blockIdx.x];
+    QItem it;
+    args.tile(it);
     const int k = args.k, b = args.b;
     const int nsrc = k;
     constexpr int PASSES = (KIND == 1) ? 3 : 1;
@@ -305,8 +341,6 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    const int *slot = args.slot;
-    const int xoff = it.xoff, yoff = it.yoff;   // X tiles (m, n) = xoff + n, Y tiles (k, n) = yoff + n
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
@@ -321,7 +355,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
                 }
                 const int n = s / steps_per_src, j = s % steps_per_src;
                 const int kb = j / PASSES, pass = j % PASSES;
-                const int sx = slot[xoff + n], sy = slot[yoff + n];
+                const int sx = args.xslot(it, n), sy = args.yslot(it, n);
                 if (sx < 0 || sy < 0) {
                     *abort_flag = 1;
                     atomicExch(args.err, 2);
@@ -393,7 +427,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
         if (KIND != 1) {
             eref = -100000;
             for (int n = 0; n < nsrc; ++n) {
-                const int e = args.exps[xoff + n] + args.exps[yoff + n];
+                const int e = args.xexp(it, n) + args.yexp(it, n);
                 eref = e > eref ? e : eref;
             }
         }
@@ -403,7 +437,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
             if (!mbar_wait(accf + a, use & 1, abort_flag)) { ok = false; break; }
             tc_fence_after();
             float sc = 1.f;
-            if (KIND != 1) sc = ldexpf(1.f, args.exps[xoff + n] + args.exps[yoff + n] - eref);
+            if (KIND != 1) sc = ldexpf(1.f, args.xexp(it, n) + args.yexp(it, n) - eref);
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + a * QBN + half * EC;
 #pragma unroll
             for (int c = 0; c < EC / 32; ++c) {
@@ -472,16 +506,16 @@ int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize
 
 size_t qgemm_smem_bytes() { return (size_t)QSTAGES * QSTAGE_BYTES + 1024 + 256; }
 
-template <int KIND>
+template <int KIND, class Args>
 static void launch_q(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0, const CUtensorMap &b1,
-                     const QArgs &args, int nitems, cudaStream_t s) {
+                     const Args &args, int nitems, cudaStream_t s) {
     static bool attr = false;
     const size_t smem = qgemm_smem_bytes();
     if (!attr) {
-        cudaFuncSetAttribute(k_qgemm<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_qgemm<KIND, Args>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_qgemm<KIND><<<nitems, QTHREADS, smem, s>>>(a0, a1, b0, b1, args);
+    k_qgemm<KIND, Args><<<nitems, QTHREADS, smem, s>>>(a0, a1, b0, b1, args);
 }
 
 void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
@@ -494,8 +528,30 @@ void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const 
     else launch_q<3>(a0, a1, b0, b1, args, nitems, s);
 }
 
-void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, double *amax, cudaStream_t s) {
-    if (ntiles > 0) k_tile_amax<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, amax);
+// FP16 (kind 2) or FP8 (kind 3) updates of up to QG_MAX out-of-core tiles; the operand
+// copies sit in the cache-slot pool mapped by `mx` / `my` (slot s at rows s*b .. s*b+b-1).
+void launch_qgemm_group(int kind, const CUtensorMap &mx, const CUtensorMap &my, const QGroup &g, const int *exps,
+                        int b, int *err, cudaStream_t s) {
+    if (g.ntiles <= 0 || g.k <= 0) return;
+    QGroupArgs a;
+    memset(&a, 0, sizeof a);
+    for (int t = 0; t < g.ntiles; ++t) {
+        a.C[t] = g.C[t];
+        for (int n = 0; n < g.k; ++n) a.xs[t][n] = (uint16_t)g.xs[t][n];
+    }
+    for (int n = 0; n < g.k; ++n) a.ys[n] = (uint16_t)g.ys[n];
+    a.exps = exps;
+    a.k = g.k;
+    a.b = b;
+    a.err = err;
+    const int nitems = g.ntiles * (b / QBM) * (b / QBN);
+    if (kind == 2) launch_q<2>(mx, mx, my, my, a, nitems, s);
+    else launch_q<3>(mx, mx, my, my, a, nitems, s);
+}
+
+void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, double *amax, cudaStream_t s,
+                      const double *alt) {
+    if (ntiles > 0) k_tile_amax<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, amax, alt);
 }
 void launch_store_round(double *W, int b, const int *tiles, int ntiles, const uint8_t *prec, const double *amaxL,
                         double *amaxS, cudaStream_t s) {
@@ -503,7 +559,61 @@ void launch_store_round(double *W, int b, const int *tiles, int ntiles, const ui
 }
 void launch_make_copies(const double *W, int b, const CopyJob *jobs, int njobs, const double *amaxS, float *hi,
                         float *lo, __half *p16, uint8_t *p8, int *e16, int *e8, cudaStream_t s) {
-    if (njobs > 0) k_make_copies<<<dim3(64, njobs), 256, 0, s>>>(W, b, jobs, amaxS, hi, lo, p16, p8, e16, e8);
+    if (njobs > 0) k_make_copies<<<dim3(64, njobs), 256, 0, s>>>(W, b, jobs, amaxS, hi, lo, p16, p8, e16, e8, CopyJob{});
+}
+
+// ------------------------------------------------------------ out-of-core, one cache slot
+// The slot pool holds FP64 tiles at pool + s b^2; exps, amax arrays are indexed by slot.
+void launch_copy_slot(const double *pool, int b, int slot, int q, const double *amaxS, __half *p16, uint8_t *p8,
+                      int *e16, int *e8, cudaStream_t s) {
+    const int blocks = (b / 32) * (b / 32);
+    k_make_copies<<<dim3(blocks < 608 ? blocks : 608, 1), 256, 0, s>>>(pool, b, nullptr, amaxS, nullptr, nullptr, p16,
+                                                                       p8, e16, e8, CopyJob{slot, q, slot});
+}
+
+// T <- its value stored in precision p (scale from *amaxL, exponent to *e_out)
+__global__ void k_round_slot(double *T, int b, int p, const double *amaxL, int *e_out) {
+    const int e = (p >= 2) ? scale_exp(*amaxL, fmt_max(p)) : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *e_out = e;
+    const int64_t bb = (int64_t)b * b;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < bb; i += (int64_t)gridDim.x * blockDim.x)
+        T[i] = to_stored(T[i], p, e);
+}
+
+// compact host copy of a stored tile: FP32 as float, FP16 / FP8 as the scaled format value
+// (exact: the tile already holds representable values); unpack is the exact inverse
+__global__ void k_pack_compact(const double *T, int b, int p, const int *e_in, void *dst) {
+    const int e = (p >= 2) ? *e_in : 0;
+    const int64_t bb = (int64_t)b * b;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < bb; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = T[i];
+        if (p == 1) static_cast<float *>(dst)[i] = (float)v;
+        else if (p == 2) static_cast<__half *>(dst)[i] = __double2half(ldexp(v, -e));
+        else static_cast<uint8_t *>(dst)[i] = (uint8_t)__nv_cvt_double_to_fp8(ldexp(v, -e), __NV_SATFINITE, __NV_E4M3);
+    }
+}
+__global__ void k_unpack_compact(const void *src, int b, int p, const int *e_in, double *T) {
+    const int e = (p >= 2) ? *e_in : 0;
+    const int64_t bb = (int64_t)b * b;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < bb; i += (int64_t)gridDim.x * blockDim.x) {
+        double v;
+        if (p == 1) v = (double)static_cast<const float *>(src)[i];
+        else if (p == 2) v = (double)__half2float(static_cast<const __half *>(src)[i]);
+        else {
+            const __half_raw hr = __nv_cvt_fp8_to_halfraw(static_cast<const __nv_fp8_storage_t *>(src)[i], __NV_E4M3);
+            v = (double)__half2float(__half(hr));
+        }
+        T[i] = ldexp(v, e);
+    }
+}
+void launch_round_slot(double *T, int b, int p, const double *amaxL, int *e_out, cudaStream_t s) {
+    k_round_slot<<<608, 256, 0, s>>>(T, b, p, amaxL, e_out);
+}
+void launch_pack_compact(const double *T, int b, int p, const int *e, void *dst, cudaStream_t s) {
+    k_pack_compact<<<608, 256, 0, s>>>(T, b, p, e, dst);
+}
+void launch_unpack_compact(const void *src, int b, int p, const int *e, double *T, cudaStream_t s) {
+    k_unpack_compact<<<608, 256, 0, s>>>(src, b, p, e, T);
 }
 
 }  // namespace tc

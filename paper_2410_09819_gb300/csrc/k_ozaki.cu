@@ -20,6 +20,8 @@
 #include <cuda.h>
 #include <cuda_fp8.h>
 
+#include <cstring>
+
 namespace tc {
 
 constexpr int ZS = 14;                 // digit planes per tile
@@ -33,13 +35,44 @@ constexpr int ZTHREADS = 192;          // producer, MMA, 4 drain warps
 constexpr unsigned long long ZTIMEOUT_NS = 4000000000ull;
 
 // ------------------------------------------------------------------- digit planes
+// Digits of one element in integer arithmetic (GB300 runs FP64 at 2 operations per clock per
+// SM, so a floating-point x16 / rint / subtract chain would make this kernel ALU-bound):
+// q = x 2^(56 - e) rounded to the nearest integer from the bit pattern (|q| <= 2^56 since
+// |x| <= 2^e), then balanced base-16 digits from the least significant end: d_s in [-8, 8]
+// for s >= 2, d_1 = what remains, in [-16, 16].  x 2^-e = sum_s d_s 16^-s + R 2^-e with
+// |R| <= 2^(e - 57), the splitting the emulated products assume.
+__device__ __forceinline__ long long fixed56(double x, int e) {
+    const long long bits = __double_as_longlong(x);
+    int ex = (int)((bits >> 52) & 0x7FF);
+    long long m = bits & 0xFFFFFFFFFFFFFLL;
+    if (ex == 0) ex = 1;                       // subnormal (or zero): no hidden bit
+    else m |= 1LL << 52;                       // |x| = m 2^(ex - 1075)
+    const int sh = ex - 1019 - e;              // x 2^(56 - e) = m 2^sh, sh <= 4
+    long long q;
+    if (sh >= 0) q = m << sh;
+    else if (sh > -63) q = (m + (1LL << (-sh - 1))) >> (-sh);
+    else q = 0;
+    return bits < 0 ? -q : q;
+}
+__device__ __forceinline__ void put_digits(long long q, uint8_t *P, int64_t o, int64_t bb) {
+#pragma unroll
+    for (int s = ZS - 1; s >= 1; --s) {
+        int r = (int)(q & 15);
+        if (r > 8) r -= 16;
+        q = (q - r) >> 4;
+        P[(int64_t)s * bb + o] = (uint8_t)__nv_cvt_float_to_fp8((float)r, __NV_SATFINITE, __NV_E4M3);
+    }
+    P[o] = (uint8_t)__nv_cvt_float_to_fp8((float)q, __NV_SATFINITE, __NV_E4M3);
+}
+
 // exps[t] = smallest e with amax[t] <= 2^e; planes of tile t at pool + (t*ZS + s) b^2,
-// each row-major (K-major) b x b.
+// each row-major (K-major) b x b.  The values come from tile t of W, or (alt != nullptr)
+// from the blockIdx.y-th tile of the contiguous buffer alt.
 __global__ void __launch_bounds__(256)
-k_digits(const double *W, int b, const int *tiles, const double *amax, uint8_t *pool, int *exps) {
+k_digits(const double *W, int b, const int *tiles, const double *amax, uint8_t *pool, int *exps, const double *alt) {
     __shared__ double S[32][33];
     const int t = tiles[blockIdx.y];
-    const double *T = W + (int64_t)t * b * b;
+    const double *T = alt ? alt + (int64_t)blockIdx.y * b * b : W + (int64_t)t * b * b;
     const double am = amax[t];
     int e = 0;
     if (am > 0.0) {
@@ -61,26 +94,52 @@ k_digits(const double *W, int b, const int *tiles, const double *amax, uint8_t *
         __syncthreads();
         for (int idx = threadIdx.x; idx < 1024; idx += 256) {
             const int c = idx & 31, r = idx >> 5;
-            double v = ldexp(S[r][c], -e);          // in [-1, 1]
-            const int64_t o = (int64_t)(r0 + r) * b + c0 + c;
-#pragma unroll
-            for (int s = 0; s < ZS; ++s) {
-                v = v * 16.0;                        // exact
-                const double d = rint(v);            // |d| <= 16 (s = 0), <= 8 after
-                v = v - d;                           // exact
-                P[(int64_t)s * bb + o] = (uint8_t)__nv_cvt_double_to_fp8(d, __NV_SATFINITE, __NV_E4M3);
-            }
+            put_digits(fixed56(S[r][c], e), P, (int64_t)(r0 + r) * b + c0 + c, bb);
         }
     }
 }
 
 // --------------------------------------------------------------------- update kernel
+// In-core form: one CTA per ZItem of a device table; sources of item `it` are the
+// consecutive digit slots it.xoff + n and it.yoff + n.
 struct ZArgs {
     const ZItem *items;
     const int *exps;
     int k, b;
     int *err;
     int assign;         // 0: C -= sum X Y^T;  1: C = sum X Y^T
+    __device__ bool tile(ZItem &it) const {
+        it = items[blockIdx.x];
+        return true;
+    }
+    __device__ int xsrc(const ZItem &it, int n) const { return it.xoff + n; }
+    __device__ int ysrc(const ZItem &it, int n) const { return it.yoff + n; }
+};
+
+// Out-of-core form: up to ZG_MAX output tiles of one tile column, whose sources sit in
+// arbitrary cache slots; the slot lists travel in the launch parameters.  The grid is
+// ntiles x (b/ZBM) x (b/ZBN); blocks entirely above the diagonal of a `lower` tile exit.
+struct ZGroupArgs {
+    double *C[ZG_MAX];
+    uint16_t xs[ZG_MAX][ZK_MAX];   // X_n of tile g: digit slot xs[g][n]
+    uint16_t ys[ZK_MAX];           // Y_n (shared by the group): digit slot ys[n]
+    const int *exps;
+    int k, b;
+    int *err;
+    int assign;
+    uint32_t lower;                // bit g: tile g is a diagonal tile
+    __device__ bool tile(ZItem &it) const {
+        const int nbm = b / ZBM, per = nbm * (b / ZBN);
+        const int g = blockIdx.x / per, r = blockIdx.x % per;
+        it.C = C[g];
+        it.xoff = g;
+        it.yoff = 0;
+        it.bm = (uint16_t)(r % nbm);
+        it.bn = (uint16_t)(r / nbm);
+        return !(((lower >> g) & 1u) && it.bm * ZBM + ZBM - 1 < it.bn * ZBN);
+    }
+    __device__ int xsrc(const ZItem &it, int n) const { return xs[it.xoff][n]; }
+    __device__ int ysrc(const ZItem &, int n) const { return ys[n]; }
 };
 
 __device__ __forceinline__ uint32_t z_smem(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -150,14 +209,22 @@ __device__ __forceinline__ void z_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Order of the X planes within a K block: plane s meets 14 - s partner planes, so its MMA
+// work falls from 14 units (s = 0) to 1 (s = 13); alternating long and short planes
+// (0, SU-1, 1, SU-2, ...) keeps the work per 16 KB stage even, and the TMA ring never has to
+// deliver the short planes' stages back to back.
+template <int SU>
+__device__ __forceinline__ int plane_order(int i) { return (i & 1) ? SU - 1 - (i >> 1) : (i >> 1); }
+
 // One CTA = one 128 x 32 block of one output tile: C -= sum_{n<k} X_n Y_n^T with X_n the
 // tiles (m, n) and Y_n the tiles (k, n), through their first SU digit planes (SU = 14 for FP64
 // outputs; SU = 10, i.e. pairs with s + t <= 11 and a truncation below 2^-40 of the tile scale,
 // for FP32 outputs: with 8 planes the truncation, which is relative to the operand tile's largest
 // entry, cost 50x in the factor's backward error at eps_high = 1e-9 on Matern matrices).
-template <int SU>
+template <int SU, class Args>
 __global__ void __launch_bounds__(ZTHREADS, 1)
-k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY, const ZArgs args) {
+k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+        const __grid_constant__ Args args) {
     extern __shared__ __align__(1024) uint8_t zsmem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(zsmem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *xbuf = smem;                             // ZXS x 16 KB
@@ -173,7 +240,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const ZItem it = args.items[blockIdx.x];
+    ZItem it;
+    if (!args.tile(it)) return;        // whole CTA, before any barrier or TMEM allocation
     const int k = args.k, b = args.b;
     const int kblocks = b / ZKB;
     if (threadIdx.x == 0) {
@@ -209,7 +277,7 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
             int xi = 0, yi = 0, issued_x = 0, issued_y = 0;
             bool ok = true;
             for (int n = 0; n < k && ok; ++n) {
-                const int xt = it.xoff + n, yt = it.yoff + n;
+                const int xt = args.xsrc(it, n), yt = args.ysrc(it, n);
                 for (int kb = 0; kb < kblocks && ok; ++kb, ++yi) {
                     const int ys = yi & 1;
                     if (!z_wait(yempty + ys, ((yi >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
@@ -218,8 +286,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                         z_tma(ybuf + ys * ZYSET + t * ZY_BYTES, &mapY, kb * ZKB, (yt * ZS + t) * b + it.bn * ZBN,
                               yfull + ys);
                     ++issued_y;
-                    for (int s = 0; s < SU; ++s, ++xi) {
-                        const int st = xi % ZXS;
+                    for (int i = 0; i < SU; ++i, ++xi) {
+                        const int s = plane_order<SU>(i), st = xi % ZXS;
                         if (!z_wait(xempty + st, ((xi / ZXS) & 1) ^ 1, abort_flag)) { ok = false; break; }
                         z_expect(xfull + st, ZX_BYTES);
                         z_tma(xbuf + st * ZX_BYTES, &mapX, kb * ZKB, (xt * ZS + s) * b + it.bm * ZBM, xfull + st);
@@ -253,8 +321,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                     if (!z_wait(yfull + ys, (yi >> 1) & 1, abort_flag)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t ybase = z_smem(ybuf + ys * ZYSET);
-                    for (int s = 0; s < SU; ++s, ++xi) {
-                        const int st = xi % ZXS;
+                    for (int i = 0; i < SU; ++i, ++xi) {
+                        const int s = plane_order<SU>(i), st = xi % ZXS;
                         if (!z_wait(xfull + st, (xi / ZXS) & 1, abort_flag)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t xa = z_smem(xbuf + st * ZX_BYTES);
@@ -268,9 +336,11 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                             for (int t0 = 0; t0 + s < SU; t0 += 8) {
                                 const int cnt = (SU - s - t0) < 8 ? (SU - s - t0) : 8;
                                 const uint32_t idesc = idesc0 | ((uint32_t)((cnt * ZBN) >> 3) << 17);
+                                // plane 0 comes first in every K block and covers all groups,
+                                // so it alone starts the accumulators of a source tile
                                 z_mma(tmem + (uint32_t)((s + t0) * ZBN), z_desc(xa + kk * 32),
                                       z_desc(ybase + t0 * ZY_BYTES + kk * 32), idesc,
-                                      (kb > 0 || s > 0 || kk > 0) ? 1u : 0u);
+                                      (kb > 0 || i > 0 || kk > 0) ? 1u : 0u);
                             }
                         }
                         z_commit(xempty + st);
@@ -296,7 +366,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
         for (int n = 0; n < k; ++n) {
             if (!z_wait(accf, n & 1, abort_flag)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int E = args.exps[it.xoff + n] + args.exps[it.yoff + n];
+            const int E = args.exps[args.xsrc(it, n)] + args.exps[args.ysrc(it, n)];
+            const double s_hi = ldexp(1.0, E - 32), s_lo = ldexp(1.0, E - 4 * (SU + 1));
             const uint32_t lanebase = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
             for (int c = 0; c < ZBN / 16; ++c) {
@@ -316,7 +387,7 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    run[c * 16 + j] += ldexp((double)hi[j], E - 32) + ldexp((double)lo[j], E - 4 * (SU + 1));
+                    run[c * 16 + j] = fma((double)lo[j], s_lo, fma((double)hi[j], s_hi, run[c * 16 + j]));
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -368,26 +439,35 @@ k_digits_src(const double *src, int b, int transpose, int dst, const double *ama
         __syncthreads();
         for (int idx = threadIdx.x; idx < 1024; idx += 256) {
             const int c = idx & 31, r = idx >> 5;
-            double v = ldexp(S[r][c], -e);
-            const int64_t o = (int64_t)(r0 + r) * b + c0 + c;
-#pragma unroll
-            for (int s = 0; s < ZS; ++s) {
-                v = v * 16.0;
-                const double d = rint(v);
-                v = v - d;
-                P[(int64_t)s * bb + o] = (uint8_t)__nv_cvt_double_to_fp8(d, __NV_SATFINITE, __NV_E4M3);
-            }
+            put_digits(fixed56(S[r][c], e), P, (int64_t)(r0 + r) * b + c0 + c, bb);
         }
     }
 }
 
+// max |src[e]| as the largest sign-cleared bit pattern (non-negative doubles order like their
+// bit patterns; integer maxima keep this off the FP64 pipe)
 __global__ void k_amax_ptr(const double *src, int64_t count, double *out) {
-    double m = 0.0;
+    unsigned long long m = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs(src[e]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0)
-        atomicMax(reinterpret_cast<unsigned long long *>(out), (unsigned long long)__double_as_longlong(m));
+        m = max(m, (unsigned long long)__double_as_longlong(src[e]) & 0x7FFFFFFFFFFFFFFFull);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long *>(out), m);
+}
+
+// zero the strictly upper part of a column-major b x b tile (a factored diagonal tile as L_kk)
+__global__ void k_lower_only(double *T, int b) {
+    const int64_t bb = (int64_t)b * b;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb; e += (int64_t)gridDim.x * blockDim.x)
+        if (e % b < e / b) T[e] = 0.0;
+}
+
+// tile tiles[y] of W += the y-th tile of src
+__global__ void k_add_tiles(double *W, int b, const int *tiles, const double *src) {
+    const int64_t bb = (int64_t)b * b;
+    double *T = W + (int64_t)tiles[blockIdx.y] * bb;
+    const double *S = src + (int64_t)blockIdx.y * bb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb; e += (int64_t)gridDim.x * blockDim.x)
+        T[e] += S[e];
 }
 
 __global__ void k_set_identity(double *T, int b) {
@@ -398,10 +478,12 @@ __global__ void k_set_identity(double *T, int b) {
 
 void launch_digits_src(const double *src, int b, int transpose, int dst, const double *amax, uint8_t *pool, int *exps,
                        cudaStream_t s) {
-    k_digits_src<<<64, 256, 0, s>>>(src, b, transpose, dst, amax, pool, exps);
+    const int blocks = (b / 32) * (b / 32);          // one 32 x 32 block per CTA pass, 4 CTAs per SM
+    k_digits_src<<<blocks < 608 ? blocks : 608, 256, 0, s>>>(src, b, transpose, dst, amax, pool, exps);
 }
 void launch_amax_ptr(const double *src, int64_t count, double *out, cudaStream_t s) {
-    k_amax_ptr<<<64, 256, 0, s>>>(src, count, out);
+    const int64_t want = (count + 4095) / 4096;
+    k_amax_ptr<<<want < 608 ? (int)want : 608, 256, 0, s>>>(src, count, out);
 }
 void launch_set_identity(double *T, int b, cudaStream_t s) { k_set_identity<<<64, 256, 0, s>>>(T, b); }
 
@@ -414,8 +496,19 @@ int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_ro
 size_t zgemm_smem_bytes() { return (size_t)ZXS * ZX_BYTES + 2 * ZYSET + 1024 + 256; }
 
 void launch_digits(const double *W, int b, const int *tiles, int ntiles, const double *amax, uint8_t *pool, int *exps,
-                   cudaStream_t s) {
-    if (ntiles > 0) k_digits<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, amax, pool, exps);
+                   cudaStream_t s, const double *alt) {
+    if (ntiles > 0) k_digits<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, amax, pool, exps, alt);
+}
+void launch_lower_only(double *T, int b, cudaStream_t s) { k_lower_only<<<64, 256, 0, s>>>(T, b); }
+__global__ void k_add_tile(double *dst, const double *src, int64_t count) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] += src[e];
+}
+void launch_add_tile(double *dst, const double *src, int b, cudaStream_t s) {
+    k_add_tile<<<608, 256, 0, s>>>(dst, src, (int64_t)b * b);
+}
+void launch_add_tiles(double *W, int b, const int *tiles, int ntiles, const double *src, cudaStream_t s) {
+    if (ntiles > 0) k_add_tiles<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, src);
 }
 
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
@@ -424,13 +517,41 @@ void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *ite
     static bool attr = false;
     const size_t smem = zgemm_smem_bytes();
     if (!attr) {
-        cudaFuncSetAttribute(k_zgemm<14>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<14, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<10, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     ZArgs a{items, exps, k, b, err, assign};
     if (planes == 10) k_zgemm<10><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
     else k_zgemm<14><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
+}
+
+void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGroup &g, const int *exps, int b,
+                        int *err, cudaStream_t s, int planes) {
+    if (g.ntiles <= 0 || g.k <= 0) return;
+    static bool attr = false;
+    const size_t smem = zgemm_smem_bytes();
+    if (!attr) {
+        cudaFuncSetAttribute(k_zgemm<14, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<10, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    ZGroupArgs a;
+    memset(&a, 0, sizeof a);
+    for (int t = 0; t < g.ntiles; ++t) {
+        a.C[t] = g.C[t];
+        if (g.lower[t]) a.lower |= 1u << t;
+        for (int n = 0; n < g.k; ++n) a.xs[t][n] = (uint16_t)g.xs[t][n];
+    }
+    for (int n = 0; n < g.k; ++n) a.ys[n] = (uint16_t)g.ys[n];
+    a.exps = exps;
+    a.k = g.k;
+    a.b = b;
+    a.err = err;
+    a.assign = g.assign;
+    const int per = (b / ZBM) * (b / ZBN);
+    if (planes == 10) k_zgemm<10><<<g.ntiles * per, ZTHREADS, smem, s>>>(mx, my, a);
+    else k_zgemm<14><<<g.ntiles * per, ZTHREADS, smem, s>>>(mx, my, a);
 }
 
 }  // namespace tc

@@ -51,8 +51,8 @@ struct Plan {
     std::vector<TStrip> strips;
     std::vector<PEntry> pentries;
     std::vector<LEntry> lentries;
-    std::vector<ZItem> zitems, zitems32, zinv;
-    bool inv_trsm = false;
+    std::vector<ZItem> zitems, zitems32, zinv, zinvc, zref;
+    bool inv_trsm = false, inv_refine = false;
     std::vector<int> dtiles;
     std::vector<ColPlan> cols;
     int64_t Ttot = 0;
@@ -94,9 +94,15 @@ Plan build_plan(tc_handle h, double *W, int *status) {
     }
     P.cols.resize(P.ntmax);
     const bool zmode = h->cfg.fp64_mode >= 1;
-    // explicit-inverse TRSM (fp64_mode 2): mixed precision only (its error, kappa(L_kk) u, is far
-    // below the accuracy level of a mixed-precision factorization), single matrix (one scratch)
-    P.inv_trsm = h->cfg.fp64_mode == 2 && h->mats.size() == 1 && h->mats[0].mixed;
+    // explicit-inverse TRSM (fp64_mode 2, single matrix: one scratch).  Mixed precision takes
+    // L_mk = C_mk L_kk^{-T} as it is (its error, kappa(L_kk) u, is far below the accuracy level
+    // of a mixed-precision factorization); an all-FP64 factorization adds one refinement step
+    // with the residual C_mk - X0 L_kk^T, which brings the backward error back to the level of
+    // substitution (the explicit inverse alone loses a factor ~kappa(L_kk)).
+    P.inv_trsm = h->cfg.fp64_mode == 2 && h->mats.size() == 1;
+    P.inv_refine = P.inv_trsm && !h->mats[0].mixed;
+    // L_kk^{-1} at invbuf, X0 of tile (k + i, k) at invbuf + i b^2 (sized by factor_matrices)
+    double *inv_scratch = static_cast<double *>(h->invbuf.p);
     auto T = [&](const MatDesc &M, int i, int j) { return W + (M.tile0 + tidx(i, j)) * bb; };
     const int nmat = (int)h->mats.size();
     for (int mi = 0; mi < nmat; ++mi) {
@@ -168,13 +174,23 @@ Plan build_plan(tc_handle h, double *W, int *status) {
         // TRSM of a mixed-precision column as C_mk L_kk^{-T} on the emulated engine (one matrix)
         C.v0 = (int)P.zinv.size();
         if (P.inv_trsm) {
+            // digit slots: C_mk (and later X0, R) in the tile's own slot, L_kk^{-1} in the slot of
+            // the diagonal tile (k, k), L_kk in that of (k+1, k+1) (diagonal tiles are never
+            // update operands, and (k+1, k+1) is not factored yet)
             const MatDesc &M = h->mats[0];
+            const int sinv = (int)(M.tile0 + tidx(k, k)), sl = (int)(M.tile0 + tidx(k + 1, k + 1));
             for (int m = k + 1; m < M.nt; ++m) {
                 double *Cp = T(M, m, k);
+                double *Cs = P.inv_refine ? inv_scratch + (int64_t)(m - k) * bb : nullptr;
+                const int sx = (int)(M.tile0 + tidx(m, k));
                 for (int bn = 0; bn < b / 32; ++bn)
-                    for (int bm = 0; bm < b / 128; ++bm)
-                        P.zinv.push_back({Cp, (int)(M.tile0 + tidx(m, k)), (int)(M.tile0 + tidx(k, k)), (uint16_t)bm,
-                                          (uint16_t)bn});
+                    for (int bm = 0; bm < b / 128; ++bm) {
+                        P.zinv.push_back({Cp, sx, sinv, (uint16_t)bm, (uint16_t)bn});
+                        if (P.inv_refine) {
+                            P.zinvc.push_back({Cs, sx, sinv, (uint16_t)bm, (uint16_t)bn});
+                            P.zref.push_back({Cp, sx, sl, (uint16_t)bm, (uint16_t)bn});
+                        }
+                    }
             }
         }
         C.nv = (int)P.zinv.size() - C.v0;
@@ -415,8 +431,9 @@ struct PlanDev {
     const TStrip *strips;
     const PEntry *pentries;
     const LEntry *lentries;
-    const ZItem *zitems = nullptr, *zitems32 = nullptr, *zinv = nullptr;
+    const ZItem *zitems = nullptr, *zitems32 = nullptr, *zinv = nullptr, *zinvc = nullptr, *zref = nullptr;
     double *zamax2 = nullptr;
+    double *zamax3 = nullptr;    // refinement: amax of L_kk, X0 and R (3 x Ttot)
     const int *dtiles = nullptr;
     int *zexps = nullptr;
     double *zamax = nullptr;
@@ -455,20 +472,27 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
         if ((rc = ensure(h, h->dpool, (size_t)Tt * 14 * bb))) return rc;
         const size_t oz = 0, oy = align_up(P.zitems.size() * sizeof(ZItem));
         const size_t ov = align_up(oy + P.zitems32.size() * sizeof(ZItem));
-        const size_t od = align_up(ov + P.zinv.size() * sizeof(ZItem)), oe = align_up(od + P.dtiles.size() * 4);
-        const size_t oa = align_up(oe + Tt * 4), oa2 = align_up(oa + Tt * 8), zt = align_up(oa2 + Tt * 8);
-        if (P.inv_trsm && (rc = ensure(h, h->invbuf, bb * sizeof(double)))) return rc;
+        const size_t ovc = align_up(ov + P.zinv.size() * sizeof(ZItem));
+        const size_t ovr = align_up(ovc + P.zinvc.size() * sizeof(ZItem));
+        const size_t od = align_up(ovr + P.zref.size() * sizeof(ZItem)), oe = align_up(od + P.dtiles.size() * 4);
+        const size_t oa = align_up(oe + Tt * 4), oa2 = align_up(oa + Tt * 8), oa3 = align_up(oa2 + Tt * 8);
+        const size_t zt = align_up(oa3 + (P.inv_refine ? 3 * Tt * 8 : 0));
         if ((rc = ensure(h, h->ztab, zt))) return rc;
         std::vector<char> zh(zt, 0);
         if (!P.zitems.empty()) memcpy(zh.data() + oz, P.zitems.data(), P.zitems.size() * sizeof(ZItem));
         if (!P.zitems32.empty()) memcpy(zh.data() + oy, P.zitems32.data(), P.zitems32.size() * sizeof(ZItem));
         if (!P.zinv.empty()) memcpy(zh.data() + ov, P.zinv.data(), P.zinv.size() * sizeof(ZItem));
+        if (!P.zinvc.empty()) memcpy(zh.data() + ovc, P.zinvc.data(), P.zinvc.size() * sizeof(ZItem));
+        if (!P.zref.empty()) memcpy(zh.data() + ovr, P.zref.data(), P.zref.size() * sizeof(ZItem));
         if (!P.dtiles.empty()) memcpy(zh.data() + od, P.dtiles.data(), P.dtiles.size() * 4);
         CK(cudaMemcpy(h->ztab.p, zh.data(), zt, cudaMemcpyHostToDevice));
         char *zb = static_cast<char *>(h->ztab.p);
         D.zitems = reinterpret_cast<const ZItem *>(zb + oz);
         D.zitems32 = reinterpret_cast<const ZItem *>(zb + oy);
         D.zinv = reinterpret_cast<const ZItem *>(zb + ov);
+        D.zinvc = reinterpret_cast<const ZItem *>(zb + ovc);
+        D.zref = reinterpret_cast<const ZItem *>(zb + ovr);
+        if (P.inv_refine) D.zamax3 = reinterpret_cast<double *>(zb + oa3);
         D.zamax2 = reinterpret_cast<double *>(zb + oa2);
         D.dtiles = reinterpret_cast<const int *>(zb + od);
         D.zexps = reinterpret_cast<int *>(zb + oe);
@@ -499,6 +523,7 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
     CK(cudaMemsetAsync(status, 0, (2 + nmat) * sizeof(int), h->s));
     if (D.zamax) CK(cudaMemsetAsync(D.zamax, 0, P.Ttot * sizeof(double), h->s));
     if (D.zamax2) CK(cudaMemsetAsync(D.zamax2, 0, P.Ttot * sizeof(double), h->s));
+    if (D.zamax3) CK(cudaMemsetAsync(D.zamax3, 0, 3 * P.Ttot * sizeof(double), h->s));
     if (M) {
         CK(cudaMemsetAsync(D.mx.amaxL, 0, M->T * sizeof(double), h->s));
         CK(cudaMemsetAsync(D.mx.amaxS, 0, M->T * sizeof(double), h->s));
@@ -549,27 +574,62 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
         }
         span_end(h, sp_potrf);
         if (C.nv) {
-            // L_mk = C_mk L_kk^{-T}: L_kk^{-T} by substitution on the identity (FP64), then digit
-            // planes of L_kk^{-1} and of every C_mk, and one emulated product per tile
+            // L_mk = C_mk L_kk^{-T}: L_kk^{-1} by column-parallel substitution (FP64), then digit
+            // planes of L_kk^{-1} and of every C_mk, and one emulated product per tile (three,
+            // with the refinement step, for an all-FP64 factorization)
             const int sp = spans ? span_begin(h, CAT_TRSM) : -1;
             const MatDesc &Md = h->mats[0];
             const int gkk = (int)(Md.tile0 + tidx(k, k));
             double *inv = static_cast<double *>(h->invbuf.p);
             uint8_t *pool = static_cast<uint8_t *>(h->dpool.p);
-            launch_set_identity(inv, b, h->s);
-            CK_LAUNCH();
-            launch_trsm_tile(inv, W + tidx(k, k) * bb, b, b, nullptr, h->s);
+            const double *Lkk0 = W + (Md.tile0 + tidx(k, k)) * bb;
+            if (b <= 2048) {
+                launch_trinv(Lkk0, b, inv, h->s);                     // inv = L_kk^{-1}
+            } else {                                                   // (its shared-memory column panel would not fit)
+                launch_set_identity(inv, b, h->s);
+                CK_LAUNCH();
+                launch_trsm_tile(inv, Lkk0, b, b, nullptr, h->s);     // inv = L_kk^{-T}
+            }
             CK_LAUNCH();
             launch_amax_ptr(inv, bb, D.zamax2 + gkk, h->s);
             CK_LAUNCH();
-            launch_digits_src(inv, b, 1, gkk, D.zamax2 + gkk, pool, D.zexps, h->s);
+            launch_digits_src(inv, b, b <= 2048 ? 0 : 1, gkk, D.zamax2 + gkk, pool, D.zexps, h->s);
             CK_LAUNCH();
             launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, D.zamax2, h->s);
             CK_LAUNCH();
             launch_digits(W, b, D.dtiles + C.dg0, C.ndg, D.zamax2, pool, D.zexps, h->s);
             CK_LAUNCH();
-            launch_zgemm(h->map_zx, h->map_zy, D.zinv + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1);
-            CK_LAUNCH();
+            if (!P.inv_refine) {
+                launch_zgemm(h->map_zx, h->map_zy, D.zinv + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1);
+                CK_LAUNCH();
+            } else {
+                // X0 = C L_kk^{-T};  R = C - X0 L_kk^T;  L_mk = X0 + R L_kk^{-T}  (C is overwritten by R)
+                const int Tt = (int)P.Ttot, gl = (int)(Md.tile0 + tidx(k + 1, k + 1));
+                double *Lkk = W + (Md.tile0 + tidx(k, k)) * bb, *X0 = inv + bb;
+                double *am_l = D.zamax3, *am_x = D.zamax3 + Tt, *am_r = D.zamax3 + 2 * Tt;
+                launch_lower_only(Lkk, b, h->s);
+                CK_LAUNCH();
+                launch_amax_ptr(Lkk, bb, am_l + gl, h->s);
+                CK_LAUNCH();
+                launch_digits_src(Lkk, b, 0, gl, am_l + gl, pool, D.zexps, h->s);
+                CK_LAUNCH();
+                launch_zgemm(h->map_zx, h->map_zy, D.zinvc + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1);
+                CK_LAUNCH();
+                launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, am_x, h->s, X0);
+                CK_LAUNCH();
+                launch_digits(W, b, D.dtiles + C.dg0, C.ndg, am_x, pool, D.zexps, h->s, X0);
+                CK_LAUNCH();
+                launch_zgemm(h->map_zx, h->map_zy, D.zref + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 0);
+                CK_LAUNCH();
+                launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, am_r, h->s);
+                CK_LAUNCH();
+                launch_digits(W, b, D.dtiles + C.dg0, C.ndg, am_r, pool, D.zexps, h->s);
+                CK_LAUNCH();
+                launch_zgemm(h->map_zx, h->map_zy, D.zinv + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1);
+                CK_LAUNCH();
+                launch_add_tiles(W, b, D.dtiles + C.dg0, C.ndg, X0, h->s);
+                CK_LAUNCH();
+            }
             span_end(h, sp);
         }
         if (C.nst) {
@@ -655,11 +715,23 @@ int factor_matrices(tc_handle h, tc_stats *stats, bool use_graph, const std::vec
     if (rc) return rc;
     status = static_cast<int *>(h->status.p);
     if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, h->mats.size()) * sizeof(double)))) return rc;
+    if (h->cfg.fp64_mode == 2 && h->mats.size() == 1) {
+        const size_t bb = (size_t)h->b * h->b;
+        const size_t tiles = mixed ? 1 : 1 + (size_t)h->mats[0].nt;
+        if ((rc = ensure(h, h->invbuf, tiles * bb * sizeof(double)))) return rc;
+    }
     Plan P = build_plan(h, W, status);
     MxpPlan M;
     if (mixed) M = build_mxp(h, W);
     const MxpPlan *Mp = mixed ? &M : nullptr;
-    const bool replay = use_graph && h->graph && key && *key == h->graph_key;
+    // a captured graph holds device pointers and reads the uploaded tables: it replays only
+    // while no buffer moved and no other factorization re-uploaded its tables
+    if (!use_graph && h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        h->graph_key.clear();
+    }
+    const bool replay = use_graph && h->graph && key && *key == h->graph_key && h->graph_gen == h->buf_gen;
     if (!replay) {
         PlanDev D;
         if ((rc = prepare_factor(h, P, Mp, D))) return rc;
@@ -682,6 +754,7 @@ int factor_matrices(tc_handle h, tc_stats *stats, bool use_graph, const std::vec
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate", __LINE__);
             h->graph_key = *key;
+            h->graph_gen = h->buf_gen;
         } else {
             if ((rc = execute_factor(h, P, Mp, D, true))) return rc;
         }
@@ -759,6 +832,7 @@ void tc_destroy(tc_handle h) {
         release(*d);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     release(h->bstage);
+    if (h->hcompact) cudaFreeHost(h->hcompact);
     if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
     if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);

@@ -65,12 +65,16 @@ struct tc_handle_s {
     // CUDA graph of the last batched factorization (replayed when the batch repeats)
     cudaGraphExec_t graph = nullptr;
     std::vector<int64_t> graph_key;
+    uint64_t buf_gen = 0;        // bumped whenever a device buffer is (re)allocated
+    uint64_t graph_gen = 0;      // buf_gen when the graph was captured (replay only if equal)
     DevBuf bstage;     // device copies of host-resident batch inputs
     // out-of-core: the factor lives in the caller's host matrix
     bool ooc = false;
     double *host_factor = nullptr;
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     DevBuf logdiag;
+    void *hcompact = nullptr;    // page-locked compact copies of final low-precision tiles
+    size_t hcompact_bytes = 0;
     int64_t launches = 0;
     int64_t upd_launches[4] = {0, 0, 0, 0};
 
@@ -125,6 +129,7 @@ inline int ensure(tc_handle h, DevBuf &d, size_t bytes) {
     if (d.p) cudaFree(d.p);
     d.p = nullptr;
     d.bytes = 0;
+    ++h->buf_gen;
     cudaError_t e = cudaMalloc(&d.p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -119,6 +119,10 @@ void launch_fix_padding_batched(const LEntry *e, int count, int ntmax, int b, cu
 // tile-pointer variants (out-of-core executor)
 void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s);
 void launch_trsm_tile(double *C, const double *L, int ld, int b, const int *status, cudaStream_t s);
+constexpr int TG_MAX = 16;   // tiles per grouped TRSM launch
+void launch_trinv(const double *L, int b, double *Y, cudaStream_t s);   // Y = L^{-1}, b x b
+void launch_trsm_group(double *const *C, int ntiles, const double *L, int ld, int b, const int *status,
+                       cudaStream_t s);
 void launch_logdiag_tile(const double *D, int b, int nv, double *out, cudaStream_t s);
 void launch_fix_padding_tile(double *T, int b, int nv, int diag, cudaStream_t s);
 void launch_fwd_update_tile(const double *L, int b, int i, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s);
@@ -158,12 +162,44 @@ struct ZItem {
     uint16_t bm, bn;
 };
 
+// One grouped out-of-core update launch: tiles C[t] -= sum_{n<k} X_{t,n} Y_n^T, the operands
+// given by digit-pool slot (ZG_MAX tiles and ZK_MAX sources at most per launch).
+constexpr int ZG_MAX = 16, ZK_MAX = 256;
+constexpr int QG_MAX = 16, QK_MAX = 256;
+struct ZGroup {
+    int ntiles = 0, k = 0;
+    int assign = 0;             // 0: C -= sum X Y^T;  1: C = sum X Y^T
+    double *C[ZG_MAX];
+    int lower[ZG_MAX] = {};
+    int xs[ZG_MAX][ZK_MAX];
+    int ys[ZK_MAX];
+};
+// The same for the FP16 / FP8 tensor-core updates (operand copies by cache slot).
+struct QGroup {
+    int ntiles = 0, k = 0;
+    double *C[QG_MAX];
+    int xs[QG_MAX][QK_MAX];
+    int ys[QK_MAX];
+};
+void launch_copy_slot(const double *pool, int b, int slot, int q, const double *amaxS, __half *p16, uint8_t *p8,
+                      int *e16, int *e8, cudaStream_t s);
+void launch_round_slot(double *T, int b, int p, const double *amaxL, int *e_out, cudaStream_t s);
+void launch_pack_compact(const double *T, int b, int p, const int *e, void *dst, cudaStream_t s);
+void launch_unpack_compact(const void *src, int b, int p, const int *e, double *T, cudaStream_t s);
+void launch_qgemm_group(int kind, const CUtensorMap &mx, const CUtensorMap &my, const QGroup &g, const int *exps,
+                        int b, int *err, cudaStream_t s);
+
 // ------------------------------------------------------------------ launchers (k_ozaki.cu)
 size_t zgemm_smem_bytes();
 void launch_digits(const double *W, int b, const int *tiles, int ntiles, const double *amax, uint8_t *pool, int *exps,
-                   cudaStream_t s);
+                   cudaStream_t s, const double *alt = nullptr);
+void launch_lower_only(double *T, int b, cudaStream_t s);
+void launch_add_tiles(double *W, int b, const int *tiles, int ntiles, const double *src, cudaStream_t s);
+void launch_add_tile(double *dst, const double *src, int b, cudaStream_t s);     // dst += src, one b x b tile
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
                   int b, int *err, cudaStream_t s, int planes = 14, int assign = 0);
+void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGroup &g, const int *exps, int b,
+                        int *err, cudaStream_t s, int planes = 14);
 void launch_digits_src(const double *src, int b, int transpose, int dst, const double *amax, uint8_t *pool, int *exps,
                        cudaStream_t s);
 void launch_amax_ptr(const double *src, int64_t count, double *out, cudaStream_t s);
@@ -176,7 +212,8 @@ size_t qgemm_smem_bytes();
 void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                   const CUtensorMap &b1, const QItem *items, int nitems, const int *slot, const int *exps,
                   int k, int b, int *err, cudaStream_t s);
-void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, double *amax, cudaStream_t s);
+void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, double *amax, cudaStream_t s,
+                      const double *alt = nullptr);
 void launch_store_round(double *W, int b, const int *tiles, int ntiles, const uint8_t *prec, const double *amaxL,
                         double *amaxS, cudaStream_t s);
 void launch_make_copies(const double *W, int b, const CopyJob *jobs, int njobs, const double *amaxS, float *hi,

@@ -1,6 +1,7 @@
 """Host-side simulator of the out-of-core static schedule (Algorithms 2 and 3).
 
-It walks the same left-looking task order as ``tile_chol_factor_ooc`` and applies the same
+It walks the same left-looking task order as ``tile_chol_factor_ooc`` (the accumulators of
+a tile column taken a group at a time) and applies the same
 cache policy (reuse on hit; on a miss the first free slot, else the least-recently-used
 slot that no pending task pins; the accumulator pinned through its updates (V1), the
 diagonal tile pinned until the column's TRSMs are done (V3)), so it predicts the library's
@@ -35,6 +36,7 @@ class _Cache:
         self.where = [-1] * ntiles
         self.clock = 0
         self.tile_bytes = tile_bytes
+        self.load_bytes = None
         self.r = SimResult()
 
     def acquire(self, t: int) -> int:
@@ -56,7 +58,7 @@ class _Cache:
         if self.slot_tile[v] >= 0:
             self.r.evictions += 1
             self.where[self.slot_tile[v]] = -1
-        self.r.h2d_bytes += self.tile_bytes
+        self.r.h2d_bytes += self.load_bytes(t) if self.load_bytes else self.tile_bytes
         self.slot_tile[v] = t
         self.where[t] = v
         self.clock += 1
@@ -64,40 +66,118 @@ class _Cache:
         return v
 
 
-def simulate(n: int, b: int, nslots: int, check: bool = False) -> SimResult:
-    """Counters of one out-of-core factorization of order n, tile b, with nslots device slots."""
+SMS = 152            # streaming multiprocessors of the GPU the groups are sized for
+TG_MAX = 16          # tiles per grouped TRSM launch
+ZG_MAX, ZK_MAX = 16, 256   # tiles and operand tiles per grouped emulated update launch
+
+
+ELEM_BYTES = {0: 8, 1: 4, 2: 2, 3: 1}   # FP64, FP32, FP16, FP8 (E4M3)
+
+
+def slots_for_cap(cap_bytes: int, n: int, b: int, emulated: bool = False, mixed: bool = False) -> int:
+    """Device slots the library carves out of ``cap_bytes``: an FP64 tile per slot, plus its
+    14 digit planes (one byte per element each) and 16 bytes of bookkeeping when the updates
+    are emulated on the tensor cores, plus (mixed precision) an FP16 and an E4M3 operand copy
+    and a 4-byte-per-element compact stage with 24 bytes of bookkeeping."""
+    nt = -(-n // b)
+    slot = b * b * 8 + (14 * b * b + 16 if emulated else 0) + (7 * b * b + 24 if mixed else 0)
+    ns = min(cap_bytes // slot, tidx(nt, 0) + 2)
+    return min(ns, 65535) if emulated else ns
+
+
+def ooc_shape(nslots: int, b: int, emulated: bool) -> tuple[int, int]:
+    """(accumulators per group, operand tiles per emulated update launch): the group fills
+    the GPU (a TRSM runs one CTA per 64-row strip) while its accumulators hold at most an
+    eighth of the cache, and one launch's pinned set -- the
+    diagonal tile, the group's accumulators and kc (G + 1) operands -- fits in the cache."""
+    strips = b // 64
+    g = max(1, min(TG_MAX, (2 * SMS + strips - 1) // strips, nslots // 8))
+    if emulated:
+        g = max(1, min(min(g, ZG_MAX), (nslots - 3) // 2))
+        kc = max(1, min(ZK_MAX, (nslots - 2 - g) // (g + 1)))
+        return g, kc
+    return max(1, min(g, nslots - 3)), 0
+
+
+def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = False, pmap=None) -> SimResult:
+    """Counters of one out-of-core factorization of order n, tile b, with nslots device slots
+    (``emulated``: the grouped operand order of the tensor-core updates; ``pmap``: an nt x nt
+    precision map, whose low-precision tiles go back to the host also as compact copies and
+    come in again only as those)."""
     nt = -(-n // b)
     T = tidx(nt, 0)
     nslots = min(nslots, T + 2)
     if nslots < 4:
         raise MemoryError("device tile cache below 4 tiles")
+    if pmap is not None and not emulated:
+        raise ValueError("mixed precision out of core runs on the tensor-core engine")
+    G, KC = ooc_shape(nslots, b, emulated)
     C = _Cache(nslots, T, b * b * 8)
     final = set()
+    prec = [0] * T
+    if pmap is not None:
+        for i in range(nt):
+            for j in range(i):
+                prec[tidx(i, j)] = int(pmap[i][j])
+    bb = b * b
+
+    def load_bytes(t):
+        return bb * ELEM_BYTES[prec[t]] if t in final else bb * 8
+
+    C.load_bytes = load_bytes
+
+    def operand(t):
+        s = C.acquire(t)
+        if check:
+            assert C.slot_tile[s] == t and t in final     # operands resident and final
+        return s
+
     for k in range(nt):
         diag = -1
-        for m in range(k, nt):
-            t = tidx(m, k)
-            sc = C.acquire(t)
-            C.pins[sc] += 1
-            for nn in range(k):
-                sx = C.acquire(tidx(m, nn))
-                C.pins[sx] += 1
-                sy = C.acquire(tidx(k, nn))
-                if check:
-                    # operands and accumulator resident, operands final
-                    assert C.slot_tile[sc] == t and C.slot_tile[sx] == tidx(m, nn) and C.slot_tile[sy] == tidx(k, nn)
-                    assert tidx(m, nn) in final and tidx(k, nn) in final
-                C.pins[sx] -= 1
-                C.r.tasks += 1
-            if m == k:
-                diag = sc
-            elif check:
-                assert C.slot_tile[diag] == tidx(k, k)       # V3: L_kk still resident
-            C.r.d2h_bytes += C.tile_bytes
-            C.r.written_back.append(t)
-            final.add(t)
-            if m != k:
-                C.pins[sc] -= 1
+        for g0 in range(k, nt, G):
+            ms = range(g0, min(nt, g0 + G))
+            sc = {}
+            for m in ms:
+                sc[m] = C.acquire(tidx(m, k))
+                C.pins[sc[m]] += 1
+            if emulated:
+                for n0 in range(0, k, KC):
+                    ns = range(n0, min(k, n0 + KC))
+                    held = []
+                    for nn in ns:
+                        held.append(operand(tidx(k, nn)))
+                        C.pins[held[-1]] += 1
+                    for m in ms:
+                        for nn in ns:
+                            held.append(operand(tidx(m, nn)))
+                            C.pins[held[-1]] += 1
+                    if check:
+                        assert all(C.slot_tile[sc[m]] == tidx(m, k) for m in ms)
+                        assert sum(1 for p in C.pins if p) <= nslots
+                    C.r.tasks += len(ms) * len(ns)
+                    for s in held:
+                        C.pins[s] -= 1
+            else:
+                for m in ms:
+                    for nn in range(k):
+                        sx = operand(tidx(m, nn))
+                        C.pins[sx] += 1
+                        operand(tidx(k, nn))
+                        if check:
+                            assert C.slot_tile[sc[m]] == tidx(m, k)   # V1: accumulator resident
+                        C.pins[sx] -= 1
+                        C.r.tasks += 1
+            if g0 == k:
+                diag = sc[k]
+            if check:
+                assert C.slot_tile[diag] == tidx(k, k)          # V3: L_kk resident for the TRSMs
+            for m in ms:
+                t = tidx(m, k)
+                C.r.d2h_bytes += C.tile_bytes + (bb * ELEM_BYTES[prec[t]] if prec[t] else 0)
+                C.r.written_back.append(t)
+                final.add(t)
+                if m != k:
+                    C.pins[sc[m]] -= 1
         C.pins[diag] -= 1
     if check:
         assert sorted(C.r.written_back) == list(range(T))  # every tile written back exactly once

@@ -206,3 +206,35 @@ def test_mixed_precision_inverse_trsm_mode(eps):
     ll64 = oracle.loglik(Lf, y)
     assert berr <= 1e-14
     assert abs(ll_ref - ll64) <= 10 * eps * abs(ll64)
+
+
+@pytest.mark.parametrize("nu,a,nug", [(0.5, 0.05, 1e-6), (2.5, 0.1, 1e-8)])
+def test_fp64_refined_inverse_trsm_mode(nu, a, nug):
+    # fp64_mode 2 on an all-FP64 map: L_mk = X0 + (C - X0 L^T) L^{-T}, X0 = C L^{-T}, all three
+    # products on the emulated engine.  The explicit inverse alone would lose ~kappa(L_kk) in
+    # the backward error (2e-14 vs 2.5e-16 for nu = 2.5 in a CPU model); one refinement step
+    # with the exact residual must land at the level of substitution.
+    n, b = 2048, 256
+    A = oracle.matern(inputs.uniform_points(n, 17, morton=True), 1.0, a, nu, nug)
+    At = to_dev(pack_padded(A, b))
+    with tc.Handle(0, fp64_mode=2) as H:
+        st = tc.tc_stats()
+        assert tc.tile_chol_factor(H.h, n, b, At, None, st) == 0
+        Lt = torch.empty_like(At)
+        tc.tile_chol_get_factor(H.h, Lt)
+        ld = tc.tile_chol_logdet(H.h)
+        assert st.t_trsm_ms > 0
+    with tc.Handle(0, fp64_mode=1) as H1:
+        assert tc.tile_chol_factor(H1.h, n, b, At) == 0
+        L1 = torch.empty_like(At)
+        tc.tile_chol_get_factor(H1.h, L1)
+    Lg, Ls = unpack_lower(Lt, n, b), unpack_lower(L1, n, b)
+    normA = np.linalg.norm(A)
+    be_g = np.linalg.norm(A - Lg @ Lg.T) / normA
+    be_s = np.linalg.norm(A - Ls @ Ls.T) / normA
+    assert be_g <= 1e-14 and be_g <= 4 * be_s + 1e-15, (be_g, be_s)
+    Lo = oracle.cholesky(A)
+    assert abs(ld - oracle.logdet(Lo)) <= 1e-10 * abs(oracle.logdet(Lo))
+    # forward agreement with the substitution factor, within kappa(A) u
+    kappa = np.linalg.cond(A)
+    assert np.max(np.abs(Lg - Ls)) <= 64 * kappa * 2.0 ** -53 * np.abs(Ls).max()

@@ -37,3 +37,60 @@ def test_hand_counted_two_by_two():
     # Nt = 2, 4 slots: (0,0) miss; (1,0) miss; column 1: (1,1) miss, (1,0) hit twice (X and Y)
     r = simulate(128, 64, 4)
     assert (r.misses, r.hits, r.evictions) == (3, 2, 0)
+
+
+@pytest.mark.parametrize("nt,slots,b", [(4, 4, 128), (8, 6, 256), (12, 10, 128), (16, 40, 1024), (20, 37, 2048),
+                                        (10, 200, 128)])
+def test_emulated_grouped_order_keeps_the_invariants(nt, slots, b):
+    r = simulate(nt * b, b, slots, check=True, emulated=True)
+    T = tidx(nt, 0)
+    assert r.d2h_bytes == T * b * b * 8
+    assert r.misses >= T and r.h2d_bytes == r.misses * b * b * 8
+    assert r.tasks == sum(k * (nt - k) for k in range(nt))
+
+
+def test_group_shape_fits_the_cache():
+    from paper_2410_09819_gb300.ooc_sim import ooc_shape
+    for b in (128, 256, 1024, 2048):
+        for ns in range(4, 400, 7):
+            g, kc = ooc_shape(ns, b, True)
+            assert 1 <= g <= 16 and 1 <= kc <= 256
+            # every acquisition of one launch finds an unpinned slot
+            assert ns >= 4 and (ns >= 1 + g + kc * (g + 1) or (g, kc) == (1, 1))
+            g0, _ = ooc_shape(ns, b, False)
+            assert 1 <= g0 <= max(1, ns - 3)
+
+
+def test_slots_for_cap_counts_digit_planes():
+    from paper_2410_09819_gb300.ooc_sim import slots_for_cap
+    b = 1024
+    cap = 100 * b * b * 8
+    assert slots_for_cap(cap, 64 * b, b) == 100
+    assert slots_for_cap(cap, 64 * b, b, emulated=True) == cap // (22 * b * b + 16)
+    assert slots_for_cap(cap, 2 * b, b) == 5             # never more than the matrix + 2
+
+
+def test_mixed_precision_reloads_move_compact_copies():
+    import numpy as np
+    nt, b, slots = 12, 128, 20
+    rng = np.random.default_rng(3)
+    pm = rng.integers(0, 4, (nt, nt))
+    r64 = simulate(nt * b, b, slots, emulated=True)
+    rmx = simulate(nt * b, b, slots, emulated=True, pmap=pm)
+    # same access sequence, so the same cache decisions
+    assert (rmx.hits, rmx.misses, rmx.evictions) == (r64.hits, r64.misses, r64.evictions)
+    # first touches move FP64; re-loads of final low tiles move 4/2/1 bytes per element
+    assert rmx.h2d_bytes < r64.h2d_bytes
+    T = tidx(nt, 0)
+    assert rmx.h2d_bytes >= T * b * b * 8
+    low = sum(1 for i in range(nt) for j in range(i) if pm[i][j])
+    extra = sum({1: 4, 2: 2, 3: 1}.get(int(pm[i][j]), 0) for i in range(nt) for j in range(i)) * b * b
+    assert rmx.d2h_bytes == T * b * b * 8 + extra and low > 0
+
+
+def test_all_fp64_map_is_the_fp64_schedule():
+    import numpy as np
+    nt, b = 10, 256
+    r = simulate(nt * b, b, 15, emulated=True, pmap=np.zeros((nt, nt), dtype=int))
+    r0 = simulate(nt * b, b, 15, emulated=True)
+    assert (r.h2d_bytes, r.d2h_bytes, r.misses) == (r0.h2d_bytes, r0.d2h_bytes, r0.misses)
