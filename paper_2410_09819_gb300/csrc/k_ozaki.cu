@@ -25,12 +25,13 @@
 namespace tc {
 
 constexpr int ZS = 14;                 // digit planes per tile
-constexpr int ZBM = 128, ZBN = 32;     // CTA block: 128 rows x 32 columns
+constexpr int ZBM = 128, ZBN = Z_BN;   // work item: 128 rows x 16 columns
 constexpr int ZKB = 128;               // K bytes (= E4M3 elements) per stage
-constexpr int ZXS = 6;                 // X-plane stages
+constexpr int ZXS = 8;                 // X-plane stages
+constexpr int ZYS = 3;                 // Y-set stages
 constexpr int ZX_BYTES = ZBM * ZKB;    // 16 KB: one X plane block
-constexpr int ZY_BYTES = ZBN * ZKB;    // 4 KB: one Y plane block
-constexpr int ZYSET = ZS * ZY_BYTES;   // 56 KB: all Y planes of a K block
+constexpr int ZY_BYTES = ZBN * ZKB;    // 2 KB: one Y plane block
+constexpr int ZYSET = ZS * ZY_BYTES;   // 28 KB: all Y planes of a K block
 constexpr int ZTHREADS = 192;          // producer, MMA, 4 drain warps
 constexpr unsigned long long ZTIMEOUT_NS = 4000000000ull;
 
@@ -100,16 +101,21 @@ k_digits(const double *W, int b, const int *tiles, const double *amax, uint8_t *
 }
 
 // --------------------------------------------------------------------- update kernel
-// In-core form: one CTA per ZItem of a device table; sources of item `it` are the
-// consecutive digit slots it.xoff + n and it.yoff + n.
+// Work items: one 128 x ZBN block (bm, bn) of one output tile.  The kernel is persistent:
+// CTA c takes items c, c + gridDim.x, ...; every role walks the same item sequence.
+
+// In-core form: item i is items[i]; its sources are the consecutive digit slots
+// it.xoff + n and it.yoff + n.
 struct ZArgs {
     const ZItem *items;
+    int nitems;
     const int *exps;
     int k, b;
     int *err;
     int assign;         // 0: C -= sum X Y^T;  1: C = sum X Y^T
-    __device__ bool tile(ZItem &it) const {
-        it = items[blockIdx.x];
+    __device__ int count() const { return nitems; }
+    __device__ bool tile(int i, ZItem &it) const {
+        it = items[i];
         return true;
     }
     __device__ int xsrc(const ZItem &it, int n) const { return it.xoff + n; }
@@ -117,20 +123,22 @@ struct ZArgs {
 };
 
 // Out-of-core form: up to ZG_MAX output tiles of one tile column, whose sources sit in
-// arbitrary cache slots; the slot lists travel in the launch parameters.  The grid is
-// ntiles x (b/ZBM) x (b/ZBN); blocks entirely above the diagonal of a `lower` tile exit.
+// arbitrary cache slots; the slot lists travel in the launch parameters.  Item i of the
+// ntiles x (b/ZBM) x (b/ZBN) blocks; blocks entirely above the diagonal of a `lower` tile
+// carry no work.
 struct ZGroupArgs {
     double *C[ZG_MAX];
     uint16_t xs[ZG_MAX][ZK_MAX];   // X_n of tile g: digit slot xs[g][n]
     uint16_t ys[ZK_MAX];           // Y_n (shared by the group): digit slot ys[n]
     const int *exps;
-    int k, b;
+    int k, b, ntiles;
     int *err;
     int assign;
     uint32_t lower;                // bit g: tile g is a diagonal tile
-    __device__ bool tile(ZItem &it) const {
+    __device__ int count() const { return ntiles * (b / ZBM) * (b / ZBN); }
+    __device__ bool tile(int i, ZItem &it) const {
         const int nbm = b / ZBM, per = nbm * (b / ZBN);
-        const int g = blockIdx.x / per, r = blockIdx.x % per;
+        const int g = i / per, r = i % per;
         it.C = C[g];
         it.xoff = g;
         it.yoff = 0;
@@ -216,11 +224,23 @@ __device__ __forceinline__ void z_ld16(uint32_t taddr, float (&v)[16]) {
 template <int SU>
 __device__ __forceinline__ int plane_order(int i) { return (i & 1) ? SU - 1 - (i >> 1) : (i >> 1); }
 
-// One CTA = one 128 x 32 block of one output tile: C -= sum_{n<k} X_n Y_n^T with X_n the
-// tiles (m, n) and Y_n the tiles (k, n), through their first SU digit planes (SU = 14 for FP64
-// outputs; SU = 10, i.e. pairs with s + t <= 11 and a truncation below 2^-40 of the tile scale,
-// for FP32 outputs: with 8 planes the truncation, which is relative to the operand tile's largest
-// entry, cost 50x in the factor's backward error at eps_high = 1e-9 on Matern matrices).
+// Persistent update kernel: C -= sum_{n<k} X_n Y_n^T for 128 x ZBN output blocks, X_n the
+// tiles (m, n) and Y_n the tiles (k, n), through their first SU digit planes (SU = 14 for
+// FP64 outputs; SU = 10, i.e. pairs with s + t <= 11 and a truncation below 2^-40 of the tile
+// scale, for FP32 outputs: with 8 planes the truncation, which is relative to the operand
+// tile's largest entry, cost 50x in the factor's backward error at eps_high = 1e-9).
+//   warp 0  TMA producer: per source and 128-byte K block, the SU Y planes of the block's ZBN
+//           columns (back to back, one stage of the Y ring) and the SU X planes (one stage
+//           each of the X ring), in the interleaved plane order;
+//   warp 1  MMA issuer: per X plane s, one tcgen05.mma with N = ZBN (SU - s) multiplies it by
+//           all its partners Y_0 .. Y_{SU-1-s} at once; column block t lands on accumulator
+//           group s + t, so the grouping by weight comes from the TMEM address;
+//   warps 2-5 drain: the SU group sums of a source leave TMEM (exact FP32 integers), are
+//           recombined by int64 Horner steps and added, scaled by 2^(e_x + e_y), to FP64
+//           running sums; C is written once per item.
+// The accumulators are double-buffered in TMEM (2 x SU x ZBN <= 512 columns), so the drain
+// of source q overlaps the MMAs of source q + 1, and the item stream never stops between
+// items (no per-item prologue).
 template <int SU, class Args>
 __global__ void __launch_bounds__(ZTHREADS, 1)
 k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
@@ -228,33 +248,35 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
     extern __shared__ __align__(1024) uint8_t zsmem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(zsmem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *xbuf = smem;                             // ZXS x 16 KB
-    uint8_t *ybuf = smem + ZXS * ZX_BYTES;            // 2 x 56 KB
-    uint64_t *xfull = reinterpret_cast<uint64_t *>(ybuf + 2 * ZYSET);
+    uint8_t *ybuf = smem + ZXS * ZX_BYTES;            // ZYS x (SU x ZBN rows x 128 B)
+    uint64_t *xfull = reinterpret_cast<uint64_t *>(ybuf + ZYS * ZYSET);
     uint64_t *xempty = xfull + ZXS;
     uint64_t *yfull = xempty + ZXS;
-    uint64_t *yempty = yfull + 2;
-    uint64_t *accf = yempty + 2;
-    uint64_t *acce = accf + 1;
-    uint64_t *done = acce + 1;
+    uint64_t *yempty = yfull + ZYS;
+    uint64_t *accf = yempty + ZYS;                    // [2]
+    uint64_t *acce = accf + 2;                        // [2]
+    uint64_t *done = acce + 2;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    ZItem it;
-    if (!args.tile(it)) return;        // whole CTA, before any barrier or TMEM allocation
     const int k = args.k, b = args.b;
     const int kblocks = b / ZKB;
+    const int nitems = args.count();
+    if ((int)blockIdx.x >= nitems) return;             // whole CTA, before any barrier
     if (threadIdx.x == 0) {
         for (int s = 0; s < ZXS; ++s) {
             z_init(xfull + s, 1);
             z_init(xempty + s, 1);
         }
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < ZYS; ++s) {
             z_init(yfull + s, 1);
             z_init(yempty + s, 1);
         }
-        z_init(accf, 1);
-        z_init(acce, 4);
+        for (int a = 0; a < 2; ++a) {
+            z_init(accf + a, 1);
+            z_init(acce + a, 4);
+        }
         z_init(done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -276,34 +298,39 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
         if (lane == 0) {
             int xi = 0, yi = 0, issued_x = 0, issued_y = 0;
             bool ok = true;
-            for (int n = 0; n < k && ok; ++n) {
-                const int xt = args.xsrc(it, n), yt = args.ysrc(it, n);
-                for (int kb = 0; kb < kblocks && ok; ++kb, ++yi) {
-                    const int ys = yi & 1;
-                    if (!z_wait(yempty + ys, ((yi >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                    z_expect(yfull + ys, SU * ZY_BYTES);
-                    for (int t = 0; t < SU; ++t)
-                        z_tma(ybuf + ys * ZYSET + t * ZY_BYTES, &mapY, kb * ZKB, (yt * ZS + t) * b + it.bn * ZBN,
-                              yfull + ys);
-                    ++issued_y;
-                    for (int i = 0; i < SU; ++i, ++xi) {
-                        const int s = plane_order<SU>(i), st = xi % ZXS;
-                        if (!z_wait(xempty + st, ((xi / ZXS) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                        z_expect(xfull + st, ZX_BYTES);
-                        z_tma(xbuf + st * ZX_BYTES, &mapX, kb * ZKB, (xt * ZS + s) * b + it.bm * ZBM, xfull + st);
-                        ++issued_x;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                ZItem it;
+                if (!args.tile(item, it)) continue;
+                for (int n = 0; n < k && ok; ++n) {
+                    const int xt = args.xsrc(it, n), yt = args.ysrc(it, n);
+                    for (int kb = 0; kb < kblocks && ok; ++kb, ++yi) {
+                        const int ys = yi % ZYS;
+                        if (!z_wait(yempty + ys, ((yi / ZYS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                        z_expect(yfull + ys, SU * ZY_BYTES);
+                        for (int t = 0; t < SU; ++t)
+                            z_tma(ybuf + ys * ZYSET + t * ZY_BYTES, &mapY, kb * ZKB, (yt * ZS + t) * b + it.bn * ZBN,
+                                  yfull + ys);
+                        ++issued_y;
+                        for (int i = 0; i < SU; ++i, ++xi) {
+                            const int s = plane_order<SU>(i), st = xi % ZXS;
+                            if (!z_wait(xempty + st, ((xi / ZXS) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                            z_expect(xfull + st, ZX_BYTES);
+                            z_tma(xbuf + st * ZX_BYTES, &mapX, kb * ZKB, (xt * ZS + s) * b + it.bm * ZBM, xfull + st);
+                            ++issued_x;
+                        }
                     }
                 }
             }
             if (!ok) {
                 *abort_flag = 1;
                 atomicExch(args.err, 1);
+                // let the copies still in flight land before the shared memory goes away
                 static __shared__ int never;
                 never = 0;
                 for (int q = issued_x - ZXS < 0 ? 0 : issued_x - ZXS; q < issued_x; ++q)
                     z_wait(xfull + q % ZXS, (q / ZXS) & 1, &never);
-                for (int q = issued_y - 2 < 0 ? 0 : issued_y - 2; q < issued_y; ++q)
-                    z_wait(yfull + (q & 1), (q >> 1) & 1, &never);
+                for (int q = issued_y - ZYS < 0 ? 0 : issued_y - ZYS; q < issued_y; ++q)
+                    z_wait(yfull + q % ZYS, (q / ZYS) & 1, &never);
             }
         }
     } else if (warp == 1) {
@@ -311,43 +338,39 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
         if (lane == 0) {
             // kind::f8f6f4, D F32, A/B E4M3, K-major, M = 128; N set per instruction
             const uint32_t idesc0 = (1u << 4) | ((uint32_t)(ZBM >> 4) << 24);
-            int xi = 0, yi = 0;
+            int xi = 0, yi = 0, q = 0;            // q: sources issued so far (all items)
             bool ok = true;
-            for (int n = 0; n < k && ok; ++n) {
-                if (!z_wait(acce, (n & 1) ^ 1, abort_flag)) { ok = false; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int kb = 0; kb < kblocks && ok; ++kb, ++yi) {
-                    const int ys = yi & 1;
-                    if (!z_wait(yfull + ys, (yi >> 1) & 1, abort_flag)) { ok = false; break; }
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                ZItem it;
+                if (!args.tile(item, it)) continue;
+                for (int n = 0; n < k && ok; ++n, ++q) {
+                    const int a = q & 1;
+                    if (!z_wait(acce + a, ((q >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t ybase = z_smem(ybuf + ys * ZYSET);
-                    for (int i = 0; i < SU; ++i, ++xi) {
-                        const int s = plane_order<SU>(i), st = xi % ZXS;
-                        if (!z_wait(xfull + st, (xi / ZXS) & 1, abort_flag)) { ok = false; break; }
+                    const uint32_t dbase = tmem + (uint32_t)(a * SU * ZBN);
+                    for (int kb = 0; kb < kblocks && ok; ++kb, ++yi) {
+                        const int ys = yi % ZYS;
+                        if (!z_wait(yfull + ys, (yi / ZYS) & 1, abort_flag)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t xa = z_smem(xbuf + st * ZX_BYTES);
-                        // The Y planes sit back to back in shared memory (plane t at t * 32 rows),
-                        // so one MMA with N = 32 * cnt multiplies X_s by Y_t0 .. Y_t0+cnt-1 at once,
-                        // and column block j of its result lands on group s + t0 + j (the TMEM
-                        // columns of group g are g * 32 .. g * 32 + 31): the grouping by weight
-                        // comes from the accumulator address.  N is at most 256 per instruction.
+                        const uint32_t ybase = z_smem(ybuf + ys * ZYSET);
+                        for (int i = 0; i < SU; ++i, ++xi) {
+                            const int s = plane_order<SU>(i), st = xi % ZXS;
+                            if (!z_wait(xfull + st, (xi / ZXS) & 1, abort_flag)) { ok = false; break; }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t xa = z_smem(xbuf + st * ZX_BYTES);
+                            const uint32_t idesc = idesc0 | ((uint32_t)(((SU - s) * ZBN) >> 3) << 17);
 #pragma unroll
-                        for (int kk = 0; kk < ZKB / 32; ++kk) {
-                            for (int t0 = 0; t0 + s < SU; t0 += 8) {
-                                const int cnt = (SU - s - t0) < 8 ? (SU - s - t0) : 8;
-                                const uint32_t idesc = idesc0 | ((uint32_t)((cnt * ZBN) >> 3) << 17);
+                            for (int kk = 0; kk < ZKB / 32; ++kk)
                                 // plane 0 comes first in every K block and covers all groups,
                                 // so it alone starts the accumulators of a source tile
-                                z_mma(tmem + (uint32_t)((s + t0) * ZBN), z_desc(xa + kk * 32),
-                                      z_desc(ybase + t0 * ZY_BYTES + kk * 32), idesc,
-                                      (kb > 0 || i > 0 || kk > 0) ? 1u : 0u);
-                            }
+                                z_mma(dbase + (uint32_t)(s * ZBN), z_desc(xa + kk * 32), z_desc(ybase + kk * 32),
+                                      idesc, (kb > 0 || i > 0 || kk > 0) ? 1u : 0u);
+                            z_commit(xempty + st);
                         }
-                        z_commit(xempty + st);
+                        if (ok) z_commit(yempty + ys);
                     }
-                    if (ok) z_commit(yempty + ys);
+                    if (ok) z_commit(accf + a);
                 }
-                if (ok) z_commit(accf);
             }
             if (!ok) {
                 *abort_flag = 1;
@@ -359,24 +382,27 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
     } else {
         // --------------------------------------------------------------- drain + epilogue
         const int quarter = warp & 3;
-        double run[ZBN];
-#pragma unroll
-        for (int j = 0; j < ZBN; ++j) run[j] = 0.0;
         bool ok = true;
-        for (int n = 0; n < k; ++n) {
-            if (!z_wait(accf, n & 1, abort_flag)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int E = args.exps[args.xsrc(it, n)] + args.exps[args.ysrc(it, n)];
-            const double s_hi = ldexp(1.0, E - 32), s_lo = ldexp(1.0, E - 4 * (SU + 1));
-            const uint32_t lanebase = tmem + ((uint32_t)(quarter * 32) << 16);
+        int q = 0;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            ZItem it;
+            if (!args.tile(item, it)) continue;
+            double run[ZBN];
 #pragma unroll
-            for (int c = 0; c < ZBN / 16; ++c) {
-                long long hi[16], lo[16];
+            for (int j = 0; j < ZBN; ++j) run[j] = 0.0;
+            for (int n = 0; n < k; ++n, ++q) {
+                const int a = q & 1;
+                if (!z_wait(accf + a, (q >> 1) & 1, abort_flag)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int E = args.exps[args.xsrc(it, n)] + args.exps[args.ysrc(it, n)];
+                const double s_hi = ldexp(1.0, E - 32), s_lo = ldexp(1.0, E - 4 * (SU + 1));
+                const uint32_t lanebase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * SU * ZBN);
+                long long hi[ZBN], lo[ZBN];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+                for (int j = 0; j < ZBN; ++j) hi[j] = lo[j] = 0;
                 for (int g = 0; g < SU; ++g) {
                     float v[16];
-                    z_ld16(lanebase + (uint32_t)(g * ZBN + c * 16), v);
+                    z_ld16(lanebase + (uint32_t)(g * ZBN), v);
                     if (g < 7) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j) hi[j] = hi[j] * 16 + __float2ll_rn(v[j]);
@@ -385,25 +411,24 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                         for (int j = 0; j < 16; ++j) lo[j] = lo[j] * 16 + __float2ll_rn(v[j]);
                     }
                 }
+                // the accumulator buffer is free for source q + 2 once every lane has read it
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) z_arrive(acce + a);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    run[c * 16 + j] = fma((double)lo[j], s_lo, fma((double)hi[j], s_hi, run[c * 16 + j]));
+                for (int j = 0; j < ZBN; ++j) run[j] = fma((double)lo[j], s_lo, fma((double)hi[j], s_hi, run[j]));
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) z_arrive(acce);
+            if (!ok) break;
+            const int row = it.bm * ZBM + quarter * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < ZBN; ++j) {
+                double *c = it.C + (int64_t)(it.bn * ZBN + j) * b + row;
+                *c = args.assign ? run[j] : *c - run[j];
+            }
         }
         if (!ok) {
             *abort_flag = 1;
             atomicExch(args.err, 1);
-        } else {
-            const int row = it.bm * ZBM + quarter * 32 + lane;
-#pragma unroll
-            for (int j = 0; j < ZBN; ++j) {
-                const int col = it.bn * ZBN + j;
-                double *c = it.C + (int64_t)col * b + row;
-                *c = args.assign ? run[j] : *c - run[j];
-            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -493,7 +518,17 @@ int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_ro
     return make_pool_map(map, pool, rows / b, b, 1, box_rows);
 }
 
-size_t zgemm_smem_bytes() { return (size_t)ZXS * ZX_BYTES + 2 * ZYSET + 1024 + 256; }
+size_t zgemm_smem_bytes() { return (size_t)ZXS * ZX_BYTES + ZYS * ZYSET + 1024 + 256; }
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    }
+    return n;
+}
 
 void launch_digits(const double *W, int b, const int *tiles, int ntiles, const double *amax, uint8_t *pool, int *exps,
                    cudaStream_t s, const double *alt) {
@@ -521,9 +556,10 @@ void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *ite
         cudaFuncSetAttribute(k_zgemm<10, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    ZArgs a{items, exps, k, b, err, assign};
-    if (planes == 10) k_zgemm<10><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
-    else k_zgemm<14><<<nitems, ZTHREADS, smem, s>>>(mx, my, a);
+    ZArgs a{items, nitems, exps, k, b, err, assign};
+    const int grid = nitems < sm_count() ? nitems : sm_count();      // persistent: one CTA per SM
+    if (planes == 10) k_zgemm<10><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else k_zgemm<14><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
 }
 
 void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGroup &g, const int *exps, int b,
@@ -547,11 +583,13 @@ void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGro
     a.exps = exps;
     a.k = g.k;
     a.b = b;
+    a.ntiles = g.ntiles;
     a.err = err;
     a.assign = g.assign;
-    const int per = (b / ZBM) * (b / ZBN);
-    if (planes == 10) k_zgemm<10><<<g.ntiles * per, ZTHREADS, smem, s>>>(mx, my, a);
-    else k_zgemm<14><<<g.ntiles * per, ZTHREADS, smem, s>>>(mx, my, a);
+    const int items = g.ntiles * (b / ZBM) * (b / ZBN);
+    const int grid = items < sm_count() ? items : sm_count();        // persistent: one CTA per SM
+    if (planes == 10) k_zgemm<10><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else k_zgemm<14><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
 }
 
 }  // namespace tc

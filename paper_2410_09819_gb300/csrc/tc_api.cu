@@ -129,7 +129,7 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                         // FP32 output: 10 digit planes of each operand, FP64 running sums
                         double *Cp = T(M, m, k);
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
-                        for (int bn = 0; bn < b / 32; ++bn)
+                        for (int bn = 0; bn < b / Z_BN; ++bn)
                             for (int bm = 0; bm < b / 128; ++bm)
                                 P.zitems32.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn});
                         P.update_flops[TC_FP32] += 2.0 * (double)b * b * K;
@@ -140,9 +140,9 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                         // emulated FP64: 128 x 32 blocks (the diagonal SYRK keeps blocks reaching the lower part)
                         double *Cp = T(M, m, k);
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
-                        for (int bn = 0; bn < b / 32; ++bn)
+                        for (int bn = 0; bn < b / Z_BN; ++bn)
                             for (int bm = 0; bm < b / 128; ++bm)
-                                if (m != k || bm * 128 + 127 >= bn * 32)
+                                if (m != k || bm * 128 + 127 >= bn * Z_BN)
                                     P.zitems.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn});
                         P.update_flops[TC_FP64] += (m == k ? 1.0 : 2.0) * (double)b * b * K;
                         continue;
@@ -183,7 +183,7 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 double *Cp = T(M, m, k);
                 double *Cs = P.inv_refine ? inv_scratch + (int64_t)(m - k) * bb : nullptr;
                 const int sx = (int)(M.tile0 + tidx(m, k));
-                for (int bn = 0; bn < b / 32; ++bn)
+                for (int bn = 0; bn < b / Z_BN; ++bn)
                     for (int bm = 0; bm < b / 128; ++bm) {
                         P.zinv.push_back({Cp, sx, sinv, (uint16_t)bm, (uint16_t)bn});
                         if (P.inv_refine) {
@@ -498,7 +498,7 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
         D.zexps = reinterpret_cast<int *>(zb + oe);
         D.zamax = reinterpret_cast<double *>(zb + oa);
         if (make_digit_map(&h->map_zx, h->dpool.p, Tt * 14 * h->b, h->b, 128) ||
-            make_digit_map(&h->map_zy, h->dpool.p, Tt * 14 * h->b, h->b, 32))
+            make_digit_map(&h->map_zy, h->dpool.p, Tt * 14 * h->b, h->b, Z_BN))
             return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the digit planes");
     }
     D.mixed = M != nullptr;

@@ -165,6 +165,7 @@ struct ZItem {
 // One grouped out-of-core update launch: tiles C[t] -= sum_{n<k} X_{t,n} Y_n^T, the operands
 // given by digit-pool slot (ZG_MAX tiles and ZK_MAX sources at most per launch).
 constexpr int ZG_MAX = 16, ZK_MAX = 256;
+constexpr int Z_BN = 16;     // columns of one emulated-update work item (rows: 128)
 constexpr int QG_MAX = 16, QK_MAX = 256;
 struct ZGroup {
     int ntiles = 0, k = 0;

@@ -249,7 +249,7 @@ int init_cache(tc_handle h, TileCache &C, double *host, int nt, int b, bool digi
         C.e16 = C.exps + nd;
         C.e8 = C.e16 + nd;
         C.tile_e = C.e8 + nd;
-        if (make_digit_map(&C.mx, C.dpool, nd * 14 * b, b, 128) || make_digit_map(&C.my, C.dpool, nd * 14 * b, b, 32))
+        if (make_digit_map(&C.mx, C.dpool, nd * 14 * b, b, 128) || make_digit_map(&C.my, C.dpool, nd * 14 * b, b, Z_BN))
             return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the digit-plane cache");
         C.dig.assign(ns, 0);
         C.has_amax.assign(ns, 0);
