@@ -54,6 +54,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_N)
+    ap.add_argument("--no-baselines", action="store_true",
+                    help="skip the comparison factorizations (cuSOLVER potrf, the DFMA FP64 path)")
+    ap.add_argument("--ooc-policy", default="V3", choices=["V3", "V2", "V1", "async", "sync"],
+                    help="out-of-core scheduling policy (Section III-C)")
     ap.add_argument("--ooc-mxp", action="store_true",
                     help="out-of-core workload in four precisions (map at eps_high 1e-9, FP64 band 2)")
     return ap.parse_args()
@@ -281,6 +285,20 @@ def run_ours(args, ws, rank, local):
                         "solve_berr_mxp": berr_mxp, "solve_berr_fp64": berr64,
                         "reference": "same matrix, all-FP64 map, emulated FP64 updates, refined solve"}
 
+    comparisons = None
+    if rank == 0 and not args.no_baselines:
+        comparisons = {}
+        src = Ah if not args.no_e2e else A
+        if w.mixed:
+            # the FP64 path of this library on the same matrix (all-FP64 map, same engine)
+            s64 = tc.tc_stats()
+            if tc.tile_chol_factor(H.h, n, b, src, None, s64) == 0:
+                comparisons["fp64_same_engine"] = {"value": flops / (s64.t_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                                                   "t_factor_ms": s64.t_ms,
+                                                   "mxp_factor_speedup": s64.t_ms / st.t_ms}
+        else:
+            comparisons.update(fp64_baselines(tc, n, b, src, local, stream))
+
     if not args.no_e2e:
         del Ah
 
@@ -304,6 +322,7 @@ def run_ours(args, ws, rank, local):
                        else "factor+solve(1 RHS, <=2 refinement)+loglik"},
             "roofline": roofline,
             "accuracy": accuracy,
+            "comparisons": comparisons,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
@@ -317,6 +336,50 @@ def run_ours(args, ws, rank, local):
         }
         print(json.dumps(line), flush=True)
     H.close()
+
+
+def fp64_baselines(tc, n, b, A, local, stream):
+    """Context numbers on the same matrix, outside the timed region: cuSOLVER potrf (through
+    torch.linalg.cholesky on the dense matrix) and this library's FP64 path on the DFMA pipe
+    (fp64_mode 0).  Each is one factorization after a small warm-up."""
+    import torch
+    out = {}
+    dev = torch.device("cuda", local)
+    flops = n ** 3 / 3.0
+    # DFMA path
+    with tc.Handle(local, stream=stream.cuda_stream, fp64_mode=0) as H0:
+        st = tc.tc_stats()
+        if tc.tile_chol_factor(H0.h, n, b, A, None, st) == 0:
+            out["fp64_dfma_path"] = {"value": flops / (st.t_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                                     "t_factor_ms": st.t_ms, "what": "this library, fp64_mode 0 (DFMA updates)"}
+    torch.cuda.empty_cache()
+    # cuSOLVER: dense lower triangle assembled from the tiles (plumbing only)
+    Ad = A if A.is_cuda else A.to(dev)
+    D = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    nt = -(-n // b)
+    off = 0
+    for m in range(nt):
+        row = Ad[off:off + (m + 1) * b * b].view(m + 1, b, b).permute(2, 0, 1).reshape(b, (m + 1) * b)
+        r1 = min((m + 1) * b, n)
+        D[m * b:r1, :min((m + 1) * b, n)] = row[:r1 - m * b, :min((m + 1) * b, n)]
+        off += (m + 1) * b * b
+    del Ad
+    D.tril_()                            # diagonal tiles may hold their upper part too
+    D += D.T.triu(1)                     # the symmetric matrix
+    torch.linalg.cholesky_ex(D[:2048, :2048])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    Lc, info = torch.linalg.cholesky_ex(D)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    if int(info.item()) == 0:
+        out["cusolver_potrf"] = {"value": flops / t / 1e12, "unit": "TFLOP/s", "t_factor_ms": t * 1e3,
+                                 "what": "torch.linalg.cholesky (cuSOLVER potrf) on the dense n x n matrix"}
+    del D, Lc
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(w, ns, pts):
@@ -569,7 +632,9 @@ def run_ooc(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     T = tc.tile_count(n, b)
     cap = int(inputs.OOC_CACHE_FRACTION * T * b * b * 8)
-    H = tc.Handle(local, stream=stream.cuda_stream, device_cap_bytes=cap, fp64_mode=args.fp64_mode)
+    from paper_2410_09819_gb300.ooc_sim import POLICIES, simulate, slots_for_cap
+    H = tc.Handle(local, stream=stream.cuda_stream, device_cap_bytes=cap, fp64_mode=args.fp64_mode,
+                  ooc=POLICIES.index(args.ooc_policy))
     link = measure_link(dev)
     pts = inputs.uniform_points(n, w.seed + 1000 * rank, w.morton)
     host0 = torch.empty(T * b * b, dtype=torch.float64, pin_memory=True)
@@ -648,7 +713,18 @@ def run_ooc(args, ws, rank, local):
         if args.fp64_mode >= 1:
             line["roofline"]["kernel"] = "k_zgemm (grouped out-of-core form)"
         line["config"]["fp64_updates"] = "emulated (E4M3 digit planes)" if args.fp64_mode >= 1 else "DFMA"
+        # host-link volume of every scheduling policy at this size and cache, from the schedule
+        # simulator (which the tests hold equal to the library's counters)
+        emu = args.fp64_mode >= 1
+        ns = slots_for_cap(cap, n, b, emulated=emu, mixed=args.ooc_mxp)
+        pm2 = pmap.numpy().reshape(nt, nt) if pmap is not None else None
+        predicted = {}
+        for pol in POLICIES:
+            r = simulate(n, b, ns, emulated=emu, pmap=pm2, policy=pol)
+            predicted[pol] = {"h2d_bytes": r.h2d_bytes, "d2h_bytes": r.d2h_bytes}
+        line["ooc_policy"] = args.ooc_policy
         line["ooc_link"] = {"h2d_bytes": h2d, "d2h_bytes": d2h, "h2d_gbs": h2d / tf / 1e9, "d2h_gbs": d2h / tf / 1e9,
+                            "policy_volumes_predicted": predicted,
                             "link_peak_gbs": link, "h2d_frac": (h2d / tf / 1e9) / link["h2d"],
                             "cache_hits": st.cache_hits, "cache_misses": st.cache_misses,
                             "evictions": st.evictions, "solve_h2d_note": "solve streams the factor again"}

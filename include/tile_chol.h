@@ -65,7 +65,17 @@ typedef struct tc_handle_s *tc_handle;
 typedef struct {
     int device;                 /* CUDA device ordinal (default 0) */
     void *stream;               /* cudaStream_t to run on; NULL: the handle makes one */
-    int ooc;                    /* reserved (out-of-core runs go through tile_chol_factor_ooc) */
+    int ooc;                    /* tile_chol_factor_ooc scheduling policy (Section III-C):
+                                   0 V3 (default): accumulators resident through their
+                                     updates, operand tiles cached (LRU), L_kk pinned until
+                                     its column's TRSMs are done;
+                                   1 V2: as V3 without the L_kk pin;
+                                   2 V1: accumulators resident, no operand reuse;
+                                   3 async: no reuse at all; every update step loads its
+                                     accumulator and copies it back;
+                                   4 sync: as async with every copy on the compute stream
+                                     (no copy / compute overlap).
+                                   Other values: TC_ERR_ARG. */
     int64_t device_cap_bytes;   /* tile_chol_factor_ooc: device tile-cache cap in bytes;
                                    0: free device memory minus 4 GiB */
     int prefetch_depth;         /* reserved: tile_chol_factor_ooc enqueues its whole static
@@ -79,11 +89,14 @@ typedef struct {
                                       outputs: normwise FP64 accuracy; 10 for FP32 outputs:
                                       below 2^-40 of the tile scale); needs 14 b^2 extra
                                       bytes per lower tile and a tile size multiple of 128;
-                                   2: as 1, and in a mixed-precision factorization of one
-                                      matrix the TRSMs run as L_mk = C_mk L_kk^{-T} on the
-                                      emulated engine (L_kk^{-T} by FP64 substitution on the
-                                      identity); the error kappa(L_kk) u of that form is far
-                                      below a mixed-precision factor's accuracy level */
+                                   2: as 1, and the TRSMs of a one-matrix factorization
+                                      (in core or out of core) run on the emulated engine as
+                                      products with L_kk^{-1} (from FP64 substitution):
+                                      low-precision tiles as L_mk = C_mk L_kk^{-T}, whose
+                                      error kappa(L_kk) u is far below their accuracy
+                                      level; FP64 tiles with one refinement step,
+                                      X0 = C L^{-T}, L_mk = X0 + (C - X0 L^T) L^{-T}, which
+                                      keeps the backward error at substitution's level */
     int reserved[7];
 } tc_config;
 

@@ -39,6 +39,12 @@ namespace {
 
 enum OpForm { OP_Z14 = 0, OP_Z10, OP_Q16, OP_Q8, OP_N };
 
+// Scheduling policies of Section III-C (tc_config.ooc): V3 the default; V2 without the
+// diagonal pin; V1 without operand reuse; async without accumulator residency (every update
+// step loads its accumulator and copies it back); sync as async with every copy on the
+// compute stream (no overlap).
+enum OocPolicy { OOC_V3 = 0, OOC_V2 = 1, OOC_V1 = 2, OOC_ASYNC = 3, OOC_SYNC = 4 };
+
 inline int elem_bytes(int p) { return p == TC_FP32 ? 4 : p == TC_FP16 ? 2 : p == TC_FP8 ? 1 : 8; }
 
 struct TileCache {
@@ -66,6 +72,7 @@ struct TileCache {
     size_t tile_bytes = 0;
     cudaStream_t cs, h2d, d2h;
     std::vector<int> slot_tile, pins, where;
+    std::vector<int> prev_tile;        // tile a free slot held before it was dropped (-1: none)
     std::vector<uint64_t> last;
     std::vector<cudaEvent_t> ready, used;
     std::vector<cudaEvent_t> tile_wb;
@@ -106,12 +113,14 @@ struct TileCache {
                 }
         }
         if (v < 0) return -1;
+        // the tile the slot held last (evicted now, or dropped earlier): its write-back reads
+        // the slot, so the copy into it waits for that write-back
+        const int old = slot_tile[v] >= 0 ? slot_tile[v] : prev_tile[v];
         if (slot_tile[v] >= 0) {
-            const int old = slot_tile[v];
             ++evictions;
             where[old] = -1;
-            if (wb_pending[old]) cudaStreamWaitEvent(h2d, tile_wb[old], 0);   // its write-back reads the slot
         }
+        if (old >= 0 && wb_pending[old]) cudaStreamWaitEvent(h2d, tile_wb[old], 0);
         cudaStreamWaitEvent(h2d, used[v], 0);                                  // last kernel that read the slot
         const bool packed = load && final_[t] && compact(t);
         if (load) {
@@ -169,9 +178,27 @@ struct TileCache {
         return s;
     }
 
+    // drop slot s from the cache (policies without reuse); its next use re-loads the tile
+    void forget(int s) {
+        if (s < 0 || pins[s] != 0 || slot_tile[s] < 0) return;
+        where[slot_tile[s]] = -1;
+        prev_tile[s] = slot_tile[s];
+        slot_tile[s] = -1;
+    }
+
     // Algorithm 2's memcpy_GPU_to_CPU: final tile back to the host matrix (and, for a
-    // low-precision tile, rounded to its stored value first and its compact copy saved)
-    void write_back(int t, int s) {
+    // low-precision tile, rounded to its stored value first and its compact copy saved);
+    // `partial`: an accumulator that is not final yet (async policies), copied back as is
+    void write_back(int t, int s, bool partial = false) {
+        if (partial) {
+            cudaEventRecord(used[s], cs);
+            cudaStreamWaitEvent(d2h, used[s], 0);
+            cudaMemcpyAsync(host + (int64_t)t * bb, ptr(s), tile_bytes, cudaMemcpyDeviceToHost, d2h);
+            d2h_bytes += (int64_t)tile_bytes;
+            cudaEventRecord(wb_event(t), d2h);
+            wb_pending[t] = 1;
+            return;
+        }
         const int p = prec.empty() ? TC_FP64 : prec[t];
         if (p != TC_FP64) {
             const int sp = span_begin(h, CAT_CONVERT);
@@ -297,7 +324,9 @@ int init_cache(tc_handle h, TileCache &C, double *host, int nt, int b, bool digi
     C.cs = h->s;
     C.h2d = h->s_h2d;
     C.d2h = h->s_d2h;
+    if (h->cfg.ooc == OOC_SYNC) C.h2d = C.d2h = h->s;      // no copy / compute overlap
     C.slot_tile.assign(ns, -1);
+    C.prev_tile.assign(ns, -1);
     C.pins.assign(ns, 0);
     C.last.assign(ns, 0);
     C.where.assign(T, -1);
@@ -368,6 +397,9 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
             }
     }
     const bool zmode = h->cfg.fp64_mode >= 1;
+    const int policy = h->cfg.ooc;
+    if (policy < OOC_V3 || policy > OOC_SYNC) return set_err(h, TC_ERR_ARG, "tc_config.ooc must be 0..4 (V3, V2, V1, async, sync)");
+    const bool keep_ops = policy <= OOC_V2, pin_diag = policy == OOC_V3, keep_acc = policy <= OOC_V1;
     if (mixed && !zmode)
         return set_err(h, TC_ERR_UNSUPPORTED, "out-of-core mixed precision runs on the tensor-core engine (fp64_mode >= 1)");
     if (zmode && b % 128)
@@ -422,21 +454,32 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
         for (int g0 = k; g0 < nt; g0 += S.group) {
             const int g1 = std::min(nt, g0 + S.group), G = g1 - g0;
             int sc[ZG_MAX];
-            for (int m = g0; m < g1; ++m) {
-                ACQ(s_acc, (int)tidx(m, k), true);       // V1: accumulators stay resident
-                sc[m - g0] = s_acc;
-                ++C.pins[s_acc];
-                if (m == nt - 1 && nv_last != b) {
-                    launch_fix_padding_tile(C.ptr(s_acc), b, nv_last, m == k, h->s);
-                    CK_LAUNCH();
-                }
-            }
+            // V1-V3: the accumulators stay resident (and pinned) through their updates
+#define ACQ_ACCS()                                                                            \
+    for (int m = g0; m < g1; ++m) {                                                           \
+        ACQ(s_acc, (int)tidx(m, k), true);                                                    \
+        sc[m - g0] = s_acc;                                                                   \
+        ++C.pins[s_acc];                                                                      \
+        if (m == nt - 1 && nv_last != b) {                                                    \
+            launch_fix_padding_tile(C.ptr(s_acc), b, nv_last, m == k, h->s);                  \
+            CK_LAUNCH();                                                                      \
+        }                                                                                     \
+    }
+            // async / sync: every update step copies its accumulators back and lets them go
+#define RELEASE_ACCS()                                                                        \
+    for (int m = g0; m < g1; ++m) {                                                           \
+        C.write_back((int)tidx(m, k), sc[m - g0], true);                                      \
+        --C.pins[sc[m - g0]];                                                                 \
+        C.forget(sc[m - g0]);                                                                 \
+    }
+            if (keep_acc) ACQ_ACCS();
             if (zmode) {
                 bool present[OP_N] = {false, false, false, false};
                 for (int m = g0; m < g1; ++m) present[form_of(m, k)] = true;
                 for (int n0 = 0; n0 < k; n0 += S.chunk) {
                     const int kc = std::min(S.chunk, k - n0);
                     int ys[ZK_MAX], xs[ZG_MAX][ZK_MAX];
+                    if (!keep_acc) ACQ_ACCS();
                     for (int nn = n0; nn < n0 + kc; ++nn) {
                         ACQ(sy, (int)tidx(k, nn), true);
                         for (int f = 0; f < OP_N; ++f)
@@ -496,15 +539,31 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                         C.touched(ys[q]);
                         --C.pins[ys[q]];
                     }
+                    if (!keep_ops) {                 // V1 / async / sync: no operand table
+                        for (int m = g0; m < g1; ++m)
+                            for (int q = 0; q < kc; ++q) C.forget(xs[m - g0][q]);
+                        for (int q = 0; q < kc; ++q) C.forget(ys[q]);
+                    }
+                    if (!keep_acc) RELEASE_ACCS();
                 }
             } else {
                 for (int m = g0; m < g1; ++m)
                     for (int nn = 0; nn < k; ++nn) {
+                        int sa = keep_acc ? sc[m - g0] : -1;
+                        if (!keep_acc) {
+                            ACQ(s1, (int)tidx(m, k), true);
+                            sa = s1;
+                            ++C.pins[sa];
+                            if (m == nt - 1 && nv_last != b) {
+                                launch_fix_padding_tile(C.ptr(sa), b, nv_last, m == k, h->s);
+                                CK_LAUNCH();
+                            }
+                        }
                         ACQ(sx, (int)tidx(m, nn), true);
                         ++C.pins[sx];
                         ACQ(sy, (int)tidx(k, nn), true);
                         const int spd = span_begin(h, CAT_UPD64);   // operands are resident from here
-                        launch_dgemm_tile({C.ptr(sc[m - g0]), C.ptr(sx), C.ptr(sy), b, b, b, m == k ? 1 : 0}, b, h->s);
+                        launch_dgemm_tile({C.ptr(sa), C.ptr(sx), C.ptr(sy), b, b, b, m == k ? 1 : 0}, b, h->s);
                         span_end(h, spd);
                         CK_LAUNCH();
                         ++h->upd_launches[TC_FP64];
@@ -512,7 +571,26 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                         C.touched(sx);
                         C.touched(sy);
                         --C.pins[sx];
+                        if (!keep_ops) {
+                            C.forget(sx);
+                            C.forget(sy);
+                        }
+                        if (!keep_acc) {
+                            C.write_back((int)tidx(m, k), sa, true);
+                            --C.pins[sa];
+                            C.forget(sa);
+                        }
                     }
+            }
+            if (!keep_acc) ACQ_ACCS();               // the accumulators once more, for POTRF / TRSM
+            if (g0 != k && !pin_diag) {              // V2 and below: L_kk may have left the cache
+                ACQ(sd, (int)tidx(k, k), true);
+                diag_slot = sd;
+                ++C.pins[sd];
+                if (inv_trsm && k + 1 < nt) {
+                    C.planes_of(C.ptr(sd), sd, 0);
+                    C.dig[sd] = C.has_amax[sd] = 0;
+                }
             }
             if (g0 == k) {
                 double *D = C.ptr(sc[0]);
@@ -611,9 +689,17 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                 ++tiles_p[m == k ? TC_FP64 : pm[(size_t)m * nt + k]];
                 if (m != k) --C.pins[sc[m - g0]];
             }
+            if (!pin_diag) {                         // V3 alone keeps L_kk pinned for the column
+                --C.pins[diag_slot];
+                if (!keep_ops) C.forget(diag_slot);
+            }
+            if (!keep_ops)
+                for (int m = std::max(g0, k + 1); m < g1; ++m) C.forget(sc[m - g0]);
         }
-        --C.pins[diag_slot];
+        if (pin_diag) --C.pins[diag_slot];
     }
+#undef ACQ_ACCS
+#undef RELEASE_ACCS
     std::vector<double> ld(nt);
     int st2[2] = {0, 0};
     CK(cudaMemcpyAsync(ld.data(), logdiag, nt * sizeof(double), cudaMemcpyDeviceToHost, h->s));

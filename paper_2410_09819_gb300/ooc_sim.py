@@ -65,6 +65,11 @@ class _Cache:
         self.last[v] = self.clock
         return v
 
+    def forget(self, s: int) -> None:
+        if self.pins[s] == 0 and self.slot_tile[s] >= 0:
+            self.where[self.slot_tile[s]] = -1
+            self.slot_tile[s] = -1
+
 
 SMS = 152            # streaming multiprocessors of the GPU the groups are sized for
 TG_MAX = 16          # tiles per grouped TRSM launch
@@ -99,11 +104,16 @@ def ooc_shape(nslots: int, b: int, emulated: bool) -> tuple[int, int]:
     return max(1, min(g, nslots - 3)), 0
 
 
-def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = False, pmap=None) -> SimResult:
+POLICIES = ("V3", "V2", "V1", "async", "sync")   # tc_config.ooc = 0 .. 4 (Section III-C)
+
+
+def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = False, pmap=None,
+             policy: str = "V3") -> SimResult:
     """Counters of one out-of-core factorization of order n, tile b, with nslots device slots
     (``emulated``: the grouped operand order of the tensor-core updates; ``pmap``: an nt x nt
     precision map, whose low-precision tiles go back to the host also as compact copies and
-    come in again only as those)."""
+    come in again only as those; ``policy``: V3 (the default), V2 without the diagonal pin, V1
+    without operand reuse, async / sync without accumulator residency either)."""
     nt = -(-n // b)
     T = tidx(nt, 0)
     nslots = min(nslots, T + 2)
@@ -111,6 +121,8 @@ def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = 
         raise MemoryError("device tile cache below 4 tiles")
     if pmap is not None and not emulated:
         raise ValueError("mixed precision out of core runs on the tensor-core engine")
+    pol = POLICIES.index(policy)
+    keep_ops, pin_diag, keep_acc = pol <= 1, pol == 0, pol <= 2
     G, KC = ooc_shape(nslots, b, emulated)
     C = _Cache(nslots, T, b * b * 8)
     final = set()
@@ -137,40 +149,73 @@ def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = 
         for g0 in range(k, nt, G):
             ms = range(g0, min(nt, g0 + G))
             sc = {}
-            for m in ms:
-                sc[m] = C.acquire(tidx(m, k))
-                C.pins[sc[m]] += 1
+
+            def acq_accs():
+                for m in ms:
+                    sc[m] = C.acquire(tidx(m, k))
+                    C.pins[sc[m]] += 1
+
+            def release_accs():
+                for m in ms:
+                    C.r.d2h_bytes += C.tile_bytes          # not final yet: copied back as FP64
+                    C.pins[sc[m]] -= 1
+                    C.forget(sc[m])
+
+            if keep_acc:
+                acq_accs()
             if emulated:
                 for n0 in range(0, k, KC):
                     ns = range(n0, min(k, n0 + KC))
-                    held = []
+                    if not keep_acc:
+                        acq_accs()
+                    ys, xs = [], []
                     for nn in ns:
-                        held.append(operand(tidx(k, nn)))
-                        C.pins[held[-1]] += 1
+                        ys.append(operand(tidx(k, nn)))
+                        C.pins[ys[-1]] += 1
                     for m in ms:
                         for nn in ns:
-                            held.append(operand(tidx(m, nn)))
-                            C.pins[held[-1]] += 1
+                            xs.append(operand(tidx(m, nn)))
+                            C.pins[xs[-1]] += 1
                     if check:
                         assert all(C.slot_tile[sc[m]] == tidx(m, k) for m in ms)
                         assert sum(1 for p in C.pins if p) <= nslots
                     C.r.tasks += len(ms) * len(ns)
-                    for s in held:
+                    for s in xs + ys:
                         C.pins[s] -= 1
+                    if not keep_ops:
+                        for s in xs + ys:
+                            C.forget(s)
+                    if not keep_acc:
+                        release_accs()
             else:
                 for m in ms:
                     for nn in range(k):
+                        if not keep_acc:
+                            sc[m] = C.acquire(tidx(m, k))
+                            C.pins[sc[m]] += 1
                         sx = operand(tidx(m, nn))
                         C.pins[sx] += 1
-                        operand(tidx(k, nn))
+                        sy = operand(tidx(k, nn))
                         if check:
                             assert C.slot_tile[sc[m]] == tidx(m, k)   # V1: accumulator resident
                         C.pins[sx] -= 1
+                        if not keep_ops:
+                            C.forget(sx)
+                            C.forget(sy)
+                        if not keep_acc:
+                            C.r.d2h_bytes += C.tile_bytes
+                            C.pins[sc[m]] -= 1
+                            C.forget(sc[m])
                         C.r.tasks += 1
+            if not keep_acc:
+                acq_accs()
+            if g0 != k and not pin_diag:
+                diag = C.acquire(tidx(k, k))
+                C.pins[diag] += 1
             if g0 == k:
                 diag = sc[k]
             if check:
-                assert C.slot_tile[diag] == tidx(k, k)          # V3: L_kk resident for the TRSMs
+                assert C.slot_tile[diag] == tidx(k, k)          # L_kk resident for the TRSMs
             for m in ms:
                 t = tidx(m, k)
                 C.r.d2h_bytes += C.tile_bytes + (bb * ELEM_BYTES[prec[t]] if prec[t] else 0)
@@ -178,7 +223,16 @@ def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = 
                 final.add(t)
                 if m != k:
                     C.pins[sc[m]] -= 1
-        C.pins[diag] -= 1
+            if not pin_diag:
+                C.pins[diag] -= 1
+                if not keep_ops:
+                    C.forget(diag)
+            if not keep_ops:
+                for m in ms:
+                    if m > k:
+                        C.forget(sc[m])
+        if pin_diag:
+            C.pins[diag] -= 1
     if check:
         assert sorted(C.r.written_back) == list(range(T))  # every tile written back exactly once
         assert all(p == 0 for p in C.pins)

@@ -17,7 +17,10 @@ from paper_2410_09819_gb300 import tile_chol as tc  # noqa: E402
 from gpu_util import pack_padded, to_dev, unpack_lower  # noqa: E402
 
 
-def ooc_factor(A, b, cap_tiles, pinned=True, emulated=False, pmap=None, mode=None):
+POLICY = {"V3": 0, "V2": 1, "V1": 2, "async": 3, "sync": 4}
+
+
+def ooc_factor(A, b, cap_tiles, pinned=True, emulated=False, pmap=None, mode=None, policy="V3"):
     """cap_tiles: device slots (an FP64 tile each, plus its digit planes when emulated, plus
     operand copies and a compact stage with a mixed-precision map)."""
     n = A.shape[0]
@@ -28,7 +31,7 @@ def ooc_factor(A, b, cap_tiles, pinned=True, emulated=False, pmap=None, mode=Non
     if mode is None:
         mode = 1 if emulated or mixed else 0
     slot = b * b * 8 + (14 * b * b + 16 if mode else 0) + (7 * b * b + 24 if mixed else 0)
-    H = tc.Handle(0, device_cap_bytes=cap_tiles * slot, fp64_mode=mode)
+    H = tc.Handle(0, device_cap_bytes=cap_tiles * slot, fp64_mode=mode, ooc=POLICY[policy])
     st = tc.tc_stats()
     m = None if pmap is None else np.ascontiguousarray(pmap, dtype=np.uint8).reshape(-1)
     info = tc.tile_chol_factor_ooc(H.h, n, b, host, m, st)
@@ -336,3 +339,33 @@ def test_ooc_inverse_trsm_mixed_matches_emulation_oracle():
     be_g = np.linalg.norm(A - Lg @ Lg.T) / normA
     be_o = np.linalg.norm(A - Lo @ Lo.T) / normA
     assert be_g <= 10 * eps and be_g <= 4 * be_o + 1e-12
+
+
+# ---------------------------------------------------- scheduling policies (Section III-C)
+@pytest.mark.parametrize("policy", ["V2", "V1", "async", "sync"])
+@pytest.mark.parametrize("emulated", [False, True])
+def test_ooc_policies_exact_and_counted(policy, emulated):
+    from paper_2410_09819_gb300.ooc_sim import simulate
+    n, b, cap = 1536, 128, 14
+    rng = np.random.default_rng(5)
+    L = np.tril(rng.integers(-1, 2, (n, n)).astype(np.float64), -1) + np.eye(n)
+    A = L @ L.T
+    H, info, host, st = ooc_factor(A, b, cap, emulated=emulated, policy=policy)
+    with H:
+        assert info == 0
+        assert np.array_equal(unpack_lower(host, n, b), L)
+        assert tc.tile_chol_logdet(H.h) == 0.0
+    r = simulate(n, b, cap, emulated=emulated, policy=policy)
+    assert (st.cache_hits, st.cache_misses, st.evictions) == (r.hits, r.misses, r.evictions)
+    assert (st.h2d_bytes, st.d2h_bytes) == (r.h2d_bytes, r.d2h_bytes)
+
+
+def test_ooc_policy_out_of_range_is_an_argument_error():
+    A = np.eye(512) * 2.0
+    with pytest.raises(tc.TileCholError) as e:
+        H = tc.Handle(0, device_cap_bytes=40 * 128 * 128 * 8, ooc=7)
+        try:
+            tc.tile_chol_factor_ooc(H.h, 512, 128, torch.from_numpy(pack_padded(A, 128)).pin_memory())
+        finally:
+            H.close()
+    assert e.value.code == -1

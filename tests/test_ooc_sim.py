@@ -94,3 +94,20 @@ def test_all_fp64_map_is_the_fp64_schedule():
     r = simulate(nt * b, b, 15, emulated=True, pmap=np.zeros((nt, nt), dtype=int))
     r0 = simulate(nt * b, b, 15, emulated=True)
     assert (r.h2d_bytes, r.d2h_bytes, r.misses) == (r0.h2d_bytes, r0.d2h_bytes, r0.misses)
+
+
+@pytest.mark.parametrize("emulated", [False, True])
+@pytest.mark.parametrize("nt,slots,b", [(12, 30, 256), (16, 60, 1024), (20, 37, 128)])
+def test_policy_volumes_follow_the_papers_order(emulated, nt, slots, b):
+    # Section V: data volume V3 < V2 < V1 < async; sync moves what async moves
+    from paper_2410_09819_gb300.ooc_sim import POLICIES
+    r = {p: simulate(nt * b, b, slots, check=True, emulated=emulated, policy=p) for p in POLICIES}
+    h = [r[p].h2d_bytes for p in ("V3", "V2", "V1", "async")]
+    assert h == sorted(h) and h[0] < h[-1]
+    assert r["sync"].h2d_bytes == r["async"].h2d_bytes and r["sync"].d2h_bytes == r["async"].d2h_bytes
+    T = tidx(nt, 0)
+    for p in ("V3", "V2", "V1"):                       # only final tiles go back
+        assert r[p].d2h_bytes == T * b * b * 8
+    assert r["async"].d2h_bytes > T * b * b * 8         # and accumulators after every step
+    for p in POLICIES:
+        assert r[p].tasks == sum(k * (nt - k) for k in range(nt))
