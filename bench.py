@@ -58,6 +58,8 @@ def parse_args():
                     help="skip the comparison factorizations (cuSOLVER potrf, the DFMA FP64 path)")
     ap.add_argument("--ooc-policy", default="V3", choices=["V3", "V2", "V1", "async", "sync"],
                     help="out-of-core scheduling policy (Section III-C)")
+    ap.add_argument("--ooc-eviction", default="lru", choices=["lru", "min"],
+                    help="out-of-core eviction: least recently used, or Belady's MIN over the static schedule")
     ap.add_argument("--ooc-mxp", action="store_true",
                     help="out-of-core workload in four precisions (map at eps_high 1e-9, FP64 band 2)")
     return ap.parse_args()
@@ -634,7 +636,7 @@ def run_ooc(args, ws, rank, local):
     cap = int(inputs.OOC_CACHE_FRACTION * T * b * b * 8)
     from paper_2410_09819_gb300.ooc_sim import POLICIES, simulate, slots_for_cap
     H = tc.Handle(local, stream=stream.cuda_stream, device_cap_bytes=cap, fp64_mode=args.fp64_mode,
-                  ooc=POLICIES.index(args.ooc_policy))
+                  ooc=POLICIES.index(args.ooc_policy), ooc_eviction=1 if args.ooc_eviction == "min" else 0)
     link = measure_link(dev)
     pts = inputs.uniform_points(n, w.seed + 1000 * rank, w.morton)
     host0 = torch.empty(T * b * b, dtype=torch.float64, pin_memory=True)
@@ -722,7 +724,11 @@ def run_ooc(args, ws, rank, local):
         for pol in POLICIES:
             r = simulate(n, b, ns, emulated=emu, pmap=pm2, policy=pol)
             predicted[pol] = {"h2d_bytes": r.h2d_bytes, "d2h_bytes": r.d2h_bytes}
+        r = simulate(n, b, ns, emulated=emu, pmap=pm2, policy="V3", eviction="min")
+        predicted["V3_belady_min"] = {"h2d_bytes": r.h2d_bytes, "d2h_bytes": r.d2h_bytes,
+                                      "note": "offline-optimal eviction over the same requests"}
         line["ooc_policy"] = args.ooc_policy
+        line["ooc_eviction"] = args.ooc_eviction
         line["ooc_link"] = {"h2d_bytes": h2d, "d2h_bytes": d2h, "h2d_gbs": h2d / tf / 1e9, "d2h_gbs": d2h / tf / 1e9,
                             "policy_volumes_predicted": predicted,
                             "link_peak_gbs": link, "h2d_frac": (h2d / tf / 1e9) / link["h2d"],

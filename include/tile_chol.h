@@ -97,7 +97,13 @@ typedef struct {
                                       level; FP64 tiles with one refinement step,
                                       X0 = C L^{-T}, L_mk = X0 + (C - X0 L^T) L^{-T}, which
                                       keeps the backward error at substitution's level */
-    int reserved[7];
+    int ooc_eviction;           /* tile_chol_factor_ooc eviction rule: 0 least recently used
+                                   (default); 1 Belady's MIN: the static schedule's whole
+                                   request sequence is known before the first copy, so the
+                                   unpinned tile whose next use lies farthest ahead leaves
+                                   (the offline optimum for the copy count).  Other values:
+                                   TC_ERR_ARG. */
+    int reserved[6];
 } tc_config;
 
 /* Per-call statistics (any field a call does not produce is left 0). */

@@ -422,7 +422,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 if (!z_wait(accf + a, (q >> 1) & 1, abort_flag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int E = args.exps[args.xsrc(it, n)] + args.exps[args.ysrc(it, n)];
-                const double s_hi = ldexp(1.0, E - 32), s_lo = ldexp(1.0, E - 4 * (SU + 1));
+                // hi holds groups 0 .. min(SU, 7) - 1, lo the rest (weights 16^-(g+2))
+                const double s_hi = ldexp(1.0, E - 4 * ((SU < 7 ? SU : 7) + 1)), s_lo = ldexp(1.0, E - 4 * (SU + 1));
                 const uint32_t lanebase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * SU * ZBN);
                 long long hi[ZBN], lo[ZBN];
 #pragma unroll
@@ -583,11 +584,13 @@ void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *ite
     if (!attr) {
         cudaFuncSetAttribute(k_zgemm<14, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<10, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<7, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     ZArgs a{items, nitems, exps, k, b, err, assign};
     const int grid = nitems < sm_count() ? nitems : sm_count();      // persistent: one CTA per SM
     if (planes == 10) k_zgemm<10><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 7) k_zgemm<7><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
     else k_zgemm<14><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
 }
 
@@ -599,6 +602,7 @@ void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGro
     if (!attr) {
         cudaFuncSetAttribute(k_zgemm<14, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<10, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<7, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     ZGroupArgs a;
@@ -618,6 +622,7 @@ void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGro
     const int items = g.ntiles * (b / ZBM) * (b / ZBN);
     const int grid = items < sm_count() ? items : sm_count();        // persistent: one CTA per SM
     if (planes == 10) k_zgemm<10><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 7) k_zgemm<7><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
     else k_zgemm<14><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
 }
 

@@ -166,6 +166,11 @@ struct ZItem {
 // given by digit-pool slot (ZG_MAX tiles and ZK_MAX sources at most per launch).
 constexpr int ZG_MAX = 16, ZK_MAX = 256;
 constexpr int Z_BN = 16;     // columns of one emulated-update work item (rows: 128)
+// Digit planes of the two approximate products of the refined TRSM (X0 = C L^{-T} and the
+// correction R L^{-T}): both need only ~2^-28 relative accuracy, since the refined result's
+// error is the product of the two (plus the exact-residual rounding); the residual
+// R = C - X0 L^T itself, which cancels, takes all 14.
+constexpr int ZREF_PLANES = 7;
 constexpr int QG_MAX = 16, QK_MAX = 256;
 struct ZGroup {
     int ntiles = 0, k = 0;

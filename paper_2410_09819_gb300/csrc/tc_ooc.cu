@@ -79,6 +79,10 @@ struct TileCache {
     std::vector<char> wb_pending;
     uint64_t clock = 0;
     int64_t hits = 0, misses = 0, evictions = 0, h2d_bytes = 0, d2h_bytes = 0, conversions = 0;
+    // Belady's MIN (optional): for request i, the index of the next request of the same tile
+    const std::vector<int64_t> *future = nullptr;
+    int64_t req = 0;
+    std::vector<int64_t> next_use;
 
     double *ptr(int s) const { return pool + (int64_t)s * bb; }
     uint8_t *stg(int s) const { return stage + (int64_t)s * 4 * bb; }
@@ -93,10 +97,13 @@ struct TileCache {
     // final low-precision tile as its compact copy, widened on the compute stream); -1 if
     // every slot is pinned (cache too small for the schedule).
     int acquire(int t, bool load) {
+        const int64_t nxt = (future && req < (int64_t)future->size()) ? (*future)[req] : 0;
+        ++req;
         if (where[t] >= 0) {
             const int s = where[t];
             ++hits;
             last[s] = ++clock;
+            if (future) next_use[s] = nxt;
             cudaStreamWaitEvent(cs, ready[s], 0);
             return s;
         }
@@ -104,7 +111,14 @@ struct TileCache {
         int v = -1;
         for (int s = 0; s < nslots && v < 0; ++s)
             if (slot_tile[s] < 0) v = s;
-        if (v < 0) {
+        if (v < 0 && future) {
+            int64_t best = -1;
+            for (int s = 0; s < nslots; ++s)
+                if (pins[s] == 0 && next_use[s] > best) {
+                    best = next_use[s];
+                    v = s;
+                }
+        } else if (v < 0) {
             uint64_t best = ~0ull;
             for (int s = 0; s < nslots; ++s)
                 if (pins[s] == 0 && last[s] < best) {
@@ -141,6 +155,7 @@ struct TileCache {
         slot_tile[v] = t;
         where[t] = v;
         last[v] = ++clock;
+        if (future) next_use[v] = nxt;
         cudaStreamWaitEvent(cs, ready[v], 0);
         if (packed) launch_unpack_compact(stg(v), b, prec[t], tile_e + t, ptr(v), cs);
         return v;
@@ -374,6 +389,48 @@ OocShape ooc_shape(int nslots, int b, bool zmode) {
     return {G, 0};
 }
 
+// The tile requests (acquisitions) of the factorization loop below, in order, for Belady's
+// MIN: the sequence depends on the schedule (policy, group, chunk) but not on what the cache
+// holds.  It must follow the loop's acquisition order; the tests hold the library's
+// counters equal to the schedule simulator's under MIN.
+std::vector<int64_t> ooc_future(int nt, const OocShape &S, bool zmode, int policy) {
+    const bool pin_diag = policy == OOC_V3, keep_acc = policy <= OOC_V1;
+    std::vector<int> seq;
+    for (int k = 0; k < nt; ++k)
+        for (int g0 = k; g0 < nt; g0 += S.group) {
+            const int g1 = std::min(nt, g0 + S.group);
+            auto accs = [&] {
+                for (int m = g0; m < g1; ++m) seq.push_back((int)tidx(m, k));
+            };
+            if (keep_acc) accs();
+            if (zmode) {
+                for (int n0 = 0; n0 < k; n0 += S.chunk) {
+                    const int kc = std::min(S.chunk, k - n0);
+                    if (!keep_acc) accs();
+                    for (int nn = n0; nn < n0 + kc; ++nn) seq.push_back((int)tidx(k, nn));
+                    for (int m = g0; m < g1; ++m)
+                        for (int nn = n0; nn < n0 + kc; ++nn) seq.push_back((int)tidx(m, nn));
+                }
+            } else {
+                for (int m = g0; m < g1; ++m)
+                    for (int nn = 0; nn < k; ++nn) {
+                        if (!keep_acc) seq.push_back((int)tidx(m, k));
+                        seq.push_back((int)tidx(m, nn));
+                        seq.push_back((int)tidx(k, nn));
+                    }
+            }
+            if (!keep_acc) accs();
+            if (g0 != k && !pin_diag) seq.push_back((int)tidx(k, k));
+        }
+    std::vector<int64_t> future(seq.size());
+    std::vector<int64_t> seen(tidx(nt, 0), (int64_t)seq.size() + 1);
+    for (int64_t i = (int64_t)seq.size() - 1; i >= 0; --i) {
+        future[i] = seen[seq[i]];
+        seen[seq[i]] = i;
+    }
+    return future;
+}
+
 }  // namespace
 
 extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_tiles, const uint8_t *map,
@@ -399,6 +456,8 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
     const bool zmode = h->cfg.fp64_mode >= 1;
     const int policy = h->cfg.ooc;
     if (policy < OOC_V3 || policy > OOC_SYNC) return set_err(h, TC_ERR_ARG, "tc_config.ooc must be 0..4 (V3, V2, V1, async, sync)");
+    if (h->cfg.ooc_eviction < 0 || h->cfg.ooc_eviction > 1)
+        return set_err(h, TC_ERR_ARG, "tc_config.ooc_eviction must be 0 (LRU) or 1 (Belady MIN)");
     const bool keep_ops = policy <= OOC_V2, pin_diag = policy == OOC_V3, keep_acc = policy <= OOC_V1;
     if (mixed && !zmode)
         return set_err(h, TC_ERR_UNSUPPORTED, "out-of-core mixed precision runs on the tensor-core engine (fp64_mode >= 1)");
@@ -432,6 +491,12 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
     double upd_flops[4] = {0, 0, 0, 0};
     int64_t tiles_p[4] = {0, 0, 0, 0};
     const OocShape S = ooc_shape(C.nslots, b, zmode);
+    std::vector<int64_t> future;
+    if (h->cfg.ooc_eviction == 1) {
+        future = ooc_future(nt, S, zmode, policy);
+        C.future = &future;
+        C.next_use.assign(C.nslots, 0);
+    }
     // fp64_mode 2: TRSM as products with L_kk^{-1} on the emulated engine (FP64 tiles refined
     // once with the exact residual), L_kk^{-1} at invbuf, X0 of group tile i at invbuf + (1+i) b^2
     const bool inv_trsm = zmode && h->cfg.fp64_mode == 2;
@@ -638,20 +703,23 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                 const int spt = span_begin(h, CAT_TRSM);
                 int so[ZG_MAX], ref[ZG_MAX], nref = 0;
                 for (int m = std::max(g0, k + 1); m < g1; ++m) so[m - std::max(g0, k + 1)] = sc[m - g0];
-                ZGroup z1;
-                z1.ntiles = noff;
-                z1.k = 1;
-                z1.assign = 1;
-                z1.ys[0] = vslot;
+                // X0 = C L^{-T}: to ~2^-28 for FP64 tiles (refined below), in full for the others
+                ZGroup z1, z1f;
+                z1.k = z1f.k = 1;
+                z1.assign = z1f.assign = 1;
+                z1.ys[0] = z1f.ys[0] = vslot;
                 for (int i = 0; i < noff; ++i) {
                     const int m = std::max(g0, k + 1) + i;
                     const bool refine = pm[(size_t)m * nt + k] == TC_FP64;
                     C.planes_of(C.ptr(so[i]), so[i]);
-                    z1.C[i] = refine ? inv + (int64_t)(1 + i) * C.bb : C.ptr(so[i]);
-                    z1.xs[i][0] = so[i];
+                    ZGroup &z = refine ? z1 : z1f;
+                    z.C[z.ntiles] = refine ? inv + (int64_t)(1 + i) * C.bb : C.ptr(so[i]);
+                    z.xs[z.ntiles][0] = so[i];
+                    ++z.ntiles;
                     if (refine) ref[nref++] = i;
                 }
-                launch_zgemm_group(C.mx, C.my, z1, C.exps, b, status + 1, h->s);      // X0 = C L^{-T}
+                launch_zgemm_group(C.mx, C.my, z1, C.exps, b, status + 1, h->s, ZREF_PLANES);
+                launch_zgemm_group(C.mx, C.my, z1f, C.exps, b, status + 1, h->s, 14);
                 if (nref) {
                     ZGroup z2, z3;
                     z2.ntiles = z3.ntiles = nref;
@@ -668,7 +736,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                     }
                     launch_zgemm_group(C.mx, C.my, z2, C.exps, b, status + 1, h->s);  // R = C - X0 L^T
                     for (int r = 0; r < nref; ++r) C.planes_of(C.ptr(so[ref[r]]), so[ref[r]]);
-                    launch_zgemm_group(C.mx, C.my, z3, C.exps, b, status + 1, h->s);  // R L^{-T}
+                    launch_zgemm_group(C.mx, C.my, z3, C.exps, b, status + 1, h->s, ZREF_PLANES);  // R L^{-T}
                     for (int r = 0; r < nref; ++r)
                         launch_add_tile(C.ptr(so[ref[r]]), inv + (int64_t)(1 + ref[r]) * C.bb, b, h->s);
                 }

@@ -26,10 +26,15 @@ class SimResult:
     d2h_bytes: int = 0
     written_back: list = field(default_factory=list)
     tasks: int = 0
+    requests: list = field(default_factory=list)
 
 
 class _Cache:
-    def __init__(self, nslots: int, ntiles: int, tile_bytes: int):
+    """Slot pool with LRU eviction (the library's policy), or, given the whole request
+    sequence (``future``: for request i, the index of the next request of the same tile),
+    Belady's MIN: evict the unpinned tile whose next use lies farthest ahead."""
+
+    def __init__(self, nslots: int, ntiles: int, tile_bytes: int, future=None):
         self.slot_tile = [-1] * nslots
         self.pins = [0] * nslots
         self.last = [0] * nslots
@@ -38,17 +43,29 @@ class _Cache:
         self.tile_bytes = tile_bytes
         self.load_bytes = None
         self.r = SimResult()
+        self.requests = []               # tiles in request order (the same for any eviction)
+        self.future = future
+        self.next_use = [0] * nslots     # MIN: next request index of the slot's tile
 
     def acquire(self, t: int) -> int:
+        i = len(self.requests)
+        self.requests.append(t)
+        nxt = self.future[i] if self.future is not None else 0
         if self.where[t] >= 0:
             s = self.where[t]
             self.r.hits += 1
             self.clock += 1
             self.last[s] = self.clock
+            self.next_use[s] = nxt
             return s
         self.r.misses += 1
         v = next((s for s, tt in enumerate(self.slot_tile) if tt < 0), -1)
-        if v < 0:
+        if v < 0 and self.future is not None:
+            best = None
+            for s in range(len(self.slot_tile)):
+                if self.pins[s] == 0 and (best is None or self.next_use[s] > best):
+                    best, v = self.next_use[s], s
+        elif v < 0:
             best = None
             for s in range(len(self.slot_tile)):
                 if self.pins[s] == 0 and (best is None or self.last[s] < best):
@@ -63,6 +80,7 @@ class _Cache:
         self.where[t] = v
         self.clock += 1
         self.last[v] = self.clock
+        self.next_use[v] = nxt
         return v
 
     def forget(self, s: int) -> None:
@@ -108,12 +126,26 @@ POLICIES = ("V3", "V2", "V1", "async", "sync")   # tc_config.ooc = 0 .. 4 (Secti
 
 
 def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = False, pmap=None,
-             policy: str = "V3") -> SimResult:
+             policy: str = "V3", eviction: str = "lru") -> SimResult:
     """Counters of one out-of-core factorization of order n, tile b, with nslots device slots
     (``emulated``: the grouped operand order of the tensor-core updates; ``pmap``: an nt x nt
     precision map, whose low-precision tiles go back to the host also as compact copies and
     come in again only as those; ``policy``: V3 (the default), V2 without the diagonal pin, V1
-    without operand reuse, async / sync without accumulator residency either)."""
+    without operand reuse, async / sync without accumulator residency either; ``eviction``:
+    "lru" (the library) or "min", Belady's offline optimum over the known request sequence,
+    for comparison)."""
+    if eviction == "min":
+        # the request sequence does not depend on eviction choices: take it from an LRU run
+        seq = simulate(n, b, nslots, emulated=emulated, pmap=pmap, policy=policy).requests
+        future, seen = [0] * len(seq), {}
+        for i in range(len(seq) - 1, -1, -1):
+            future[i] = seen.get(seq[i], len(seq) + 1)
+            seen[seq[i]] = i
+        return _simulate(n, b, nslots, check, emulated, pmap, policy, future)
+    return _simulate(n, b, nslots, check, emulated, pmap, policy, None)
+
+
+def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
     nt = -(-n // b)
     T = tidx(nt, 0)
     nslots = min(nslots, T + 2)
@@ -124,7 +156,7 @@ def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = 
     pol = POLICIES.index(policy)
     keep_ops, pin_diag, keep_acc = pol <= 1, pol == 0, pol <= 2
     G, KC = ooc_shape(nslots, b, emulated)
-    C = _Cache(nslots, T, b * b * 8)
+    C = _Cache(nslots, T, b * b * 8, future)
     final = set()
     prec = [0] * T
     if pmap is not None:
@@ -236,4 +268,5 @@ def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = 
     if check:
         assert sorted(C.r.written_back) == list(range(T))  # every tile written back exactly once
         assert all(p == 0 for p in C.pins)
+    C.r.requests = C.requests
     return C.r

@@ -38,7 +38,8 @@ class TileCholError(RuntimeError):
 class tc_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("ooc", ctypes.c_int),
                 ("device_cap_bytes", ctypes.c_int64), ("prefetch_depth", ctypes.c_int),
-                ("lookahead", ctypes.c_int), ("fp64_mode", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("lookahead", ctypes.c_int), ("fp64_mode", ctypes.c_int), ("ooc_eviction", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class tc_stats(ctypes.Structure):

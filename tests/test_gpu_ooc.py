@@ -20,7 +20,7 @@ from gpu_util import pack_padded, to_dev, unpack_lower  # noqa: E402
 POLICY = {"V3": 0, "V2": 1, "V1": 2, "async": 3, "sync": 4}
 
 
-def ooc_factor(A, b, cap_tiles, pinned=True, emulated=False, pmap=None, mode=None, policy="V3"):
+def ooc_factor(A, b, cap_tiles, pinned=True, emulated=False, pmap=None, mode=None, policy="V3", eviction=0):
     """cap_tiles: device slots (an FP64 tile each, plus its digit planes when emulated, plus
     operand copies and a compact stage with a mixed-precision map)."""
     n = A.shape[0]
@@ -31,7 +31,7 @@ def ooc_factor(A, b, cap_tiles, pinned=True, emulated=False, pmap=None, mode=Non
     if mode is None:
         mode = 1 if emulated or mixed else 0
     slot = b * b * 8 + (14 * b * b + 16 if mode else 0) + (7 * b * b + 24 if mixed else 0)
-    H = tc.Handle(0, device_cap_bytes=cap_tiles * slot, fp64_mode=mode, ooc=POLICY[policy])
+    H = tc.Handle(0, device_cap_bytes=cap_tiles * slot, fp64_mode=mode, ooc=POLICY[policy], ooc_eviction=eviction)
     st = tc.tc_stats()
     m = None if pmap is None else np.ascontiguousarray(pmap, dtype=np.uint8).reshape(-1)
     info = tc.tile_chol_factor_ooc(H.h, n, b, host, m, st)
@@ -369,3 +369,21 @@ def test_ooc_policy_out_of_range_is_an_argument_error():
         finally:
             H.close()
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("emulated,policy", [(False, "V3"), (True, "V3"), (True, "async"), (False, "V1")])
+def test_ooc_belady_min_eviction(emulated, policy):
+    # the library's MIN follows the simulator's decisions exactly, and copies no more than LRU
+    from paper_2410_09819_gb300.ooc_sim import simulate
+    n, b, cap = 2560, 128, 37
+    rng = np.random.default_rng(9)
+    L = np.tril(rng.integers(-1, 2, (n, n)).astype(np.float64), -1) + np.eye(n)
+    A = L @ L.T
+    H, info, host, st = ooc_factor(A, b, cap, emulated=emulated, policy=policy, eviction=1)
+    with H:
+        assert info == 0
+        assert np.array_equal(unpack_lower(host, n, b), L)
+    r = simulate(n, b, cap, emulated=emulated, policy=policy, eviction="min")
+    assert (st.cache_hits, st.cache_misses, st.evictions) == (r.hits, r.misses, r.evictions)
+    assert (st.h2d_bytes, st.d2h_bytes) == (r.h2d_bytes, r.d2h_bytes)
+    assert st.h2d_bytes <= simulate(n, b, cap, emulated=emulated, policy=policy).h2d_bytes

@@ -111,3 +111,20 @@ def test_policy_volumes_follow_the_papers_order(emulated, nt, slots, b):
     assert r["async"].d2h_bytes > T * b * b * 8         # and accumulators after every step
     for p in POLICIES:
         assert r[p].tasks == sum(k * (nt - k) for k in range(nt))
+
+
+@pytest.mark.parametrize("emulated", [False, True])
+@pytest.mark.parametrize("nt,slots,b", [(12, 30, 256), (20, 37, 128), (16, 60, 1024)])
+def test_belady_min_never_loses_to_lru(emulated, nt, slots, b):
+    # the static schedule's request sequence does not depend on eviction, so the offline
+    # optimum (evict the tile needed farthest ahead) is computable; it must not miss more
+    lru = simulate(nt * b, b, slots, check=True, emulated=emulated)
+    opt = simulate(nt * b, b, slots, check=True, emulated=emulated, eviction="min")
+    assert opt.requests == lru.requests
+    assert opt.misses <= lru.misses and opt.h2d_bytes <= lru.h2d_bytes
+    assert opt.d2h_bytes == lru.d2h_bytes
+
+
+def test_belady_min_hand_case():
+    # 4 slots, Nt = 3, DFMA order: LRU and MIN agree while nothing must be evicted
+    assert simulate(3 * 64, 64, 8, eviction="min").misses == simulate(3 * 64, 64, 8).misses == tidx(3, 0)
