@@ -613,7 +613,7 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
                 CK_LAUNCH();
                 launch_digits_src(Lkk, b, 0, gl, am_l + gl, pool, D.zexps, h->s);
                 CK_LAUNCH();
-                launch_zgemm(h->map_zx, h->map_zy, D.zinvc + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, ZREF_PLANES, 1);
+                launch_zgemm(h->map_zx, h->map_zy, D.zinvc + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1);
                 CK_LAUNCH();
                 launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, am_x, h->s, X0);
                 CK_LAUNCH();

@@ -166,10 +166,12 @@ struct ZItem {
 // given by digit-pool slot (ZG_MAX tiles and ZK_MAX sources at most per launch).
 constexpr int ZG_MAX = 16, ZK_MAX = 256;
 constexpr int Z_BN = 16;     // columns of one emulated-update work item (rows: 128)
-// Digit planes of the two approximate products of the refined TRSM (X0 = C L^{-T} and the
-// correction R L^{-T}): both need only ~2^-28 relative accuracy, since the refined result's
-// error is the product of the two (plus the exact-residual rounding); the residual
-// R = C - X0 L^T itself, which cancels, takes all 14.
+// Digit planes of the correction product R L^{-T} of the refined TRSM.  Truncation is
+// relative to each operand's largest entry, so a product's relative error is amplified by
+// A ~ K max|C| max|L^{-1}| / |X| (cancellation; A ~ 200 on Matern tiles).  X0 = C L^{-T} and
+// the residual R = C - X0 L^T keep all 14 planes (R ~ 2^-54 A |C|); the correction's own
+// truncation then adds ~2^-28 A |R| ~ 2^-82 A^2 |X|, far below FP64 rounding.  (X0 on 7
+// planes as well gave 2^-56 A^2 = 6.6e-13 backward error: measured, and rejected.)
 constexpr int ZREF_PLANES = 7;
 constexpr int QG_MAX = 16, QK_MAX = 256;
 struct ZGroup {

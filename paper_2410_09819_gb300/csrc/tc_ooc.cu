@@ -703,7 +703,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                 const int spt = span_begin(h, CAT_TRSM);
                 int so[ZG_MAX], ref[ZG_MAX], nref = 0;
                 for (int m = std::max(g0, k + 1); m < g1; ++m) so[m - std::max(g0, k + 1)] = sc[m - g0];
-                // X0 = C L^{-T}: to ~2^-28 for FP64 tiles (refined below), in full for the others
+                // X0 = C L^{-T} (FP64 tiles into the scratch X0, refined below; the others final)
                 ZGroup z1, z1f;
                 z1.k = z1f.k = 1;
                 z1.assign = z1f.assign = 1;
@@ -718,7 +718,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                     ++z.ntiles;
                     if (refine) ref[nref++] = i;
                 }
-                launch_zgemm_group(C.mx, C.my, z1, C.exps, b, status + 1, h->s, ZREF_PLANES);
+                launch_zgemm_group(C.mx, C.my, z1, C.exps, b, status + 1, h->s, 14);
                 launch_zgemm_group(C.mx, C.my, z1f, C.exps, b, status + 1, h->s, 14);
                 if (nref) {
                     ZGroup z2, z3;
