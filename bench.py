@@ -50,10 +50,15 @@ def parse_args():
     ap.add_argument("--fp64-mode", type=int, default=2, choices=[0, 1, 2],
                     help="FP64 updates: 0 DFMA pipe, 1 emulated on FP8 tensor cores (exact digit planes), "
                          "2 as 1 plus inverse-based TRSM in mixed precision")
+    ap.add_argument("--fp32-updates", type=int, default=0, choices=[0, 1],
+                    help="FP32 output tiles with emulated FP64: 0 on 10 digit planes, 1 as TF32 x 3")
     ap.add_argument("--n", type=int, default=0, help="override n (smaller quick runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_N)
+    ap.add_argument("--sweep", action="store_true",
+                    help="accuracy / performance sweep of Section V: weak, medium, strong correlation x "
+                         "accuracy levels 1e-5 .. 1e-11 (one JSON object; --n sets the order, default 65536)")
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the comparison factorizations (cuSOLVER potrf, the DFMA FP64 path)")
     ap.add_argument("--ooc-policy", default="V3", choices=["V3", "V2", "V1", "async", "sync"],
@@ -163,7 +168,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    H = tc.Handle(local, stream=stream.cuda_stream, fp64_mode=args.fp64_mode)
+    H = tc.Handle(local, stream=stream.cuda_stream, fp64_mode=args.fp64_mode, fp32_updates=args.fp32_updates)
     nt = tc.ntiles(n, b)
     T = tc.tile_count(n, b)
     seed = w.seed + 1000 * rank
@@ -483,7 +488,7 @@ def run_batched(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    H = tc.Handle(local, stream=stream.cuda_stream, fp64_mode=args.fp64_mode)
+    H = tc.Handle(local, stream=stream.cuda_stream, fp64_mode=args.fp64_mode, fp32_updates=args.fp32_updates)
     bw = inputs.batched_workload(args.count, 5 + 1000 * rank)
     ns = bw.ns
     pts = [torch.from_numpy(bw.points(i)).to(dev) for i in range(len(ns))]
@@ -749,11 +754,61 @@ def run_ooc(args, ws, rank, local):
     H.close()
 
 
+def run_sweep(args, local):
+    """Section V's accuracy study on this library: for each theta set (weak, medium, strong
+    correlation) the FP64 factor as reference, then the four-precision factor at each accuracy
+    level: log-likelihood (y from the generator), log-determinant, KL divergence (Eq. 3 at
+    y = 0), precision mix and factorization TFLOP/s (one timed run after one warm-up)."""
+    import torch
+
+    from paper_2410_09819_gb300 import tile_chol as tc
+    n = args.n or 65536
+    b = 1024 if n >= 16384 else 256
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    nt = tc.ntiles(n, b)
+    T = tc.tile_count(n, b)
+    out = {"metric": "Section V sweep: KL divergence, log-likelihood error and TFLOP/s vs accuracy level",
+           "n": n, "tile": b, "band": 2, "nugget": 1e-6, "points": "seeded uniform in [0,1]^2, Morton-sorted",
+           "fp64_mode": args.fp64_mode, "fp32_updates": args.fp32_updates, "rows": []}
+    pts = torch.from_numpy(inputs.uniform_points(n, 7, True)).to(dev)
+    y = torch.from_numpy(inputs.gaussian(n, 1, 11)[:, 0].copy()).to(dev)
+    A = torch.empty(T * b * b, dtype=torch.float64, device=dev)
+    pm = torch.zeros(nt * nt, dtype=torch.uint8)
+    with tc.Handle(local, stream=stream.cuda_stream, fp64_mode=args.fp64_mode, fp32_updates=args.fp32_updates) as H:
+        for name, (s2, beta, nu) in inputs.THETA_SETS.items():
+            tc.tc_matern_tiles(H.h, n, b, pts, s2, beta, nu, 1e-6, A)
+            st = tc.tc_stats()
+            tc.tile_chol_factor(H.h, n, b, A, None, st)
+            ld64, ll64 = tc.tile_chol_logdet(H.h), tc.tile_chol_loglik(H.h, y)
+            row = {"theta": name, "sigma2": s2, "beta": beta, "nu": nu,
+                   "fp64": {"tflops": n ** 3 / 3 / (st.t_ms / 1e3) / 1e12, "logdet": ld64, "loglik": ll64}, "levels": []}
+            for eps in inputs.SWEEP_EPS:
+                tc.tile_chol_precision_map(H.h, n, b, A, eps, 2, 4, pm)
+                tc.tile_chol_factor(H.h, n, b, A, pm, None)          # warm-up (plan, pools)
+                st = tc.tc_stats()
+                info = tc.tile_chol_factor(H.h, n, b, A, pm, st)
+                if info:
+                    row["levels"].append({"eps_high": eps, "info": info, "tiles_by_prec": list(st.tiles),
+                                          "note": "the low-precision factor lost positive definiteness"})
+                    continue
+                ld, ll = tc.tile_chol_logdet(H.h), tc.tile_chol_loglik(H.h, y)
+                row["levels"].append({"eps_high": eps, "tflops": n ** 3 / 3 / (st.t_ms / 1e3) / 1e12,
+                                      "tiles_by_prec": list(st.tiles), "kl_divergence": 0.5 * (ld - ld64),
+                                      "loglik_rel_err": abs(ll - ll64) / abs(ll64), "logdet": ld})
+            out["rows"].append(row)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     ws, rank, local = dist_info()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.sweep:
+        run_sweep(args, local)
         return
     if ws > 1:
         import torch

@@ -103,7 +103,13 @@ typedef struct {
                                    unpinned tile whose next use lies farthest ahead leaves
                                    (the offline optimum for the copy count).  Other values:
                                    TC_ERR_ARG. */
-    int reserved[6];
+    int fp32_updates;           /* with fp64_mode >= 1, how FP32 output tiles are updated:
+                                   0 (default): 10 digit planes on the FP8 tensor cores
+                                   (truncation below 2^-40 of the tile scale, FP64 sums);
+                                   1: 3 x TF32 tensor-core products with FP32 accumulation
+                                   (as with fp64_mode 0: FP32-level arithmetic, the
+                                   paper's FP32 tiles).  Other values: TC_ERR_ARG. */
+    int reserved[5];
 } tc_config;
 
 /* Per-call statistics (any field a call does not produce is left 0). */
@@ -131,7 +137,9 @@ typedef struct {
 /* Defaults: device 0, own stream, cap 0 (auto), prefetch 2, lookahead 1. */
 void tc_config_default(tc_config *cfg);
 
-/* Create a handle on cfg->device.  cfg may be NULL (defaults).  *out is set on TC_OK. */
+/* Create a handle on cfg->device.  cfg may be NULL (defaults).  *out is set on TC_OK.
+ * TC_ERR_ARG: fp64_mode outside 0..2 or fp32_updates outside 0..1.  (Out of core, FP32
+ * output tiles always take the digit-plane path.) */
 int tc_create(tc_handle *out, const tc_config *cfg);
 
 /* Release every device and host resource of the handle (NULL is allowed). */

@@ -125,7 +125,7 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 if (M.nt <= k) continue;
                 for (int m = k; m < M.nt; ++m) {
                     const bool fp64 = (m == k) || !M.mixed || M.map[(size_t)m * M.nt + k] == TC_FP64;
-                    if (!fp64 && zmode && M.map[(size_t)m * M.nt + k] == TC_FP32) {
+                    if (!fp64 && zmode && h->cfg.fp32_updates == 0 && M.map[(size_t)m * M.nt + k] == TC_FP32) {
                         // FP32 output: 10 digit planes of each operand, FP64 running sums
                         double *Cp = T(M, m, k);
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
@@ -264,7 +264,8 @@ struct MxpPlan {
 
 MxpPlan build_mxp(tc_handle h, double *W) {
     MxpPlan X;
-    const bool zmode = h->cfg.fp64_mode >= 1;   // FP32 outputs then run on digit planes
+    // FP32 outputs on digit planes (fp64_mode >= 1 and fp32_updates 0), else as TF32 x 3
+    const bool zmode = h->cfg.fp64_mode >= 1 && h->cfg.fp32_updates == 0;
     const int b = h->b;
     const int64_t bb = (int64_t)b * b;
     int ntmax = 0;
@@ -793,6 +794,10 @@ int tc_create(tc_handle *out, const tc_config *cfg) {
     tc_handle h = new tc_handle_s();
     if (cfg) h->cfg = *cfg;
     else tc_config_default(&h->cfg);
+    if (h->cfg.fp64_mode < 0 || h->cfg.fp64_mode > 2 || h->cfg.fp32_updates < 0 || h->cfg.fp32_updates > 1) {
+        delete h;
+        return TC_ERR_ARG;
+    }
     h->device = h->cfg.device;
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);

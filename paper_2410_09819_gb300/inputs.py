@@ -96,6 +96,11 @@ WORKLOADS = {
     "ooc_n262144": MaternWorkload("ooc_n262144", 262144, 2048, 0.5, 0.02, 1.0, 1e-4, 4),
 }
 
+# The paper's accuracy study (Section V): exponential kernel, variance 1, range beta for weak,
+# medium and strong spatial correlation, and accuracy levels of the precision map.
+THETA_SETS = {"weak": (1.0, 0.02627, 0.5), "medium": (1.0, 0.078809, 0.5), "strong": (1.0, 0.210158, 0.5)}
+SWEEP_EPS = (1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 1e-11)
+
 
 @dataclass
 class BatchedWorkload:

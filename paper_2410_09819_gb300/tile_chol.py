@@ -39,7 +39,7 @@ class tc_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("ooc", ctypes.c_int),
                 ("device_cap_bytes", ctypes.c_int64), ("prefetch_depth", ctypes.c_int),
                 ("lookahead", ctypes.c_int), ("fp64_mode", ctypes.c_int), ("ooc_eviction", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("fp32_updates", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class tc_stats(ctypes.Structure):
