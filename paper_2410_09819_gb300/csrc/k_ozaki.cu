@@ -585,12 +585,16 @@ void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *ite
         cudaFuncSetAttribute(k_zgemm<14, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<10, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<7, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<6, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<4, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     ZArgs a{items, nitems, exps, k, b, err, assign};
     const int grid = nitems < sm_count() ? nitems : sm_count();      // persistent: one CTA per SM
     if (planes == 10) k_zgemm<10><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
     else if (planes == 7) k_zgemm<7><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 6) k_zgemm<6><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 4) k_zgemm<4><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
     else k_zgemm<14><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
 }
 
@@ -603,6 +607,8 @@ void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGro
         cudaFuncSetAttribute(k_zgemm<14, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<10, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<7, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<6, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_zgemm<4, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     ZGroupArgs a;
@@ -623,6 +629,8 @@ void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGro
     const int grid = items < sm_count() ? items : sm_count();        // persistent: one CTA per SM
     if (planes == 10) k_zgemm<10><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
     else if (planes == 7) k_zgemm<7><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 6) k_zgemm<6><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 4) k_zgemm<4><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
     else k_zgemm<14><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
 }
 

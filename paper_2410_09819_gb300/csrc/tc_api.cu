@@ -37,6 +37,7 @@ struct ColPlan {
     int z0 = 0, nz = 0;          // emulated-FP64 update items
     int y0 = 0, ny = 0;          // emulated FP32-output update items (10 digit planes)
     int v0 = 0, nv = 0;          // TRSM as an emulated product with L_kk^{-1} (assign mode)
+    int nvp[4] = {0, 0, 0, 0};   //   ... of which per output precision (items in that order)
     int dg0 = 0, ndg = 0;        // tiles whose digit planes are made after the column's TRSMs
     int it0 = 0, nit = 0;        // FP64 update items
     int red0 = 0, nred = 0;      // split-K reductions
@@ -179,7 +180,11 @@ Plan build_plan(tc_handle h, double *W, int *status) {
             // update operands, and (k+1, k+1) is not factored yet)
             const MatDesc &M = h->mats[0];
             const int sinv = (int)(M.tile0 + tidx(k, k)), sl = (int)(M.tile0 + tidx(k + 1, k + 1));
+            // tiles in precision order: one product launch per output precision
+            for (int p = 0; p < 4; ++p)
             for (int m = k + 1; m < M.nt; ++m) {
+                if ((M.mixed ? (int)M.map[(size_t)m * M.nt + k] : TC_FP64) != p) continue;
+                const size_t before = P.zinv.size();
                 double *Cp = T(M, m, k);
                 double *Cs = P.inv_refine ? inv_scratch + (int64_t)(m - k) * bb : nullptr;
                 const int sx = (int)(M.tile0 + tidx(m, k));
@@ -191,6 +196,7 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                             P.zref.push_back({Cp, sx, sl, (uint16_t)bm, (uint16_t)bn});
                         }
                     }
+                C.nvp[p] += (int)(P.zinv.size() - before);
             }
         }
         C.nv = (int)P.zinv.size() - C.v0;
@@ -601,8 +607,14 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
             launch_digits(W, b, D.dtiles + C.dg0, C.ndg, D.zamax2, pool, D.zexps, h->s);
             CK_LAUNCH();
             if (!P.inv_refine) {
-                launch_zgemm(h->map_zx, h->map_zy, D.zinv + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1);
-                CK_LAUNCH();
+                // the product's truncation stays below the rounding to each stored precision
+                int off = C.v0;
+                for (int p = 0; p < 4; ++p) {
+                    launch_zgemm(h->map_zx, h->map_zy, D.zinv + off, C.nvp[p], D.zexps, 1, b, status + 1, h->s,
+                                 ZTRSM_PLANES[p], 1);
+                    CK_LAUNCH();
+                    off += C.nvp[p];
+                }
             } else {
                 // X0 = C L_kk^{-T};  R = C - X0 L_kk^T;  L_mk = X0 + R L_kk^{-T}  (C is overwritten by R)
                 const int Tt = (int)P.Ttot, gl = (int)(Md.tile0 + tidx(k + 1, k + 1));

@@ -173,6 +173,10 @@ constexpr int Z_BN = 16;     // columns of one emulated-update work item (rows: 
 // truncation then adds ~2^-28 A |R| ~ 2^-82 A^2 |X|, far below FP64 rounding.  (X0 on 7
 // planes as well gave 2^-56 A^2 = 6.6e-13 backward error: measured, and rejected.)
 constexpr int ZREF_PLANES = 7;
+// Digit planes of the TRSM product L_mk = C_mk L_kk^{-T} for a tile stored in precision p
+// (FP64, FP32, FP16, FP8): truncation 16^-planes of the tile scale, amplified by A ~ 2^8,
+// stays below the rounding to the stored format (2^-32 < 2^-24, 2^-16 < 2^-11, 2^-8 < 2^-4).
+constexpr int ZTRSM_PLANES[4] = {14, 10, 6, 4};
 constexpr int QG_MAX = 16, QK_MAX = 256;
 struct ZGroup {
     int ntiles = 0, k = 0;

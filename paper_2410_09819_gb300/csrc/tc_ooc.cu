@@ -703,23 +703,27 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                 const int spt = span_begin(h, CAT_TRSM);
                 int so[ZG_MAX], ref[ZG_MAX], nref = 0;
                 for (int m = std::max(g0, k + 1); m < g1; ++m) so[m - std::max(g0, k + 1)] = sc[m - g0];
-                // X0 = C L^{-T} (FP64 tiles into the scratch X0, refined below; the others final)
-                ZGroup z1, z1f;
-                z1.k = z1f.k = 1;
-                z1.assign = z1f.assign = 1;
-                z1.ys[0] = z1f.ys[0] = vslot;
+                // X0 = C L^{-T} (FP64 tiles into the scratch X0, refined below; the others final,
+                // on as many planes as their stored precision needs)
+                ZGroup z1[4];
+                for (int p = 0; p < 4; ++p) {
+                    z1[p].k = 1;
+                    z1[p].assign = 1;
+                    z1[p].ys[0] = vslot;
+                }
                 for (int i = 0; i < noff; ++i) {
                     const int m = std::max(g0, k + 1) + i;
-                    const bool refine = pm[(size_t)m * nt + k] == TC_FP64;
+                    const int p = pm[(size_t)m * nt + k];
+                    const bool refine = p == TC_FP64;
                     C.planes_of(C.ptr(so[i]), so[i]);
-                    ZGroup &z = refine ? z1 : z1f;
+                    ZGroup &z = z1[p];
                     z.C[z.ntiles] = refine ? inv + (int64_t)(1 + i) * C.bb : C.ptr(so[i]);
                     z.xs[z.ntiles][0] = so[i];
                     ++z.ntiles;
                     if (refine) ref[nref++] = i;
                 }
-                launch_zgemm_group(C.mx, C.my, z1, C.exps, b, status + 1, h->s, 14);
-                launch_zgemm_group(C.mx, C.my, z1f, C.exps, b, status + 1, h->s, 14);
+                for (int p = 0; p < 4; ++p)
+                    launch_zgemm_group(C.mx, C.my, z1[p], C.exps, b, status + 1, h->s, ZTRSM_PLANES[p]);
                 if (nref) {
                     ZGroup z2, z3;
                     z2.ntiles = z3.ntiles = nref;
