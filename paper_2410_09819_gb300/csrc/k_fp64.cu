@@ -325,7 +325,7 @@ __device__ __forceinline__ void warp_tri64(double (*S)[65], double *blk, bool fo
 // Forward substitution with one diagonal tile, one right-hand side r (in place): per 64-row
 // block, the product with the solved part (256 threads, 4 partial sums per row, fixed order)
 // and the warp solve of the diagonal block.
-__device__ __forceinline__ void fwd_diag_body(const double *L, int b, double *r) {
+__device__ __forceinline__ void fwd_diag_body(const double *L, int ld, int b, double *r) {
     __shared__ double red[4][64];
     __shared__ double blk[64];
     __shared__ double S[64][65];
@@ -334,11 +334,11 @@ __device__ __forceinline__ void fwd_diag_body(const double *L, int b, double *r)
     const int rr = tid & 63, part = tid >> 6;
     for (int jb = 0; jb < b / 64; ++jb) {
         double acc = 0.0;
-        for (int l = part; l < jb * 64; l += 4) acc = fma(L[(int64_t)l * b + jb * 64 + rr], z[l], acc);
+        for (int l = part; l < jb * 64; l += 4) acc = fma(L[(int64_t)l * ld + jb * 64 + rr], z[l], acc);
         red[part][rr] = acc;
         for (int idx = tid; idx < 4096; idx += 256) {
             const int lr = idx & 63, lc = idx >> 6;
-            S[lr][lc] = (lr >= lc) ? L[(int64_t)(jb * 64 + lc) * b + jb * 64 + lr] : 0.0;
+            S[lr][lc] = (lr >= lc) ? L[(int64_t)(jb * 64 + lc) * ld + jb * 64 + lr] : 0.0;
         }
         __syncthreads();
         if (tid < 64) blk[tid] = z[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
@@ -351,7 +351,7 @@ __device__ __forceinline__ void fwd_diag_body(const double *L, int b, double *r)
 }
 
 // Back substitution with one diagonal tile: L_jj^T x = z, one right-hand side (in place).
-__device__ __forceinline__ void bwd_diag_body(const double *L, int b, double *x) {
+__device__ __forceinline__ void bwd_diag_body(const double *L, int ld, int b, double *x) {
     __shared__ double S[64][65];
     __shared__ double red[4][64];
     __shared__ double blk[64];
@@ -361,12 +361,12 @@ __device__ __forceinline__ void bwd_diag_body(const double *L, int b, double *x)
         // acc[r] = sum_{l >= (jb+1)*64} L[l][jb*64 + r] x[l]: rows of the tile's column block,
         // read along l (column-major L: contiguous in l for a fixed column)
         double acc = 0.0;
-        const double *Lc = L + (int64_t)(jb * 64 + rr) * b;
+        const double *Lc = L + (int64_t)(jb * 64 + rr) * ld;
         for (int l = (jb + 1) * 64 + part; l < b; l += 4) acc = fma(Lc[l], x[l], acc);
         red[part][rr] = acc;
         for (int idx = tid; idx < 4096; idx += 256) {
             const int lr = idx & 63, lc = idx >> 6;
-            S[lr][lc] = (lr >= lc) ? L[(int64_t)(jb * 64 + lc) * b + jb * 64 + lr] : 0.0;
+            S[lr][lc] = (lr >= lc) ? L[(int64_t)(jb * 64 + lc) * ld + jb * 64 + lr] : 0.0;
         }
         __syncthreads();
         if (tid < 64) blk[tid] = x[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
@@ -378,9 +378,55 @@ __device__ __forceinline__ void bwd_diag_body(const double *L, int b, double *x)
     }
 }
 
-// Forward substitution with one diagonal tile: L_jj z = r for each RHS column (one CTA each).
-__global__ void __launch_bounds__(256) k_fwd_diag(const double *L, int b, double *R, int64_t ldr) {
-    fwd_diag_body(L, b, R + blockIdx.x * ldr);
+// Inside a diagonal tile, after a sub-block solve: R[r] -= sum_c L[c ld + r] Z[c] for the
+// `rows` rows below the sub-block (one CTA per 64 rows, four partial sums per row).
+template <int NQ>
+__global__ void __launch_bounds__(256)
+k_gemv_below(const double *L, int ld, int cols, const double *Z, double *R, int64_t ldr, int nrhs) {
+    __shared__ double red[64][17];
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6, r0 = blockIdx.x * 64;
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (int c = part; c < cols; c += 4) {
+        const double l = L[(int64_t)c * ld + r0 + rr];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if (q < nrhs) acc[q] = fma(l, Z[q * ldr + c], acc[q]);
+    }
+    part_reduce_sub(red, acc, nrhs, R, ldr, r0);
+}
+
+// The back-substitution counterpart: R[i] -= sum_c L[i ld + c] X[c] for the rows above the
+// sub-block (L points at the sub-block's first row, column 0; a warp per output row, lanes
+// along c, so each row of L^T is read contiguously).
+template <int NQ>
+__global__ void __launch_bounds__(256)
+k_gemv_above(const double *L, int ld, int cols, const double *X, double *R, int64_t ldr, int nrhs) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * 64 + warp; i < blockIdx.x * 64 + 64; i += 8) {
+        double acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+        for (int c = lane; c < cols; c += 32) {
+            const double l = L[(int64_t)i * ld + c];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nrhs) acc[q] = fma(l, X[q * ldr + c], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && q < nrhs) R[q * ldr + i] -= v;
+        }
+    }
+}
+
+// Forward substitution with the s x s lower triangle at L (leading dimension ld): L z = r for
+// each RHS column (one CTA each).
+__global__ void __launch_bounds__(256) k_fwd_diag(const double *L, int ld, int b, double *R, int64_t ldr) {
+    fwd_diag_body(L, ld, b, R + blockIdx.x * ldr);
 }
 
 // r_i -= L_ij z_j for every tile row i > j; one CTA per 64-row chunk of a tile row.
@@ -413,9 +459,9 @@ k_fwd_update(const double *W, int b, int j, double *R, int64_t ldr, int nrhs) {
     part_reduce_sub(red, acc, nrhs, R, ldr, (int64_t)i * b + r0);
 }
 
-// Back substitution with one diagonal tile: L_jj^T x = z for each RHS column (one CTA each).
-__global__ void __launch_bounds__(256) k_bwd_diag(const double *L, int b, double *R, int64_t ldr) {
-    bwd_diag_body(L, b, R + blockIdx.x * ldr);
+// Back substitution with the s x s lower triangle at L: L^T x = z for each RHS column.
+__global__ void __launch_bounds__(256) k_bwd_diag(const double *L, int ld, int b, double *R, int64_t ldr) {
+    bwd_diag_body(L, ld, b, R + blockIdx.x * ldr);
 }
 
 // z_i -= L_ji^T x_j for every tile row i < j; one CTA per 64-row chunk of tile row i.
@@ -670,7 +716,7 @@ void launch_fix_padding_batched(const LEntry *e, int count, int ntmax, int b, cu
 // ------------------------------------------------------------ grouped (batched) solves
 __global__ void __launch_bounds__(256) k_fwd_diag_g(const SDiag *__restrict__ e, double *R, int b) {
     const SDiag E = e[blockIdx.y];
-    fwd_diag_body(E.L, b, R + E.off + blockIdx.x * E.ldr);
+    fwd_diag_body(E.L, b, b, R + E.off + blockIdx.x * E.ldr);
 }
 
 template <int NQ>
@@ -701,7 +747,7 @@ __global__ void __launch_bounds__(256) k_fwd_update_g(const SUpd *__restrict__ u
 
 __global__ void __launch_bounds__(256) k_bwd_diag_g(const SDiag *__restrict__ e, double *R, int b) {
     const SDiag E = e[blockIdx.y];
-    bwd_diag_body(E.L, b, R + E.off + blockIdx.x * E.ldr);
+    bwd_diag_body(E.L, b, b, R + E.off + blockIdx.x * E.ldr);
 }
 
 template <int NQ>
@@ -893,15 +939,31 @@ void launch_fix_padding(double *W, int nt, int b, int64_t n, cudaStream_t s) {
 void launch_zero_upper_diag(double *W, int nt, int b, int64_t n, cudaStream_t s) {
     k_zero_upper_diag<<<dim3(64, (n % b) ? 2 * nt - 1 : nt), 256, 0, s>>>(W, nt, b, n);
 }
+// A diagonal tile's substitution in sub-blocks of DIAG_SUB rows: a one-CTA triangular solve
+// per sub-block, then a many-CTA product with the rest of its columns (the one-CTA part,
+// bound by a single SM's FP64 rate, shrinks from b^2/2 to b DIAG_SUB/2 multiply-adds).
+constexpr int DIAG_SUB = 256;
 void launch_fwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
-    k_fwd_diag<<<nrhs, 256, 0, s>>>(Ljj, b, R, ldr);
+    const int S = (b % DIAG_SUB) ? b : DIAG_SUB;     // tiles not a multiple of it: one block
+    for (int sb = 0; sb < b / S; ++sb) {
+        k_fwd_diag<<<nrhs, 256, 0, s>>>(Ljj + (int64_t)sb * S * b + sb * S, b, S, R + sb * S, ldr);
+        const int rows = b - (sb + 1) * S;
+        if (rows > 0)
+            NQ_DISPATCH(nrhs, k_gemv_below, rows / 64, 256, 0, s, Ljj + (int64_t)sb * S * b + (sb + 1) * S, b, S,
+                        R + sb * S, R + (sb + 1) * S, ldr, nrhs);
+    }
 }
 void launch_fwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
     const int ntiles = nt - 1 - j;
     if (ntiles > 0) NQ_DISPATCH(nrhs, k_fwd_update, ntiles * (b / 64), 256, 0, s, W, b, j, R, ldr, nrhs);
 }
 void launch_bwd_diag(const double *Ljj, int b, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
-    k_bwd_diag<<<nrhs, 256, 0, s>>>(Ljj, b, R, ldr);
+    const int S = (b % DIAG_SUB) ? b : DIAG_SUB;     // tiles not a multiple of it: one block
+    for (int sb = b / S - 1; sb >= 0; --sb) {
+        k_bwd_diag<<<nrhs, 256, 0, s>>>(Ljj + (int64_t)sb * S * b + sb * S, b, S, R + sb * S, ldr);
+        if (sb > 0)
+            NQ_DISPATCH(nrhs, k_gemv_above, sb * S / 64, 256, 0, s, Ljj + sb * S, b, S, R + sb * S, R, ldr, nrhs);
+    }
 }
 void launch_bwd_update(const double *W, int nt, int b, int j, double *R, int64_t ldr, int nrhs, cudaStream_t s) {
     (void)nt;

