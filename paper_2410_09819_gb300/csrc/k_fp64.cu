@@ -96,33 +96,39 @@ k_dgemm_reduce(const DRed *__restrict__ reds, int ld, const double *__restrict__
 
 // ------------------------------------------------------------------------------- POTRF
 // Factor the 64 x 64 lower block at D in place (right-looking in shared memory).  A
-// non-positive pivot records the 1-based global column in *status and stops.
-__global__ void __launch_bounds__(256) k_potrf_block(double *D, int ld, int col0, int *status) {
-    if (failed(status)) return;
+// non-positive pivot records the 1-based global column in *status and stops.  Each step
+// touches only the trailing triangle (threads: row r = tid % 64, columns c = j+1+tid/64 step 4)
+// and scales the column by the pivot's reciprocal: GB300 retires about 2 FP64 operations per
+// clock per SM, so every skipped multiply-add and division counts.
+__device__ __forceinline__ void potrf64_body(double *D, int ld, int col0, int *status) {
     __shared__ double S[64][65];
     __shared__ int fail;
-    const int tid = threadIdx.x;
+    __shared__ double rp;
+    const int tid = threadIdx.x, r = tid & 63, cg = tid >> 6;
     for (int idx = tid; idx < 4096; idx += 256) {
-        const int r = idx & 63, c = idx >> 6;
-        S[r][c] = (r >= c) ? D[(int64_t)c * ld + r] : 0.0;
+        const int rr = idx & 63, c = idx >> 6;
+        S[rr][c] = (rr >= c) ? D[(int64_t)c * ld + rr] : 0.0;
     }
     if (tid == 0) fail = 0;
     __syncthreads();
     for (int j = 0; j < 64; ++j) {
         if (tid == 0) {
             const double d = S[j][j];
-            if (!(d > 0.0)) fail = j + 1;
-            else S[j][j] = sqrt(d);
+            if (!(d > 0.0)) {
+                fail = j + 1;
+            } else {
+                const double sd = sqrt(d);
+                S[j][j] = sd;
+                rp = 1.0 / sd;
+            }
         }
         __syncthreads();
         if (fail) break;
-        const double p = S[j][j];
-        if (tid > j && tid < 64) S[tid][j] = S[tid][j] / p;
+        if (tid > j && tid < 64) S[tid][j] *= rp;
         __syncthreads();
-        for (int idx = tid; idx < 4096; idx += 256) {
-            const int r = idx & 63, c = idx >> 6;
-            if (c > j && r >= c) S[r][c] = S[r][c] - S[r][j] * S[c][j];
-        }
+        const double lrj = S[r][j];
+        for (int c = j + 1 + cg; c < 64; c += 4)
+            if (r >= c) S[r][c] = fma(-lrj, S[c][j], S[r][c]);
         __syncthreads();
     }
     if (fail) {
@@ -130,44 +136,57 @@ __global__ void __launch_bounds__(256) k_potrf_block(double *D, int ld, int col0
         return;
     }
     for (int idx = tid; idx < 4096; idx += 256) {
-        const int r = idx & 63, c = idx >> 6;
-        if (r >= c) D[(int64_t)c * ld + r] = S[r][c];
+        const int rr = idx & 63, c = idx >> 6;
+        if (rr >= c) D[(int64_t)c * ld + rr] = S[rr][c];
     }
 }
-
-// Right-side solve of a 64-row strip held in shared memory: X L^T = S in place, L the
-// 64 x 64 lower block in Ls.  Column j: X[r][j] = (S[r][j] - sum_{l<j} X[r][l] L[j][l]) / L[j][j],
-// applied right-looking (after X[:, j] is known, S[:, c] -= X[:, j] L[c][j] for c > j).
-__device__ __forceinline__ void strip_solve(double (*Ss)[65], double (*Ls)[65]) {
-    const int tid = threadIdx.x;
-    for (int j = 0; j < 64; ++j) {
-        if (tid < 64) Ss[tid][j] = Ss[tid][j] / Ls[j][j];
-        __syncthreads();
-        for (int idx = tid; idx < 4096; idx += 256) {
-            const int r = idx & 63, c = idx >> 6;
-            if (c > j) Ss[r][c] = Ss[r][c] - Ss[r][j] * Ls[c][j];
-        }
-        __syncthreads();
-    }
-}
-
-// POTRF panel: rows below the factored 64-block within the diagonal tile.
-__global__ void __launch_bounds__(256) k_trsm_rows(double *P, const double *L, int ld, const int *status) {
+__global__ void __launch_bounds__(256) k_potrf_block(double *D, int ld, int col0, int *status) {
     if (failed(status)) return;
-    __shared__ double Ls[64][65], Ss[64][65];
+    potrf64_body(D, ld, col0, status);
+}
+
+// Right-side solve of a strip of ROWS rows held in shared memory: X L^T = S in place, L the
+// 64 x 64 lower block in Ls, rinv[j] = 1 / L[j][j].  Column j: X[r][j] = S[r][j] / L[j][j], then
+// S[r][c] -= X[r][j] L[c][j] for c > j (threads: row tid % ROWS, columns step 256 / ROWS).
+template <int ROWS>
+__device__ __forceinline__ void strip_solve(double (*Ss)[65], double (*Ls)[65], const double *rinv) {
+    const int tid = threadIdx.x, r = tid % ROWS, cg = tid / ROWS;
+    constexpr int CS = 256 / ROWS;
+    for (int j = 0; j < 64; ++j) {
+        if (tid < ROWS) Ss[tid][j] *= rinv[j];
+        __syncthreads();
+        const double xrj = Ss[r][j];
+        for (int c = j + 1 + cg; c < 64; c += CS) Ss[r][c] = fma(-xrj, Ls[c][j], Ss[r][c]);
+        __syncthreads();
+    }
+}
+
+// POTRF panel: rows below the factored 64-block within the diagonal tile, 16-row strips
+// (the solve is bound by one SM's FP64 rate, so more, smaller strips finish sooner).
+constexpr int PANEL_ROWS = 16;
+__device__ __forceinline__ void panel_body(double *Pb, const double *L, int ld) {
+    __shared__ double Ls[64][65], Ss[PANEL_ROWS][65], rinv[64];
     const int tid = threadIdx.x;
-    double *Pb = P + blockIdx.x * 64;
     for (int idx = tid; idx < 4096; idx += 256) {
         const int r = idx & 63, c = idx >> 6;
         Ls[r][c] = (r >= c) ? L[(int64_t)c * ld + r] : 0.0;
+    }
+    for (int idx = tid; idx < PANEL_ROWS * 64; idx += 256) {
+        const int r = idx % PANEL_ROWS, c = idx / PANEL_ROWS;
         Ss[r][c] = Pb[(int64_t)c * ld + r];
     }
     __syncthreads();
-    strip_solve(Ss, Ls);
-    for (int idx = tid; idx < 4096; idx += 256) {
-        const int r = idx & 63, c = idx >> 6;
+    if (tid < 64) rinv[tid] = 1.0 / Ls[tid][tid];
+    __syncthreads();
+    strip_solve<PANEL_ROWS>(Ss, Ls, rinv);
+    for (int idx = tid; idx < PANEL_ROWS * 64; idx += 256) {
+        const int r = idx % PANEL_ROWS, c = idx / PANEL_ROWS;
         Pb[(int64_t)c * ld + r] = Ss[r][c];
     }
+}
+__global__ void __launch_bounds__(256) k_trsm_rows(double *P, const double *L, int ld, const int *status) {
+    if (failed(status)) return;
+    panel_body(P + blockIdx.x * PANEL_ROWS, L, ld);
 }
 
 // Column TRSM (Algorithm 1: A_mk = A_mk L_kk^{-T}): one CTA per 64-row strip of a tile,
@@ -180,6 +199,7 @@ k_trsm_strips(const TStrip *__restrict__ strips, int ld, int b, const int *statu
     double(*Ys)[64] = reinterpret_cast<double(*)[64]>(smem + 16 * 64);
     double(*Ls)[65] = reinterpret_cast<double(*)[65]>(smem + 32 * 64);
     double(*Ss)[65] = reinterpret_cast<double(*)[65]>(smem + 32 * 64 + 64 * 65);
+    double *rinv = smem + 32 * 64 + 2 * 64 * 65;
     const TStrip st = strips[blockIdx.x];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double *X = st.C + st.r0;
@@ -196,7 +216,9 @@ k_trsm_strips(const TStrip *__restrict__ strips, int ld, int b, const int *statu
             Ls[r][c] = (r >= c) ? st.L[(int64_t)(jb * 64 + c) * ld + jb * 64 + r] : 0.0;
         }
         __syncthreads();
-        strip_solve(Ss, Ls);
+        if (tid < 64) rinv[tid] = 1.0 / Ls[tid][tid];
+        __syncthreads();
+        strip_solve<64>(Ss, Ls, rinv);
         for (int idx = tid; idx < 4096; idx += 256) {
             const int r = idx & 63, c = idx >> 6;
             X[(int64_t)(jb * 64 + c) * ld + r] = Ss[r][c];
@@ -602,69 +624,21 @@ __global__ void __launch_bounds__(1024) k_dot_self(const double *v, int64_t n, d
 __global__ void __launch_bounds__(256) k_potrf_blocks(const PEntry *__restrict__ e, int ld) {
     const PEntry E = e[blockIdx.x];
     if (failed(E.status)) return;
-    __shared__ double S[64][65];
-    __shared__ int fail;
-    const int tid = threadIdx.x;
-    double *D = E.D;
-    for (int idx = tid; idx < 4096; idx += 256) {
-        const int r = idx & 63, c = idx >> 6;
-        S[r][c] = (r >= c) ? D[(int64_t)c * ld + r] : 0.0;
-    }
-    if (tid == 0) fail = 0;
-    __syncthreads();
-    for (int j = 0; j < 64; ++j) {
-        if (tid == 0) {
-            const double d = S[j][j];
-            if (!(d > 0.0)) fail = j + 1;
-            else S[j][j] = sqrt(d);
-        }
-        __syncthreads();
-        if (fail) break;
-        const double p = S[j][j];
-        if (tid > j && tid < 64) S[tid][j] = S[tid][j] / p;
-        __syncthreads();
-        for (int idx = tid; idx < 4096; idx += 256) {
-            const int r = idx & 63, c = idx >> 6;
-            if (c > j && r >= c) S[r][c] = S[r][c] - S[r][j] * S[c][j];
-        }
-        __syncthreads();
-    }
-    if (fail) {
-        if (tid == 0) atomicCAS(E.status, 0, E.col0 + fail);
-        return;
-    }
-    for (int idx = tid; idx < 4096; idx += 256) {
-        const int r = idx & 63, c = idx >> 6;
-        if (r >= c) D[(int64_t)c * ld + r] = S[r][c];
-    }
+    potrf64_body(E.D, ld, E.col0, E.status);
 }
 
 // Batched POTRF panel: rows below each entry's factored 64-block (grid.y = entry).
 __global__ void __launch_bounds__(256) k_trsm_rows_batched(const PEntry *__restrict__ e, int ld) {
     const PEntry E = e[blockIdx.y];
-    if (failed(E.status) || (int)blockIdx.x * 64 >= E.rows) return;
-    __shared__ double Ls[64][65], Ss[64][65];
-    const int tid = threadIdx.x;
-    const double *L = E.D;
-    double *Pb = E.D + 64 + blockIdx.x * 64;
-    for (int idx = tid; idx < 4096; idx += 256) {
-        const int r = idx & 63, c = idx >> 6;
-        Ls[r][c] = (r >= c) ? L[(int64_t)c * ld + r] : 0.0;
-        Ss[r][c] = Pb[(int64_t)c * ld + r];
-    }
-    __syncthreads();
-    strip_solve(Ss, Ls);
-    for (int idx = tid; idx < 4096; idx += 256) {
-        const int r = idx & 63, c = idx >> 6;
-        Pb[(int64_t)c * ld + r] = Ss[r][c];
-    }
+    if (failed(E.status) || (int)blockIdx.x * PANEL_ROWS >= E.rows) return;
+    panel_body(E.D + 64 + blockIdx.x * PANEL_ROWS, E.D, ld);
 }
 
 void launch_potrf_blocks(const PEntry *e, int n, int ld, cudaStream_t s) {
     if (n > 0) k_potrf_blocks<<<n, 256, 0, s>>>(e, ld);
 }
 void launch_trsm_rows_batched(const PEntry *e, int n, int max_rows, int ld, cudaStream_t s) {
-    if (n > 0 && max_rows > 0) k_trsm_rows_batched<<<dim3(max_rows / 64, n), 256, 0, s>>>(e, ld);
+    if (n > 0 && max_rows > 0) k_trsm_rows_batched<<<dim3(max_rows / PANEL_ROWS, n), 256, 0, s>>>(e, ld);
 }
 
 
@@ -917,10 +891,10 @@ void launch_potrf_block(double *D, int ld, int col0, int *status, cudaStream_t s
     k_potrf_block<<<1, 256, 0, s>>>(D, ld, col0, status);
 }
 void launch_trsm_rows(double *P, const double *L, int ld, int rows, const int *status, cudaStream_t s) {
-    if (rows > 0) k_trsm_rows<<<rows / 64, 256, 0, s>>>(P, L, ld, status);
+    if (rows > 0) k_trsm_rows<<<rows / PANEL_ROWS, 256, 0, s>>>(P, L, ld, status);
 }
 void launch_trsm_strips(const TStrip *strips, int nstrips, int ld, int b, const int *status, cudaStream_t s) {
-    const size_t smem = (32 * 64 + 2 * 64 * 65) * sizeof(double);
+    const size_t smem = (32 * 64 + 2 * 64 * 65 + 64) * sizeof(double);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_trsm_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1032,6 +1006,7 @@ k_trsm_tile(const __grid_constant__ TGroup g, const double *L, int ld, int b, co
     double(*Ys)[64] = reinterpret_cast<double(*)[64]>(smem + 16 * 64);
     double(*Ls)[65] = reinterpret_cast<double(*)[65]>(smem + 32 * 64);
     double(*Ss)[65] = reinterpret_cast<double(*)[65]>(smem + 32 * 64 + 64 * 65);
+    double *rinv = smem + 32 * 64 + 2 * 64 * 65;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double *X = C + blockIdx.x * 64;
     for (int jb = 0; jb < b / 64; ++jb) {
@@ -1047,7 +1022,9 @@ k_trsm_tile(const __grid_constant__ TGroup g, const double *L, int ld, int b, co
             Ls[r][c] = (r >= c) ? L[(int64_t)(jb * 64 + c) * ld + jb * 64 + r] : 0.0;
         }
         __syncthreads();
-        strip_solve(Ss, Ls);
+        if (tid < 64) rinv[tid] = 1.0 / Ls[tid][tid];
+        __syncthreads();
+        strip_solve<64>(Ss, Ls, rinv);
         for (int idx = tid; idx < 4096; idx += 256) {
             const int r = idx & 63, c = idx >> 6;
             X[(int64_t)(jb * 64 + c) * ld + r] = Ss[r][c];
@@ -1195,7 +1172,7 @@ void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s) {
     k_dgemm_tile<<<dim3(job.M / 64, job.N / 64), 256, 0, s>>>(job, ld);
 }
 static size_t trsm_tile_smem() {
-    const size_t smem = (32 * 64 + 2 * 64 * 65) * sizeof(double);
+    const size_t smem = (32 * 64 + 2 * 64 * 65 + 64) * sizeof(double);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_trsm_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
