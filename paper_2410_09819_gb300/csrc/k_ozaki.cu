@@ -56,15 +56,28 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
     else q = 0;
     return bits < 0 ? -q : q;
 }
-__device__ __forceinline__ void put_digits(long long q, uint8_t *P, int64_t o, int64_t bb) {
+// Four adjacent elements (columns 4j .. 4j+3 of a row): one 32-bit store per plane.
+__device__ __forceinline__ uint32_t e4m3_digit(int d) {
+    return (uint32_t)(uint8_t)__nv_cvt_float_to_fp8((float)d, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ void put_digits4(const long long (&q0)[4], uint8_t *P, int64_t o, int64_t bb) {
+    long long q[4] = {q0[0], q0[1], q0[2], q0[3]};
 #pragma unroll
     for (int s = ZS - 1; s >= 1; --s) {
-        int r = (int)(q & 15);
-        if (r > 8) r -= 16;
-        q = (q - r) >> 4;
-        P[(int64_t)s * bb + o] = (uint8_t)__nv_cvt_float_to_fp8((float)r, __NV_SATFINITE, __NV_E4M3);
+        uint32_t w = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int r = (int)(q[u] & 15);
+            if (r > 8) r -= 16;
+            q[u] = (q[u] - r) >> 4;
+            w |= e4m3_digit(r) << (8 * u);
+        }
+        *reinterpret_cast<uint32_t *>(P + (int64_t)s * bb + o) = w;
     }
-    P[o] = (uint8_t)__nv_cvt_float_to_fp8((float)q, __NV_SATFINITE, __NV_E4M3);
+    uint32_t w = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w |= e4m3_digit((int)q[u]) << (8 * u);
+    *reinterpret_cast<uint32_t *>(P + o) = w;
 }
 
 // exps[t] = smallest e with amax[t] <= 2^e; planes of tile t at pool + (t*ZS + s) b^2,
@@ -94,9 +107,11 @@ k_digits(const double *W, int b, const int *tiles, const double *amax, uint8_t *
             S[r][c] = T[(int64_t)(c0 + c) * b + r0 + r];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 1024; idx += 256) {
-            const int c = idx & 31, r = idx >> 5;
-            put_digits(fixed56(S[r][c], e), P, (int64_t)(r0 + r) * b + c0 + c, bb);
+        {   // 256 threads x 4 adjacent columns = the 32 x 32 block
+            const int c = (threadIdx.x & 7) * 4, r = threadIdx.x >> 3;
+            const long long q[4] = {fixed56(S[r][c], e), fixed56(S[r][c + 1], e), fixed56(S[r][c + 2], e),
+                                    fixed56(S[r][c + 3], e)};
+            put_digits4(q, P, (int64_t)(r0 + r) * b + c0 + c, bb);
         }
     }
 }
@@ -492,9 +507,11 @@ k_digits_src(const double *src, int b, int transpose, int dst, const double *ama
             S[r][c] = transpose ? src[(int64_t)(r0 + r) * b + c0 + c] : src[(int64_t)(c0 + c) * b + r0 + r];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 1024; idx += 256) {
-            const int c = idx & 31, r = idx >> 5;
-            put_digits(fixed56(S[r][c], e), P, (int64_t)(r0 + r) * b + c0 + c, bb);
+        {   // 256 threads x 4 adjacent columns = the 32 x 32 block
+            const int c = (threadIdx.x & 7) * 4, r = threadIdx.x >> 3;
+            const long long q[4] = {fixed56(S[r][c], e), fixed56(S[r][c + 1], e), fixed56(S[r][c + 2], e),
+                                    fixed56(S[r][c + 3], e)};
+            put_digits4(q, P, (int64_t)(r0 + r) * b + c0 + c, bb);
         }
     }
 }
