@@ -895,10 +895,9 @@ void launch_trsm_rows(double *P, const double *L, int ld, int rows, const int *s
 }
 void launch_trsm_strips(const TStrip *strips, int nstrips, int ld, int b, const int *status, cudaStream_t s) {
     const size_t smem = (32 * 64 + 2 * 64 * 65 + 64) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0;
+    if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_trsm_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
     }
     if (nstrips > 0) k_trsm_strips<<<nstrips, 256, smem, s>>>(strips, ld, b, status);
 }
@@ -1173,10 +1172,9 @@ void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s) {
 }
 static size_t trsm_tile_smem() {
     const size_t smem = (32 * 64 + 2 * 64 * 65 + 64) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0;
+    if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_trsm_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
     }
     return smem;
 }
@@ -1193,11 +1191,10 @@ void launch_trsm_group(double *const *C, int ntiles, const double *L, int ld, in
 }
 void launch_trinv(const double *L, int b, double *Y, cudaStream_t s) {
     const size_t smem = ((size_t)b * TRINV_COLS + 64 * 65 + 64 * TRINV_COLS) * sizeof(double);
-    static int attr_b = 0;
-    if (attr_b < b) {
-        cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_b = b;
-    }
+    static unsigned long long attr = 0;
+    if (first_on_device(attr))     // sized for the largest tile it serves (b <= 2048)
+        cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(((size_t)2048 * TRINV_COLS + 64 * 65 + 64 * TRINV_COLS) * sizeof(double)));
     k_trinv<<<b / TRINV_COLS, 256, smem, s>>>(L, b, Y);
 }
 void launch_logdiag_tile(const double *D, int b, int nv, double *out, cudaStream_t s) {

@@ -596,15 +596,14 @@ void launch_add_tiles(double *W, int b, const int *tiles, int ntiles, const doub
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
                   int b, int *err, cudaStream_t s, int planes, int assign) {
     if (nitems <= 0 || k <= 0) return;
-    static bool attr = false;
+    static unsigned long long attr = 0;
     const size_t smem = zgemm_smem_bytes();
-    if (!attr) {
+    if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_zgemm<14, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<10, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<7, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<6, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<4, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
     }
     ZArgs a{items, nitems, exps, k, b, err, assign};
     const int grid = nitems < sm_count() ? nitems : sm_count();      // persistent: one CTA per SM
@@ -618,15 +617,14 @@ void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *ite
 void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGroup &g, const int *exps, int b,
                         int *err, cudaStream_t s, int planes) {
     if (g.ntiles <= 0 || g.k <= 0) return;
-    static bool attr = false;
+    static unsigned long long attr = 0;
     const size_t smem = zgemm_smem_bytes();
-    if (!attr) {
+    if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_zgemm<14, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<10, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<7, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<6, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<4, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
     }
     ZGroupArgs a;
     memset(&a, 0, sizeof a);

@@ -120,6 +120,17 @@ void launch_fix_padding_batched(const LEntry *e, int count, int ntmax, int b, cu
 void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s);
 void launch_trsm_tile(double *C, const double *L, int ld, int b, const int *status, cudaStream_t s);
 constexpr int TG_MAX = 16;   // tiles per grouped TRSM launch
+
+// Function attributes (dynamic shared-memory opt-in) are per device: true the first time it
+// is called for the current device (one bit per device ordinal; setting one twice is harmless).
+inline bool first_on_device(unsigned long long &mask) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (mask & bit) return false;
+    mask |= bit;
+    return true;
+}
 void launch_trinv(const double *L, int b, double *Y, cudaStream_t s);   // Y = L^{-1}, b x b
 void launch_trsm_group(double *const *C, int ntiles, const double *L, int ld, int b, const int *status,
                        cudaStream_t s);
