@@ -330,12 +330,7 @@ def run_ours(args, ws, rank, local):
             "dtype": ("f64" if args.fp64_mode == 0 else "f64 (updates emulated on e4m3 tensor cores)")
             if not w.mixed else "f64+f32/tf32+f16+e4m3",
             "data": "synthetic", "impl": "ours",
-            "config": {"workload": w.name, "n": n, "tile": b, "nu": w.nu, "range": w.range_a, "sigma2": w.sigma2,
-                       "nugget": w.nugget, "points": "seeded uniform in [0,1]^2" + (", Morton-sorted" if w.morton else ""),
-                       "precision": "per-tile map" if w.mixed else "FP64", "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (no flush needed)",
-                       "step": "map+factor+solve(1 RHS, <=2 refinement)+loglik through a refined solve" if w.mixed
-                       else "factor+solve(1 RHS, <=2 refinement)+loglik"},
+            "config": workload_config(w, n, b, ws),
             "roofline": roofline,
             "accuracy": accuracy,
             "comparisons": comparisons,
@@ -352,6 +347,16 @@ def run_ours(args, ws, rank, local):
         }
         print(json.dumps(line), flush=True)
     H.close()
+
+
+def workload_config(w, n, b, ws):
+    """The `config` object of a line for an in-core workload (both arms print the same)."""
+    return {"workload": w.name, "n": n, "tile": b, "nu": w.nu, "range": w.range_a, "sigma2": w.sigma2,
+            "nugget": w.nugget, "points": "seeded uniform in [0,1]^2" + (", Morton-sorted" if w.morton else ""),
+            "precision": "per-tile map" if w.mixed else "FP64", "parallelism": f"replicas x{ws}",
+            "l2": "inputs larger than L2 (no flush needed)",
+            "step": "map+factor+solve(1 RHS, <=2 refinement)+loglik through a refined solve" if w.mixed
+            else "factor+solve(1 RHS, <=2 refinement)+loglik"}
 
 
 def fp64_baselines(tc, n, b, A, local, stream):
@@ -432,7 +437,7 @@ def run_reference(args, ws, rank):
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "n": n, "tile": w.tile, "sample_n": ns},
+            "config": dict(workload_config(w, n, w.tile, ws), sample_n=ns),
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
