@@ -1033,49 +1033,50 @@ k_trsm_tile(const __grid_constant__ TGroup g, const double *L, int ld, int b, co
 }
 
 // Y = L^{-1} for a lower-triangular b x b tile L (column-major, ld = b), by forward
-// substitution L y_c = e_c column by column: CTA x owns columns 8x .. 8x+7, whose entries
-// above the diagonal block are zero; for each 64-row block the product with the already
-// solved rows (kept in shared memory) is followed by the 64 x 64 diagonal solve.
-constexpr int TRINV_COLS = 8;
+// substitution L y_c = e_c column by column.  CTA x owns columns 4x .. 4x+3 and
+// b-4-4x .. b-1-4x: a long and a short group, so every CTA carries about the same work
+// (column c costs (b - c)^2 / 2 multiply-adds).  For each group, and each 64-row block from
+// the group's first nonzero row on, the product with the already solved rows (kept in shared
+// memory) is followed by the 64 x 64 diagonal solve.
+constexpr int TRINV_COLS = 4;
 __global__ void __launch_bounds__(256) k_trinv(const double *__restrict__ L, int b, double *__restrict__ Y) {
     extern __shared__ double tsm[];
-    double *Ys = tsm;                               // b x 8: the CTA's columns, row-major by row
+    double *Ys = tsm;                               // b x 4: the group's columns, row-major by row
     double(*Ld)[65] = reinterpret_cast<double(*)[65]>(tsm + (size_t)b * TRINV_COLS);
     double(*Acc)[TRINV_COLS] = reinterpret_cast<double(*)[TRINV_COLS]>(tsm + (size_t)b * TRINV_COLS + 64 * 65);
-    const int tid = threadIdx.x, c0 = blockIdx.x * TRINV_COLS;
-    const int ib0 = c0 / 64;
-    const int r = tid & 63, cg = tid >> 6;          // row in block, column pair
-    for (int i = tid; i < ib0 * 64 * TRINV_COLS; i += 256) Ys[i] = 0.0;
-    for (int ib = ib0; ib < b / 64; ++ib) {
-        const int row = ib * 64 + r;
-        double a0 = (row == c0 + 2 * cg) ? 1.0 : 0.0, a1 = (row == c0 + 2 * cg + 1) ? 1.0 : 0.0;
-        for (int l = ib0 * 64; l < ib * 64; ++l) {
-            const double lv = L[(int64_t)l * b + row];
-            a0 = fma(-lv, Ys[l * TRINV_COLS + 2 * cg], a0);
-            a1 = fma(-lv, Ys[l * TRINV_COLS + 2 * cg + 1], a1);
-        }
-        Acc[r][2 * cg] = a0;
-        Acc[r][2 * cg + 1] = a1;
-        for (int i = tid; i < 4096; i += 256) {
-            const int rr = i & 63, cc = i >> 6;
-            Ld[rr][cc] = (rr >= cc) ? L[(int64_t)(ib * 64 + cc) * b + ib * 64 + rr] : 0.0;
-        }
-        __syncthreads();
-        for (int j = 0; j < 64; ++j) {
-            if (tid < TRINV_COLS) Acc[j][tid] = Acc[j][tid] / Ld[j][j];
-            __syncthreads();
-            for (int i = tid; i < 64 * TRINV_COLS; i += 256) {
-                const int rr = i / TRINV_COLS, cc = i % TRINV_COLS;
-                if (rr > j) Acc[rr][cc] = fma(-Ld[rr][j], Acc[j][cc], Acc[rr][cc]);
+    const int tid = threadIdx.x;
+    const int r = tid & 63, cg = tid >> 6;          // row in block, column of the group
+    for (int grp = 0; grp < 2; ++grp) {
+        const int c0 = grp == 0 ? (int)blockIdx.x * TRINV_COLS : b - TRINV_COLS - (int)blockIdx.x * TRINV_COLS;
+        const int ib0 = c0 / 64;
+        __syncthreads();                            // the previous group's output is written
+        for (int i = tid; i < ib0 * 64 * TRINV_COLS; i += 256) Ys[i] = 0.0;
+        for (int ib = ib0; ib < b / 64; ++ib) {
+            const int row = ib * 64 + r;
+            double a = (row == c0 + cg) ? 1.0 : 0.0;
+            for (int l = ib0 * 64; l < ib * 64; ++l) a = fma(-L[(int64_t)l * b + row], Ys[l * TRINV_COLS + cg], a);
+            Acc[r][cg] = a;
+            for (int i = tid; i < 4096; i += 256) {
+                const int rr = i & 63, cc = i >> 6;
+                Ld[rr][cc] = (rr >= cc) ? L[(int64_t)(ib * 64 + cc) * b + ib * 64 + rr] : 0.0;
             }
             __syncthreads();
+            for (int j = 0; j < 64; ++j) {
+                if (tid < TRINV_COLS) Acc[j][tid] = Acc[j][tid] / Ld[j][j];
+                __syncthreads();
+                {
+                    const int rr = tid / TRINV_COLS, cc = tid % TRINV_COLS;    // 64 x 4 = 256 threads
+                    if (rr > j) Acc[rr][cc] = fma(-Ld[rr][j], Acc[j][cc], Acc[rr][cc]);
+                }
+                __syncthreads();
+            }
+            Ys[(ib * 64 + tid / TRINV_COLS) * TRINV_COLS + tid % TRINV_COLS] = Acc[tid / TRINV_COLS][tid % TRINV_COLS];
+            __syncthreads();
         }
-        for (int i = tid; i < 64 * TRINV_COLS; i += 256) Ys[(ib * 64 + i / TRINV_COLS) * TRINV_COLS + i % TRINV_COLS] = Acc[i / TRINV_COLS][i % TRINV_COLS];
-        __syncthreads();
-    }
-    for (int i = tid; i < b * TRINV_COLS; i += 256) {
-        const int rr = i % b, cc = i / b;
-        Y[(int64_t)(c0 + cc) * b + rr] = Ys[rr * TRINV_COLS + cc];
+        for (int i = tid; i < b * TRINV_COLS; i += 256) {
+            const int rr = i % b, cc = i / b;
+            Y[(int64_t)(c0 + cc) * b + rr] = Ys[rr * TRINV_COLS + cc];
+        }
     }
 }
 
@@ -1195,7 +1196,7 @@ void launch_trinv(const double *L, int b, double *Y, cudaStream_t s) {
     if (first_on_device(attr))     // sized for the largest tile it serves (b <= 2048)
         cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(((size_t)2048 * TRINV_COLS + 64 * 65 + 64 * TRINV_COLS) * sizeof(double)));
-    k_trinv<<<b / TRINV_COLS, 256, smem, s>>>(L, b, Y);
+    k_trinv<<<b / (2 * TRINV_COLS), 256, smem, s>>>(L, b, Y);
 }
 void launch_logdiag_tile(const double *D, int b, int nv, double *out, cudaStream_t s) {
     k_logdiag_tile<<<1, 256, 0, s>>>(D, b, nv, out);
