@@ -185,10 +185,14 @@ int tile_chol_precision_map(tc_handle h, int64_t n, int b, const double *A_tiles
  *   tile_chol_precision_map; the diagonal is treated as FP64 whatever it holds.
  *   Each update C_mk -= sum_{n<k} L_mn L_kn^T runs in the precision of its output
  *   tile p(m, k): operand tiles stored wider are rounded to it (RNE, fresh power-of-two
- *   scale for FP16/FP8), narrower ones are widened exactly.  FP64 updates use DFMA;
- *   FP32 updates run as three TF32 tensor-core products (hi*hi + hi*lo + lo*hi),
- *   FP16 and FP8 (E4M3) on the tensor cores, all with FP32 accumulation.  POTRF and
- *   TRSM are FP64; each final L_mk is then stored in p(m, k).
+ *   scale for FP16/FP8), narrower ones are widened exactly.  FP16 and FP8 (E4M3)
+ *   updates run on the tensor cores with FP32 accumulation.  FP64 and FP32 updates
+ *   follow cfg.fp64_mode: with 0, FP64 on the DFMA pipe and FP32 as three TF32
+ *   tensor-core products (hi*hi + hi*lo + lo*hi); with 1 or 2, both as exact products of
+ *   base-16 digit planes on the E4M3 tensor cores (14 planes for FP64 outputs, 10 for
+ *   FP32, or TF32 x 3 with cfg.fp32_updates = 1) with FP64 sums.  POTRF is FP64; the
+ *   TRSM is FP64 substitution (modes 0, 1) or, in mode 2, products with L_kk^{-1} on the
+ *   emulated engine (see fp64_mode).  Each final L_mk is then stored in p(m, k).
  * Runs in device memory: the handle holds a working copy of the factor (and, when
  *   A_tiles is host memory, a device copy of A); TC_ERR_OOM when that does not fit (use
  *   tile_chol_factor_ooc).
@@ -201,12 +205,20 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles,
  * Out-of-core factorization (Sections III-C and IV-B, Algorithms 2 and 3): A_tiles is HOST
  * memory (best page-locked) holding A in the tile layout; on return it holds the factor L
  * (in place, as the paper's write-back does; upper triangles of diagonal tiles are left as
- * they were, padding rows/columns as those of the identity).  The device keeps a cache of
- * at most cfg.device_cap_bytes of tiles: a tile an update needs is reused when cached, else
- * copied in, evicting the least-recently-used tile that no pending task pins; the
- * accumulator tile stays resident through its updates and L_kk until every TRSM of
- * column k is done.  Copies run on their own streams, overlapped with the kernels.
- * map must be NULL or all-FP64 in this build (TC_ERR_UNSUPPORTED otherwise).
+ * they were, or zero with fp64_mode 2; padding rows/columns as those of the identity).  The
+ * device keeps a cache of at most cfg.device_cap_bytes of tiles (with fp64_mode >= 1 each
+ * slot also holds the tile's 14 digit planes, and with a mixed map its FP16 / E4M3 operand
+ * copies and a compact stage, so fewer tiles fit): a tile an update needs is reused when
+ * cached, else copied in, evicting per cfg.ooc_eviction (least recently used, or Belady's
+ * MIN) a tile that no pending task pins; under the default policy (cfg.ooc = V3) the
+ * accumulator tile stays resident through its updates and L_kk until every TRSM of column
+ * k is done.  The accumulators of a column are processed a group at a time.  Copies run on
+ * their own streams, overlapped with the kernels.
+ * map: NULL or all-FP64 with any fp64_mode; a mixed map needs fp64_mode >= 1
+ * (TC_ERR_UNSUPPORTED otherwise).  Final low-precision tiles are written back both as FP64
+ * (into A_tiles) and as a compact copy at their precision into a page-locked store the
+ * handle owns (TC_ERR_HOSTMEM if it cannot be allocated); later loads of such a tile move
+ * only the compact copy.
  * stats reports host<->device bytes, cache hits/misses/evictions.  Afterwards
  * tile_chol_solve / tile_chol_loglik stream the factor from A_tiles (no refinement: A is
  * gone) and tile_chol_logdet is available.  A_tiles must stay valid until then.
