@@ -205,7 +205,7 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles,
  * Out-of-core factorization (Sections III-C and IV-B, Algorithms 2 and 3): A_tiles is HOST
  * memory (best page-locked) holding A in the tile layout; on return it holds the factor L
  * (in place, as the paper's write-back does; upper triangles of diagonal tiles are left as
- * they were, or zero with fp64_mode 2; padding rows/columns as those of the identity).  The
+ * they were, or zeroed by fp64_mode 2; padding rows/columns as those of the identity).  The
  * device keeps a cache of at most cfg.device_cap_bytes of tiles (with fp64_mode >= 1 each
  * slot also holds the tile's 14 digit planes, and with a mixed map its FP16 / E4M3 operand
  * copies and a compact stage, so fewer tiles fit): a tile an update needs is reused when
