@@ -208,8 +208,14 @@ def run_ours(args, ws, rank, local):
     upd_flops = upd_ms = 0.0
     launches = 0
     agg = None
+    marks = [ev0]                       # per-step boundaries on the same stream (best / median)
+    factor_ms = []
     for _ in range(args.steps):
         st, ss, ll = step()
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        marks.append(e)
+        factor_ms.append(st.t_ms)
         upd_flops += st.update_flops[0]
         upd_ms += st.t_update_ms[0]
         # the refined log-likelihood repeats the solve's launches (plus its dot product)
@@ -221,6 +227,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         dist.barrier()
     t = ev0.elapsed_time(ev1) / 1e3
+    step_ms = [a.elapsed_time(c) for a, c in zip(marks[:-1], marks[1:])]
     if ws > 1:
         tt = torch.tensor([t], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -343,7 +350,10 @@ def run_ours(args, ws, rank, local):
                        "berr": ss.berr, "refine_iters": ss.refine_iters, "loglik": ll,
                        "update_tflops_by_prec": [(st.update_flops[p] / st.t_update_ms[p] / 1e9) if st.t_update_ms[p] else None
                                                  for p in range(4)],
-                       "tiles_by_prec": list(st.tiles), "kernel_source_sha": sha},
+                       "tiles_by_prec": list(st.tiles), "kernel_source_sha": sha,
+                       "step_ms": step_ms, "step_ms_best": min(step_ms), "step_ms_median": float(np.median(step_ms)),
+                       "factor_ms_steps": factor_ms,
+                       "tflops_factor_only_best": flops / (min(factor_ms) / 1e3) / 1e12},
         }
         print(json.dumps(line), flush=True)
     H.close()
