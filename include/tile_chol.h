@@ -151,11 +151,14 @@ const char *tc_last_error(tc_handle h);
 /*
  * Synthetic covariance, Eq. 2 (Section III-D): writes the lower tiles of
  *   Sigma_ij = sigma2 / (2^(nu-1) Gamma(nu)) (h/a)^nu K_nu(h/a) + nugget [i == j],
- * h = |s_i - s_j|, for nu in {0.5, 1.5, 2.5} (closed forms e^-x, (1+x)e^-x,
- * (1+x+x^2/3)e^-x with x = h/a).  points: n x 2 row-major doubles (x_i, y_i).
- * A_tiles: output, T b*b doubles in the tile layout above (padding set to identity).
+ * h = |s_i - s_j|, x = h/a.  nu in {0.5, 1.5, 2.5} takes the closed forms e^-x, (1+x)e^-x,
+ * (1+x+x^2/3)e^-x; any other nu in (0, 16] evaluates K_nu on the device (Temme's series for
+ * x <= 2, Temme's normalising sum with Miller's backward recurrence above, then the upward
+ * recurrence in nu; relative error a few units of 1e-15).  points: n x 2 row-major doubles
+ * (x_i, y_i).  A_tiles: output, T b*b doubles in the tile layout above (padding set to
+ * identity).
  * Errors: TC_ERR_ARG for n < 1, b not in [64, 4096] or not a multiple of 64, a <= 0,
- * sigma2 <= 0 or another nu.
+ * sigma2 <= 0 or nu outside (0, 16].
  */
 int tc_matern_tiles(tc_handle h, int64_t n, int b, const double *points,
                     double sigma2, double range_a, double nu, double nugget,

@@ -865,11 +865,11 @@ int tc_matern_tiles(tc_handle h, int64_t n, int b, const double *points, double 
     if (rc) return rc;
     if (!points || !A_tiles) return set_err(h, TC_ERR_ARG, "points and A_tiles must not be NULL");
     if (!(range_a > 0) || !(sigma2 > 0)) return set_err(h, TC_ERR_ARG, "range and variance must be positive");
-    int nu2 = 0;
+    int nu2 = 0;                                  // 0: the Bessel form for any other nu
     if (nu == 0.5) nu2 = 1;
     else if (nu == 1.5) nu2 = 3;
     else if (nu == 2.5) nu2 = 5;
-    else return set_err(h, TC_ERR_ARG, "smoothness must be 0.5, 1.5 or 2.5");
+    else if (!(nu > 0.0 && nu <= 16.0)) return set_err(h, TC_ERR_ARG, "smoothness must lie in (0, 16]");
     CK(cudaSetDevice(h->device));
     const int nt = (int)((n + b - 1) / b);
     const double *dpts = points;
@@ -888,7 +888,7 @@ int tc_matern_tiles(tc_handle h, int64_t n, int b, const double *points, double 
         if (rc) { release(tmp_pts); return rc; }
         dout = static_cast<double *>(tmp_out.p);
     }
-    launch_matern(dout, n, b, nt, dpts, sigma2, range_a, nu2, nugget, h->s);
+    launch_matern(dout, n, b, nt, dpts, sigma2, range_a, nu2, nu, nugget, h->s);
     CK_LAUNCH();
     if (!out_dev) CK(cudaMemcpyAsync(A_tiles, dout, bytes, cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));

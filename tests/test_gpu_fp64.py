@@ -53,6 +53,59 @@ def test_matern_tiles_match_oracle(H, nu):
     assert np.array_equal(full[n:, n:], np.eye(N - n)) and not np.any(full[n:, :n])
 
 
+@pytest.mark.parametrize("nu", [0.3, 0.8, 1.0, 1.25, 2.0, 3.7, 7.5, 16.0])
+@pytest.mark.parametrize("a", [0.07, 0.6])
+def test_matern_general_nu_matches_oracle(H, nu, a):
+    # Eq. 2 through K_nu for a smoothness without a closed form; a = 0.6 puts most x = h/a
+    # below 2 (Temme's series), a = 0.07 most above (the backward recurrence).  The oracle is
+    # scipy's K_nu, up to 8e-14 (nu = 0.8) from 40-digit values on these inputs; the device
+    # arithmetic stays within 5e-15 of them.
+    n, b = 1000, 128
+    pts = inputs.uniform_points(n, seed=5)
+    A = torch.full((tc.tile_count(n, b) * b * b,), float("nan"), dtype=torch.float64, device=DEV)
+    tc.tc_matern_tiles(H.h, n, b, to_dev(pts), 1.3, a, nu, 1e-5, A)
+    got = unpack_sym(A, n, b)
+    ref = oracle.matern_bessel(pts, 1.3, a, nu, 1e-5)
+    assert np.allclose(got, ref, rtol=2e-13, atol=1e-300)
+    assert np.array_equal(np.diag(got), np.full(n, 1.3 + 1e-5))
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+def test_matern_general_nu_meets_closed_forms(H, nu):
+    # a smoothness one part in 1e13 off a half integer takes the Bessel path; Eq. 2 is smooth
+    # in nu, so it must land within ~1e-12 of the closed form at the half integer
+    n, b = 512, 128
+    pts = inputs.uniform_points(n, seed=6)
+    A = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=DEV)
+    tc.tc_matern_tiles(H.h, n, b, to_dev(pts), 1.0, 0.2, nu * (1 + 1e-13), 0.0, A)
+    got = unpack_sym(A, n, b)
+    assert np.allclose(got, oracle.matern(pts, 1.0, 0.2, nu, 0.0), rtol=1e-11, atol=0)
+
+
+def test_matern_rejects_smoothness_out_of_range(H):
+    pts = inputs.uniform_points(128, seed=1)
+    A = torch.empty(tc.tile_count(128, 128) * 128 * 128, dtype=torch.float64, device=DEV)
+    for nu in (0.0, -1.0, 16.5, float("nan")):
+        with pytest.raises(tc.TileCholError):
+            tc.tc_matern_tiles(H.h, 128, 128, to_dev(pts), 1.0, 0.1, nu, 0.0, A)
+
+
+def test_general_nu_factor_matches_oracle(H):
+    # nu = 1 (an integer order: mu = 0 in Temme's series) through the whole FP64 path
+    n, b = 768, 128
+    pts = inputs.uniform_points(n, seed=7, morton=True)
+    At = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=DEV)
+    tc.tc_matern_tiles(H.h, n, b, to_dev(pts), 1.0, 0.05, 1.0, 1e-4, At)
+    assert tc.tile_chol_factor(H.h, n, b, At) == 0
+    A = oracle.matern_bessel(pts, 1.0, 0.05, 1.0, 1e-4)
+    Lo = oracle.cholesky(A)
+    assert abs(tc.tile_chol_logdet(H.h) - oracle.logdet(Lo)) <= 1e-11 * abs(oracle.logdet(Lo))
+    L = torch.empty_like(At)
+    tc.tile_chol_get_factor(H.h, L)
+    Lg = unpack_lower(L, n, b)
+    assert np.linalg.norm(A - Lg @ Lg.T) / np.linalg.norm(A) <= 64 * n * U
+
+
 def test_matern_full_size_sampled_entries(H):
     w = inputs.WORKLOADS["fp64_n65536"]
     pts = w.points()

@@ -111,6 +111,38 @@ def test_matern_closed_forms_equal_bessel_form(nu):
     assert np.allclose(A, B, rtol=1e-12, atol=1e-300)
 
 
+@pytest.mark.parametrize("nu", [0.3, 0.8, 1.0, 1.25, 3.7, 7.5, 16.0])
+def test_matern_bessel_equals_the_integral_form(nu):
+    # K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt (DLMF 10.32.9), integrated by quadrature:
+    # pins the Bessel form of Eq. 2 for any smoothness without going through K_nu itself
+    from scipy.integrate import quad
+    from scipy.special import gamma
+    pts = np.array([[0.0, 0.0], [0.3, 0.4], [0.05, 0.0], [0.9, 0.9], [0.001, 0.0]])
+    a = 0.25
+    C = oracle.matern_bessel(pts, 1.0, a, nu)
+    for j in range(1, len(pts)):
+        x = float(np.hypot(*(pts[j] - pts[0]))) / a
+        tmax = float(np.arccosh(max(1000.0 / x, 1.0))) + 1.0        # the integrand is < e^-900 beyond
+        f = lambda t: 0.5 * (np.exp(nu * t - x * np.cosh(t)) + np.exp(-nu * t - x * np.cosh(t)))
+        kx = quad(f, 0.0, tmax, epsabs=0, epsrel=1e-13, limit=400)[0]
+        ref = 2.0 ** (1.0 - nu) / gamma(nu) * x ** nu * kx
+        assert abs(C[j, 0] - ref) <= 1e-11 * ref, (nu, x)
+    assert C[0, 0] == 1.0 and np.allclose(C, C.T, rtol=0, atol=0)
+
+
+def test_matern_bessel_against_high_precision_values():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    pts = inputs.uniform_points(40, seed=8)
+    for nu in (0.3, 0.8, 1.25, 7.5):
+        C = oracle.matern_bessel(pts, 1.0, 0.1, nu)
+        for i, j in ((1, 0), (7, 3), (20, 11), (39, 38)):
+            x = mpmath.sqrt(sum((mpmath.mpf(float(pts[i, k])) - mpmath.mpf(float(pts[j, k]))) ** 2 for k in (0, 1)))
+            x = x / mpmath.mpf(0.1)
+            ref = float(mpmath.mpf(2) ** (1 - nu) / mpmath.gamma(nu) * x ** nu * mpmath.besselk(nu, x))
+            assert abs(C[i, j] - ref) <= 1e-13 * ref, (nu, i, j)
+
+
 def test_loglik_matches_scipy_gaussian_logpdf():
     from scipy.stats import multivariate_normal
     pts = inputs.uniform_points(150, seed=9)
