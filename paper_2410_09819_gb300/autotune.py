@@ -1,21 +1,29 @@
-"""Tile-size autotuner for the batched factorization.
+"""Autotuners for the two shapes that are free at run time.
 
-Times ``tile_chol_factor_batched`` (graph replay, after one capture) for each candidate tile
-size on the caller's batch and returns the fastest.  The tile size is the only free shape
-parameter of the kernels: the FP64 update works on 64 x 64 register blocks and the tensor-core
-update on 128 x 128 blocks whatever the tile, so the tile size sets the number of tasks, the
-parallelism per column step and the amount of padding of ragged matrices.
+* In core, batched: the tile size.  The FP64 update works on 64 x 64 register blocks and the
+  tensor-core updates on fixed 128-row blocks whatever the tile, so the tile size sets the number
+  of tasks, the parallelism per column step and the padding of ragged matrices.
+  ``pick_batched_tile`` times ``tile_chol_factor_batched`` (graph replay, after one capture) for
+  each candidate on the caller's batch and returns the fastest.
+* Out of core: the tile size, the scheduling policy and the eviction rule under a device-cache
+  cap.  The static schedule makes the copy volume of every candidate computable in advance
+  (``ooc_sim`` predicts the library's counters exactly), so ``rank_ooc_candidates`` keeps the
+  candidates within a slack of the smallest predicted volume and ``pick_ooc_config`` times only
+  those, through a caller-supplied run.  The prefetch depth is not a free parameter: the
+  executor enqueues its whole static schedule, so copies run ahead as far as free slots allow.
 """
 from __future__ import annotations
 
 import time
+from dataclasses import dataclass
 
-from . import tile_chol as tc
+from . import ooc_sim
 
 
 def pick_batched_tile(H, ns, make_inputs, candidates=(128, 256), repeats=2):
     """make_inputs(b) -> (A_list, maps) for tile size b.  Returns (best_b, {b: seconds})."""
     import torch
+    from . import tile_chol as tc
     times = {}
     for b in candidates:
         A_list, maps = make_inputs(b)
@@ -30,4 +38,63 @@ def pick_batched_tile(H, ns, make_inputs, candidates=(128, 256), repeats=2):
         times[b] = best
         del A_list, maps
         torch.cuda.empty_cache()
+    return min(times, key=times.get), times
+
+
+@dataclass(frozen=True)
+class OocCandidate:
+    """One out-of-core configuration: tc_config.ooc = POLICIES.index(policy),
+    tc_config.ooc_eviction = 0 (lru) or 1 (min), tile size b, with its predicted copies."""
+    b: int
+    policy: str
+    eviction: str
+    nslots: int
+    h2d_bytes: int
+    d2h_bytes: int
+
+    @property
+    def bytes_moved(self) -> int:
+        return self.h2d_bytes + self.d2h_bytes
+
+    def config_fields(self) -> dict:
+        return {"ooc": ooc_sim.POLICIES.index(self.policy), "ooc_eviction": 0 if self.eviction == "lru" else 1}
+
+
+def rank_ooc_candidates(n, cap_bytes, tiles=(1024, 2048), policies=("V3",), evictions=("lru", "min"),
+                        emulated=True, pmap_for=None, slack=1.25):
+    """Predicted copies of every (tile, policy, eviction) under the device-cache cap, the ones
+    within ``slack`` x the smallest predicted volume, fewest bytes first.  ``pmap_for(b)`` gives
+    the precision map for tile size b (None: all FP64).  Tiles the cap cannot hold (the
+    simulator's MemoryError) and tile sizes the emulated engine cannot run (b not a multiple of
+    128) are left out."""
+    if slack < 1.0:
+        raise ValueError("slack must be >= 1")
+    out = []
+    for b in tiles:
+        if emulated and b % 128:
+            continue
+        pmap = pmap_for(b) if pmap_for is not None else None
+        nslots = ooc_sim.slots_for_cap(cap_bytes, n, b, emulated, mixed=pmap is not None)
+        for p in policies:
+            for e in evictions:
+                try:
+                    r = ooc_sim.simulate(n, b, nslots, emulated=emulated, pmap=pmap, policy=p, eviction=e)
+                except MemoryError:
+                    continue
+                out.append(OocCandidate(b, p, e, nslots, r.h2d_bytes, r.d2h_bytes))
+    if not out:
+        return []
+    best = min(c.bytes_moved for c in out)
+    keep = [c for c in out if c.bytes_moved <= slack * best]
+    return sorted(keep, key=lambda c: (c.bytes_moved, c.b, c.policy, c.eviction))
+
+
+def pick_ooc_config(candidates, run, repeats=1):
+    """Times run(candidate) -> seconds (one out-of-core factorization in that configuration, the
+    host matrix restored by the caller) for each candidate; returns (best, {candidate: seconds})."""
+    if not candidates:
+        raise ValueError("no candidate configuration fits the cache")
+    times = {}
+    for c in candidates:
+        times[c] = min(run(c) for _ in range(repeats))
     return min(times, key=times.get), times

@@ -128,3 +128,57 @@ def test_belady_min_never_loses_to_lru(emulated, nt, slots, b):
 def test_belady_min_hand_case():
     # 4 slots, Nt = 3, DFMA order: LRU and MIN agree while nothing must be evicted
     assert simulate(3 * 64, 64, 8, eviction="min").misses == simulate(3 * 64, 64, 8).misses == tidx(3, 0)
+
+
+# ---------------------------------------------------------------- out-of-core tuner (host half)
+def test_ooc_tuner_ranks_by_predicted_volume():
+    from paper_2410_09819_gb300.autotune import rank_ooc_candidates
+    from paper_2410_09819_gb300.ooc_sim import slots_for_cap
+    n = 16 * 256
+    cap = 40 * (256 * 256 * 8 + 14 * 256 * 256 + 16)
+    cands = rank_ooc_candidates(n, cap, tiles=(128, 256, 320), policies=("V3", "V1"), evictions=("lru", "min"),
+                                slack=10.0)
+    assert cands and all(c.b in (128, 256) for c in cands)          # 320 is no multiple of 128
+    vols = [c.bytes_moved for c in cands]
+    assert vols == sorted(vols)
+    for c in cands:                                                  # each prediction is the simulator's
+        r = simulate(n, c.b, slots_for_cap(cap, n, c.b, True), emulated=True, policy=c.policy, eviction=c.eviction)
+        assert (c.h2d_bytes, c.d2h_bytes) == (r.h2d_bytes, r.d2h_bytes)
+        assert c.nslots == slots_for_cap(cap, n, c.b, True)
+    # for one tile and policy, MIN never moves more than LRU
+    by = {(c.b, c.policy, c.eviction): c.bytes_moved for c in cands}
+    for b in (128, 256):
+        for p in ("V3", "V1"):
+            if (b, p, "lru") in by and (b, p, "min") in by:
+                assert by[(b, p, "min")] <= by[(b, p, "lru")]
+    tight = rank_ooc_candidates(n, cap, tiles=(128, 256), policies=("V3", "V1"), slack=1.0)
+    assert tight and all(c.bytes_moved == vols[0] for c in tight)
+    assert tight[0].config_fields()["ooc"] in (0, 2)
+
+
+def test_ooc_tuner_skips_tiles_the_cache_cannot_hold():
+    from paper_2410_09819_gb300.autotune import rank_ooc_candidates
+    n, b = 8 * 256, 256
+    tiny = 3 * (b * b * 8 + 14 * b * b + 16)                         # three slots: too few for any launch
+    assert rank_ooc_candidates(n, tiny, tiles=(b,)) == []
+    with pytest.raises(ValueError):
+        rank_ooc_candidates(n, tiny, tiles=(b,), slack=0.5)
+
+
+def test_ooc_tuner_times_only_the_ranked_candidates():
+    from paper_2410_09819_gb300.autotune import pick_ooc_config, rank_ooc_candidates
+    n = 12 * 256
+    cap = 30 * (256 * 256 * 8 + 14 * 256 * 256 + 16)
+    cands = rank_ooc_candidates(n, cap, tiles=(128, 256), evictions=("lru", "min"), slack=2.0)
+    seen = []
+
+    def run(c):                       # a stand-in for one timed factorization: 1 s per 10 GB moved
+        seen.append(c)
+        return c.bytes_moved / 1e10 + (0.0 if c.b == 256 else 0.5)
+
+    best, times = pick_ooc_config(cands, run, repeats=2)
+    assert len(seen) == 2 * len(cands) and set(times) == set(cands)
+    assert times[best] == min(times.values())
+    assert best.config_fields()["ooc_eviction"] == (0 if best.eviction == "lru" else 1)
+    with pytest.raises(ValueError):
+        pick_ooc_config([], run)
