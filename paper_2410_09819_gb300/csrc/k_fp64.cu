@@ -895,9 +895,10 @@ void launch_trsm_rows(double *P, const double *L, int ld, int rows, const int *s
 }
 void launch_trsm_strips(const TStrip *strips, int nstrips, int ld, int b, const int *status, cudaStream_t s) {
     const size_t smem = (32 * 64 + 2 * 64 * 65 + 64) * sizeof(double);
-    static unsigned long long attr = 0;
-    if (first_on_device(attr)) {
+    static std::atomic<unsigned long long> attr{0};
+    if (attrs_pending(attr)) {
         cudaFuncSetAttribute(k_trsm_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        mark_attrs_set(attr);
     }
     if (nstrips > 0) k_trsm_strips<<<nstrips, 256, smem, s>>>(strips, ld, b, status);
 }
@@ -1173,9 +1174,10 @@ void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s) {
 }
 static size_t trsm_tile_smem() {
     const size_t smem = (32 * 64 + 2 * 64 * 65 + 64) * sizeof(double);
-    static unsigned long long attr = 0;
-    if (first_on_device(attr)) {
+    static std::atomic<unsigned long long> attr{0};
+    if (attrs_pending(attr)) {
         cudaFuncSetAttribute(k_trsm_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        mark_attrs_set(attr);
     }
     return smem;
 }
@@ -1192,10 +1194,12 @@ void launch_trsm_group(double *const *C, int ntiles, const double *L, int ld, in
 }
 void launch_trinv(const double *L, int b, double *Y, cudaStream_t s) {
     const size_t smem = ((size_t)b * TRINV_COLS + 64 * 65 + 64 * TRINV_COLS) * sizeof(double);
-    static unsigned long long attr = 0;
-    if (first_on_device(attr))     // sized for the largest tile it serves (b <= 2048)
+    static std::atomic<unsigned long long> attr{0};
+    if (attrs_pending(attr)) {     // sized for the largest tile it serves (b <= 2048)
         cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(((size_t)2048 * TRINV_COLS + 64 * 65 + 64 * TRINV_COLS) * sizeof(double)));
+        mark_attrs_set(attr);
+    }
     k_trinv<<<b / (2 * TRINV_COLS), 256, smem, s>>>(L, b, Y);
 }
 void launch_logdiag_tile(const double *D, int b, int nv, double *out, cudaStream_t s) {

@@ -536,10 +536,11 @@ size_t qgemm_smem_bytes() { return (size_t)QSTAGES * QSTAGE_BYTES + 1024 + 256; 
 template <int KIND, class Args>
 static void launch_q(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0, const CUtensorMap &b1,
                      const Args &args, int nitems, cudaStream_t s) {
-    static unsigned long long attr = 0;
+    static std::atomic<unsigned long long> attr{0};
     const size_t smem = qgemm_smem_bytes();
-    if (first_on_device(attr)) {
+    if (attrs_pending(attr)) {
         cudaFuncSetAttribute(k_qgemm<KIND, Args>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        mark_attrs_set(attr);
     }
     k_qgemm<KIND, Args><<<nitems, QTHREADS, smem, s>>>(a0, a1, b0, b1, args);
 }

@@ -567,12 +567,15 @@ int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_ro
 
 size_t zgemm_smem_bytes() { return (size_t)ZXS * ZX_BYTES + ZYS * ZYSET + 1024 + 256; }
 
-static int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+static int sm_count() {            // per device, cached
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> &c = cache[dev & 63];
+    int n = c.load(std::memory_order_relaxed);
+    if (n <= 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        c.store(n, std::memory_order_relaxed);
     }
     return n;
 }
@@ -596,14 +599,15 @@ void launch_add_tiles(double *W, int b, const int *tiles, int ntiles, const doub
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
                   int b, int *err, cudaStream_t s, int planes, int assign) {
     if (nitems <= 0 || k <= 0) return;
-    static unsigned long long attr = 0;
+    static std::atomic<unsigned long long> attr{0};
     const size_t smem = zgemm_smem_bytes();
-    if (first_on_device(attr)) {
+    if (attrs_pending(attr)) {
         cudaFuncSetAttribute(k_zgemm<14, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<10, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<7, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<6, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<4, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        mark_attrs_set(attr);
     }
     ZArgs a{items, nitems, exps, k, b, err, assign};
     const int grid = nitems < sm_count() ? nitems : sm_count();      // persistent: one CTA per SM
@@ -617,14 +621,15 @@ void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *ite
 void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGroup &g, const int *exps, int b,
                         int *err, cudaStream_t s, int planes) {
     if (g.ntiles <= 0 || g.k <= 0) return;
-    static unsigned long long attr = 0;
+    static std::atomic<unsigned long long> attr{0};
     const size_t smem = zgemm_smem_bytes();
-    if (first_on_device(attr)) {
+    if (attrs_pending(attr)) {
         cudaFuncSetAttribute(k_zgemm<14, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<10, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<7, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<6, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_zgemm<4, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        mark_attrs_set(attr);
     }
     ZGroupArgs a;
     memset(&a, 0, sizeof a);

@@ -1,6 +1,7 @@
 // Internal declarations shared by the tile_chol translation units (not part of the ABI).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -121,15 +122,20 @@ void launch_dgemm_tile(const DJob &job, int ld, cudaStream_t s);
 void launch_trsm_tile(double *C, const double *L, int ld, int b, const int *status, cudaStream_t s);
 constexpr int TG_MAX = 16;   // tiles per grouped TRSM launch
 
-// Function attributes (dynamic shared-memory opt-in) are per device: true the first time it
-// is called for the current device (one bit per device ordinal; setting one twice is harmless).
-inline bool first_on_device(unsigned long long &mask) {
+// Function attributes (dynamic shared-memory opt-in) are per device.  attrs_pending() stays
+// true for the current device until mark_attrs_set() records it (one bit per device ordinal),
+// so a host thread never launches before the attributes are in place: two threads may both
+// set them once, which is harmless.
+inline unsigned long long device_bit() {
     int dev = 0;
     cudaGetDevice(&dev);
-    const unsigned long long bit = 1ull << (dev & 63);
-    if (mask & bit) return false;
-    mask |= bit;
-    return true;
+    return 1ull << (dev & 63);
+}
+inline bool attrs_pending(const std::atomic<unsigned long long> &mask) {
+    return !(mask.load(std::memory_order_acquire) & device_bit());
+}
+inline void mark_attrs_set(std::atomic<unsigned long long> &mask) {
+    mask.fetch_or(device_bit(), std::memory_order_release);
 }
 void launch_trinv(const double *L, int b, double *Y, cudaStream_t s);   // Y = L^{-1}, b x b
 void launch_trsm_group(double *const *C, int ntiles, const double *L, int ld, int b, const int *status,
