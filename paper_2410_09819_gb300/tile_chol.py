@@ -118,6 +118,32 @@ def _ptr(x) -> int | None:
     raise TypeError(f"unsupported buffer type {type(x)!r}")
 
 
+def _need(x, kind: str, count: int | None, what: str) -> None:
+    """Reject a torch tensor or numpy array of the wrong element type, or with fewer than
+    ``count`` elements, before the library reads or writes through its address (the C ABI sees
+    only a pointer).  Raw integer addresses and None pass through unchecked."""
+    if x is None or isinstance(x, int):
+        return
+    if hasattr(x, "data_ptr"):
+        dt, size = str(x.dtype).replace("torch.", ""), x.numel()
+    elif isinstance(x, np.ndarray):
+        dt, size = str(x.dtype), x.size
+    else:
+        return                                  # _ptr rejects other buffer types
+    if dt != kind:
+        raise TileCholError(-1, f"{what} must hold {kind} elements, not {dt}")
+    if count is not None and size < count:
+        raise TileCholError(-1, f"{what} needs at least {count} elements, has {size}")
+
+
+def _need_tiles(n, b, A_tiles, map_=None, what="A_tiles"):
+    """The packed lower tiles (T b^2 doubles) and a precision map (Nt^2 bytes) of order n, tile b;
+    sizes are checked only for n, b the library accepts at all (it reports the rest itself)."""
+    ok = isinstance(n, (int, np.integer)) and isinstance(b, (int, np.integer)) and n >= 1 and b >= 1
+    _need(A_tiles, "float64", tile_count(n, b) * b * b if ok else None, what)
+    _need(map_, "uint8", ntiles(n, b) ** 2 if ok else None, "map")
+
+
 def _check(h, rc: int, allow_positive: bool = False) -> int:
     if rc == TC_OK or (allow_positive and rc > 0):
         return rc
@@ -157,16 +183,22 @@ def tc_last_error(h) -> str:
 
 
 def tc_matern_tiles(h, n, b, points, sigma2, range_a, nu, nugget, A_tiles) -> None:
+    _need(points, "float64", 2 * n if isinstance(n, (int, np.integer)) and n >= 1 else None, "points")
+    _need_tiles(n, b, A_tiles)
     _check(h, lib().tc_matern_tiles(h, n, b, _ptr(points), sigma2, range_a, nu, nugget, _ptr(A_tiles)))
 
 
 def tile_chol_precision_map(h, n, b, A_tiles, eps_high, band, prec_set, map_out, norms_out=None) -> None:
+    _need_tiles(n, b, A_tiles, map_out)
+    if isinstance(n, (int, np.integer)) and isinstance(b, (int, np.integer)) and n >= 1 and b >= 1:
+        _need(norms_out, "float64", ntiles(n, b) ** 2 + 1, "norms_out")
     _check(h, lib().tile_chol_precision_map(h, n, b, _ptr(A_tiles), eps_high, band, prec_set,
                                             _ptr(map_out), _ptr(norms_out)))
 
 
 def tile_chol_factor(h, n, b, A_tiles, map=None, stats: tc_stats | None = None) -> int:
     """Returns 0, or the 1-based column of a non-positive pivot (matrix not SPD)."""
+    _need_tiles(n, b, A_tiles, map)
     return _check(h, lib().tile_chol_factor(h, n, b, _ptr(A_tiles), _ptr(map),
                                             ctypes.byref(stats) if stats is not None else None),
                   allow_positive=True)
@@ -174,12 +206,15 @@ def tile_chol_factor(h, n, b, A_tiles, map=None, stats: tc_stats | None = None) 
 
 def tile_chol_factor_ooc(h, n, b, A_tiles, map=None, stats: tc_stats | None = None) -> int:
     """Out-of-core factor: A_tiles (host) is overwritten by L.  Returns 0 or the failing column."""
+    _need_tiles(n, b, A_tiles, map)
     return _check(h, lib().tile_chol_factor_ooc(h, n, b, _ptr(A_tiles), _ptr(map),
                                                 ctypes.byref(stats) if stats is not None else None),
                   allow_positive=True)
 
 
 def tile_chol_solve(h, nrhs, B, ldb, X, ldx, max_refine=0, target_berr=0.0, stats: tc_stats | None = None) -> None:
+    _need(B, "float64", None, "B")
+    _need(X, "float64", None, "X")
     _check(h, lib().tile_chol_solve(h, nrhs, _ptr(B), ldb, _ptr(X), ldx, max_refine, target_berr,
                                     ctypes.byref(stats) if stats is not None else None))
 
@@ -192,6 +227,7 @@ def tile_chol_logdet(h) -> float:
 
 def tile_chol_loglik(h, y=None) -> float:
     out = ctypes.c_double()
+    _need(y, "float64", None, "y")
     _check(h, lib().tile_chol_loglik(h, _ptr(y), ctypes.byref(out)))
     return out.value
 
@@ -199,11 +235,13 @@ def tile_chol_loglik(h, y=None) -> float:
 def tile_chol_loglik_refined(h, y, max_refine=5, target_berr=1e-14):
     """Eq. 1 with y^T Sigma^{-1} y from a refined solve.  Returns (loglik, backward error)."""
     out, be = ctypes.c_double(), ctypes.c_double()
+    _need(y, "float64", None, "y")
     _check(h, lib().tile_chol_loglik_refined(h, _ptr(y), max_refine, target_berr, ctypes.byref(out), ctypes.byref(be)))
     return out.value, be.value
 
 
 def tile_chol_get_factor(h, L_tiles) -> None:
+    _need(L_tiles, "float64", None, "L_tiles")
     _check(h, lib().tile_chol_get_factor(h, _ptr(L_tiles)))
 
 
@@ -252,6 +290,7 @@ def tile_chol_loglik_batched(h, y_list, count=None):
 
 def tile_chol_precision_map_noalloc(n, b, A_tiles, eps_high, band, prec_set, map_out, stream=None) -> None:
     """Precision map into a caller-owned device buffer without any allocation (see the header)."""
+    _need_tiles(n, b, A_tiles, map_out)
     rc = lib().tile_chol_precision_map_noalloc(n, b, _ptr(A_tiles), eps_high, band, prec_set, _ptr(map_out),
                                                stream)
     if rc != TC_OK:
