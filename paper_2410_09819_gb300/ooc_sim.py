@@ -27,6 +27,7 @@ class SimResult:
     written_back: list = field(default_factory=list)
     tasks: int = 0
     requests: list = field(default_factory=list)
+    schedule: list = field(default_factory=list)   # ("gemm", m, k, n) / ("potrf", k, k) / ("trsm", m, k)
 
 
 class _Cache:
@@ -212,6 +213,7 @@ def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
                         assert all(C.slot_tile[sc[m]] == tidx(m, k) for m in ms)
                         assert sum(1 for p in C.pins if p) <= nslots
                     C.r.tasks += len(ms) * len(ns)
+                    C.r.schedule.extend(("gemm", m, k, nn) for m in ms for nn in ns)
                     for s in xs + ys:
                         C.pins[s] -= 1
                     if not keep_ops:
@@ -239,6 +241,7 @@ def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
                             C.pins[sc[m]] -= 1
                             C.forget(sc[m])
                         C.r.tasks += 1
+                        C.r.schedule.append(("gemm", m, k, nn))
             if not keep_acc:
                 acq_accs()
             if g0 != k and not pin_diag:
@@ -250,6 +253,7 @@ def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
                 assert C.slot_tile[diag] == tidx(k, k)          # L_kk resident for the TRSMs
             for m in ms:
                 t = tidx(m, k)
+                C.r.schedule.append(("potrf", k, k) if m == k else ("trsm", m, k))
                 C.r.d2h_bytes += C.tile_bytes + (bb * ELEM_BYTES[prec[t]] if prec[t] else 0)
                 C.r.written_back.append(t)
                 final.add(t)
@@ -270,3 +274,53 @@ def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
         assert all(p == 0 for p in C.pins)
     C.r.requests = C.requests
     return C.r
+
+
+def left_looking_tasks(nt: int) -> list:
+    """Algorithm 1's static order for Nt tile columns: for each column k, the updates
+    ("gemm", m, k, n) of every tile m >= k over the finished columns n < k (the SYRK when
+    m = k), then ("potrf", k, k), then ("trsm", m, k) for m > k."""
+    out = []
+    for k in range(nt):
+        out.extend(("gemm", m, k, n) for m in range(k, nt) for n in range(k))
+        out.append(("potrf", k, k))
+        out.extend(("trsm", m, k) for m in range(k + 1, nt))
+    return out
+
+
+def validate_schedule(tasks, nt: int) -> None:
+    """Host-side check of a task list against the dependencies of the left-looking
+    factorization (Section III-A): an update of tile (m, k) with column n < k reads the final
+    tiles (m, n) and (k, n) and runs once, before (m, k) is final; POTRF(k, k) and TRSM(m, k)
+    follow all k updates of their tile, TRSM after POTRF(k, k); every lower tile ends final.
+    Raises ValueError at the first violation."""
+    final, seen, done = set(), set(), {}
+    for i, task in enumerate(tasks):
+        op, m, k = task[0], task[1], task[2]
+        if not (0 <= k <= m < nt):
+            raise ValueError(f"task {i} {task}: tile outside the lower triangle")
+        if (m, k) in final:
+            raise ValueError(f"task {i} {task}: tile ({m}, {k}) is already final")
+        if op == "gemm":
+            n = task[3]
+            if not 0 <= n < k:
+                raise ValueError(f"task {i} {task}: source column must precede column {k}")
+            if (m, n) not in final or (k, n) not in final:
+                raise ValueError(f"task {i} {task}: reads a tile that is not final")
+            if task in seen:
+                raise ValueError(f"task {i} {task}: update repeated")
+            seen.add(task)
+            done[(m, k)] = done.get((m, k), 0) + 1
+        elif op in ("potrf", "trsm"):
+            if (op == "potrf") != (m == k):
+                raise ValueError(f"task {i} {task}: POTRF is for diagonal tiles, TRSM for the others")
+            if done.get((m, k), 0) != k:
+                raise ValueError(f"task {i} {task}: {done.get((m, k), 0)} of {k} updates done")
+            if op == "trsm" and (k, k) not in final:
+                raise ValueError(f"task {i} {task}: L_kk is not final")
+            final.add((m, k))
+        else:
+            raise ValueError(f"task {i} {task}: unknown operation")
+    missing = tidx(nt, 0) - len(final)
+    if missing:
+        raise ValueError(f"{missing} lower tiles never become final")

@@ -182,3 +182,51 @@ def test_ooc_tuner_times_only_the_ranked_candidates():
     assert best.config_fields()["ooc_eviction"] == (0 if best.eviction == "lru" else 1)
     with pytest.raises(ValueError):
         pick_ooc_config([], run)
+
+
+# ---------------------------------------------------------------- host validator of task lists
+@pytest.mark.parametrize("emulated", [False, True])
+@pytest.mark.parametrize("policy", ["V3", "V1", "async"])
+def test_executed_schedules_satisfy_the_dependencies(emulated, policy):
+    from paper_2410_09819_gb300.ooc_sim import left_looking_tasks, validate_schedule
+    nt, b = 11, 256
+    r = simulate(nt * b, b, 24, check=True, emulated=emulated, policy=policy)
+    validate_schedule(r.schedule, nt)
+    assert sum(1 for t in r.schedule if t[0] == "gemm") == r.tasks
+    assert sorted(r.schedule) == sorted(left_looking_tasks(nt))     # the same tasks, regrouped
+
+
+def _corrupt(kind, tasks):
+    t = list(tasks)
+    gemms = [i for i, x in enumerate(t) if x[0] == "gemm"]
+    if kind == "drop_update":
+        del t[gemms[len(gemms) // 2]]
+    elif kind == "repeat_update":
+        t.insert(gemms[-1], t[gemms[-1]])
+    elif kind == "trsm_before_potrf":
+        i = next(i for i, x in enumerate(t) if x[0] == "potrf" and x[1] == 3)
+        j = next(j for j, x in enumerate(t) if x[0] == "trsm" and x[2] == 3)
+        t[i], t[j] = t[j], t[i]
+    elif kind == "read_before_final":      # an update of column 4 moved ahead of the TRSM it reads
+        i = next(i for i, x in enumerate(t) if x[0] == "gemm" and x[2] == 4 and x[3] == 3 and x[1] == 6)
+        j = next(j for j, x in enumerate(t) if x[0] == "trsm" and x[1] == 6 and x[2] == 3)
+        t.insert(j, t.pop(i))
+    elif kind == "truncated":
+        t = t[:-1]
+    elif kind == "upper_tile":
+        t.append(("trsm", 2, 5))
+    return t
+
+
+@pytest.mark.parametrize("kind", ["drop_update", "repeat_update", "trsm_before_potrf", "read_before_final",
+                                  "truncated", "upper_tile"])
+def test_validator_catches_a_corrupted_task_list(kind):
+    from paper_2410_09819_gb300.ooc_sim import left_looking_tasks, validate_schedule
+    nt = 8
+    good = left_looking_tasks(nt)
+    validate_schedule(good, nt)
+    with pytest.raises(ValueError):
+        validate_schedule(_corrupt(kind, good), nt)
+    r = simulate(nt * 128, 128, 14, emulated=True)
+    with pytest.raises(ValueError):
+        validate_schedule(_corrupt(kind, r.schedule), nt)
