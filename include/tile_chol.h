@@ -157,8 +157,8 @@ const char *tc_last_error(tc_handle h);
  * recurrence in nu; relative error a few units of 1e-15).  points: n x 2 row-major doubles
  * (x_i, y_i).  A_tiles: output, T b*b doubles in the tile layout above (padding set to
  * identity).
- * Errors: TC_ERR_ARG for n < 1, b not in [64, 4096] or not a multiple of 64, a <= 0,
- * sigma2 <= 0 or nu outside (0, 16].
+ * Errors: TC_ERR_ARG for n < 1, b not in [64, 4096] or not a multiple of 64, more than
+ * 65535 lower tiles (Nt > 361), a <= 0, sigma2 <= 0 or nu outside (0, 16].
  */
 int tc_matern_tiles(tc_handle h, int64_t n, int b, const double *points,
                     double sigma2, double range_a, double nu, double nugget,

@@ -870,8 +870,10 @@ int tc_matern_tiles(tc_handle h, int64_t n, int b, const double *points, double 
     else if (nu == 1.5) nu2 = 3;
     else if (nu == 2.5) nu2 = 5;
     else if (!(nu > 0.0 && nu <= 16.0)) return set_err(h, TC_ERR_ARG, "smoothness must lie in (0, 16]");
-    CK(cudaSetDevice(h->device));
     const int nt = (int)((n + b - 1) / b);
+    if ((int64_t)nt * (nt + 1) / 2 > 65535)           // one grid row per lower tile
+        return set_err(h, TC_ERR_ARG, "the generator takes at most 65535 lower tiles (Nt <= 361)");
+    CK(cudaSetDevice(h->device));
     const double *dpts = points;
     DevBuf tmp_pts, tmp_out;
     if (!on_device(points)) {
