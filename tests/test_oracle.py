@@ -1,6 +1,7 @@
 """Pins for the CPU oracle against facts that do not come from the oracle itself:
 closed forms, brute force on tiny inputs, and independent library routines."""
 import itertools
+import os
 import math
 from fractions import Fraction
 
@@ -337,3 +338,38 @@ def test_mxp_low_precision_tiles_are_stored_values():
         if i > j and pm[i, j] == FP32:
             t = L[i * b:(i + 1) * b, j * b:(j + 1) * b]
             assert np.array_equal(t.astype(np.float32).astype(np.float64), t)
+
+
+# ---------------------------------------------------------------- golden fixtures
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def test_section5_theta_sets_match_the_paper():
+    rows = {r[0]: r[1:] for r in _golden_rows("section5_theta.txt")}
+    for name in ("weak", "medium", "strong"):
+        assert inputs.THETA_SETS[name] == tuple(float(v) for v in rows[name]), name
+    for level in rows["levels"]:
+        assert float(level) in inputs.SWEEP_EPS
+
+
+def test_oracle_reproduces_its_golden_values():
+    # stored by tests/golden/make_oracle_golden.py, which calls the oracle only
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_oracle_golden", os.path.join(GOLDEN, "make_oracle_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    stored = {r[0]: float(r[1]) for r in _golden_rows("oracle_fp64_n2048.txt")}
+    now = mod.values()
+    assert set(now) == set(stored)
+    for k in ("logdet", "loglik"):
+        assert abs(now[k] - stored[k]) <= 1e-12 * abs(stored[k]), k
+    for k, v in now.items():
+        if k.startswith("L["):
+            assert abs(v - stored[k]) <= 1e-13, k
+    # the first column is the closed form sqrt(sigma^2 + nugget), A[1,0] / L[0,0]
+    assert stored["L[0,0]"] == pytest.approx(math.sqrt(1.0 + 1e-6), rel=1e-15)
