@@ -38,7 +38,10 @@ Readings where the paper is silent (all listed in the design notes):
 
 Parity notes: the FP64 functions are pinned by closed forms (Pascal, tridiagonal,
 exponential covariance on a line, integer factors) and brute-force determinants in
-``tests/test_oracle.py``; the rounding helpers are pinned against numpy/torch casts;
+``tests/test_oracle.py``; ``matern_bessel`` by the closed forms at half-integer nu and, for
+other nu, by quadrature of K_nu's integral form and by 40-digit values; a regression file
+``tests/golden/oracle_fp64_n2048.txt`` holds reference values; the rounding helpers are
+pinned against numpy/torch casts;
 ``mxp_cholesky`` is pinned by exact integer cases and by reducing to ``cholesky`` on an
 all-FP64 map.
 """
