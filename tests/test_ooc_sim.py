@@ -230,3 +230,34 @@ def test_validator_catches_a_corrupted_task_list(kind):
     r = simulate(nt * 128, 128, 14, emulated=True)
     with pytest.raises(ValueError):
         validate_schedule(_corrupt(kind, r.schedule), nt)
+
+
+def test_random_configurations_keep_every_invariant():
+    # property check over random orders, tiles, caches, policies, engines and maps
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    import numpy as np
+    from paper_2410_09819_gb300.ooc_sim import POLICIES, validate_schedule
+
+    @hyp.settings(max_examples=40, deadline=None)
+    @hyp.given(nt=st.integers(1, 9), b=st.sampled_from([128, 256]), extra=st.integers(0, 40),
+               policy=st.sampled_from(POLICIES), emulated=st.booleans(), mixed=st.booleans(),
+               eviction=st.sampled_from(["lru", "min"]), seed=st.integers(0, 1000))
+    def check(nt, b, extra, policy, emulated, mixed, eviction, seed):
+        pm = None
+        if mixed and emulated:
+            pm = np.random.default_rng(seed).integers(0, 4, (nt, nt))
+        slots = 4 + extra
+        try:
+            r = simulate(nt * b, b, slots, check=True, emulated=emulated, pmap=pm, policy=policy, eviction=eviction)
+        except MemoryError:
+            return
+        validate_schedule(r.schedule, nt)
+        T = tidx(nt, 0)
+        assert r.tasks == sum(k * (nt - k) for k in range(nt))
+        assert r.misses >= T and len(r.requests) == r.hits + r.misses
+        if eviction == "min":
+            lru = simulate(nt * b, b, slots, emulated=emulated, pmap=pm, policy=policy)
+            assert r.misses <= lru.misses and r.requests == lru.requests
+
+    check()
