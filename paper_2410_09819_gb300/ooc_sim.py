@@ -10,6 +10,7 @@ before a run.  ``check=True`` also asserts the scheduling invariants at every st
 """
 from __future__ import annotations
 
+import heapq
 from dataclasses import dataclass, field
 
 
@@ -33,7 +34,11 @@ class SimResult:
 class _Cache:
     """Slot pool with LRU eviction (the library's policy), or, given the whole request
     sequence (``future``: for request i, the index of the next request of the same tile),
-    Belady's MIN: evict the unpinned tile whose next use lies farthest ahead."""
+    Belady's MIN: evict the unpinned tile whose next use lies farthest ahead.
+
+    Decisions: a miss takes the lowest-numbered free slot; else the unpinned slot used least
+    recently (LRU) or needed farthest ahead (MIN; ties to the lowest slot number).  Heaps with
+    lazy deletion find both in O(log slots), so caches of thousands of slots simulate quickly."""
 
     def __init__(self, nslots: int, ntiles: int, tile_bytes: int, future=None):
         self.slot_tile = [-1] * nslots
@@ -47,6 +52,47 @@ class _Cache:
         self.requests = []               # tiles in request order (the same for any eviction)
         self.future = future
         self.next_use = [0] * nslots     # MIN: next request index of the slot's tile
+        self.free = list(range(nslots))  # min-heap of free slot numbers (entries may be stale)
+        self.order = []                  # LRU: (last use, slot); MIN: (-next use, slot); lazy
+        self.parked = {}                 # slot -> key of a heap entry set aside while pinned
+
+    def _touch(self, s: int) -> None:
+        key = -self.next_use[s] if self.future is not None else self.last[s]
+        heapq.heappush(self.order, (key, s))
+        if len(self.order) > 8 * len(self.slot_tile) + 1024:        # drop stale entries
+            self.order = [(-self.next_use[v] if self.future is not None else self.last[v], v)
+                          for v in range(len(self.slot_tile)) if self.slot_tile[v] >= 0]
+            heapq.heapify(self.order)
+            self.parked.clear()
+
+    def _victim(self) -> int:
+        while self.free:
+            s = heapq.heappop(self.free)
+            if self.slot_tile[s] < 0:
+                return s
+        v = -1
+        while self.order:
+            key, s = heapq.heappop(self.order)
+            cur = -self.next_use[s] if self.future is not None else self.last[s]
+            if self.slot_tile[s] < 0 or cur != key:
+                continue                                   # stale entry
+            if self.pins[s]:
+                self.parked[s] = key                       # back in the heap when unpinned
+                continue
+            v = s
+            break
+        return v
+
+    def pin(self, s: int) -> None:
+        self.pins[s] += 1
+
+    def unpin(self, s: int) -> None:
+        self.pins[s] -= 1
+        if self.pins[s] == 0 and s in self.parked:
+            key = self.parked.pop(s)
+            cur = -self.next_use[s] if self.future is not None else self.last[s]
+            if self.slot_tile[s] >= 0 and cur == key:
+                heapq.heappush(self.order, (key, s))
 
     def acquire(self, t: int) -> int:
         i = len(self.requests)
@@ -58,19 +104,10 @@ class _Cache:
             self.clock += 1
             self.last[s] = self.clock
             self.next_use[s] = nxt
+            self._touch(s)
             return s
         self.r.misses += 1
-        v = next((s for s, tt in enumerate(self.slot_tile) if tt < 0), -1)
-        if v < 0 and self.future is not None:
-            best = None
-            for s in range(len(self.slot_tile)):
-                if self.pins[s] == 0 and (best is None or self.next_use[s] > best):
-                    best, v = self.next_use[s], s
-        elif v < 0:
-            best = None
-            for s in range(len(self.slot_tile)):
-                if self.pins[s] == 0 and (best is None or self.last[s] < best):
-                    best, v = self.last[s], s
+        v = self._victim()
         if v < 0:
             raise MemoryError("device tile cache too small for the schedule")
         if self.slot_tile[v] >= 0:
@@ -82,12 +119,14 @@ class _Cache:
         self.clock += 1
         self.last[v] = self.clock
         self.next_use[v] = nxt
+        self._touch(v)
         return v
 
     def forget(self, s: int) -> None:
         if self.pins[s] == 0 and self.slot_tile[s] >= 0:
             self.where[self.slot_tile[s]] = -1
             self.slot_tile[s] = -1
+            heapq.heappush(self.free, s)
 
 
 SMS = 152            # streaming multiprocessors of the GPU the groups are sized for
@@ -127,14 +166,14 @@ POLICIES = ("V3", "V2", "V1", "async", "sync")   # tc_config.ooc = 0 .. 4 (Secti
 
 
 def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = False, pmap=None,
-             policy: str = "V3", eviction: str = "lru") -> SimResult:
+             policy: str = "V3", eviction: str = "lru", record: bool = False) -> SimResult:
     """Counters of one out-of-core factorization of order n, tile b, with nslots device slots
     (``emulated``: the grouped operand order of the tensor-core updates; ``pmap``: an nt x nt
     precision map, whose low-precision tiles go back to the host also as compact copies and
     come in again only as those; ``policy``: V3 (the default), V2 without the diagonal pin, V1
     without operand reuse, async / sync without accumulator residency either; ``eviction``:
     "lru" (the library) or "min", Belady's offline optimum over the known request sequence,
-    for comparison)."""
+    for comparison; ``record``: keep the executed task list in ``SimResult.schedule``)."""
     if eviction == "min":
         # the request sequence does not depend on eviction choices: take it from an LRU run
         seq = simulate(n, b, nslots, emulated=emulated, pmap=pmap, policy=policy).requests
@@ -142,11 +181,11 @@ def simulate(n: int, b: int, nslots: int, check: bool = False, emulated: bool = 
         for i in range(len(seq) - 1, -1, -1):
             future[i] = seen.get(seq[i], len(seq) + 1)
             seen[seq[i]] = i
-        return _simulate(n, b, nslots, check, emulated, pmap, policy, future)
-    return _simulate(n, b, nslots, check, emulated, pmap, policy, None)
+        return _simulate(n, b, nslots, check, emulated, pmap, policy, future, record)
+    return _simulate(n, b, nslots, check, emulated, pmap, policy, None, record)
 
 
-def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
+def _simulate(n, b, nslots, check, emulated, pmap, policy, future, record=False) -> SimResult:
     nt = -(-n // b)
     T = tidx(nt, 0)
     nslots = min(nslots, T + 2)
@@ -186,12 +225,12 @@ def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
             def acq_accs():
                 for m in ms:
                     sc[m] = C.acquire(tidx(m, k))
-                    C.pins[sc[m]] += 1
+                    C.pin(sc[m])
 
             def release_accs():
                 for m in ms:
                     C.r.d2h_bytes += C.tile_bytes          # not final yet: copied back as FP64
-                    C.pins[sc[m]] -= 1
+                    C.unpin(sc[m])
                     C.forget(sc[m])
 
             if keep_acc:
@@ -204,18 +243,19 @@ def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
                     ys, xs = [], []
                     for nn in ns:
                         ys.append(operand(tidx(k, nn)))
-                        C.pins[ys[-1]] += 1
+                        C.pin(ys[-1])
                     for m in ms:
                         for nn in ns:
                             xs.append(operand(tidx(m, nn)))
-                            C.pins[xs[-1]] += 1
+                            C.pin(xs[-1])
                     if check:
                         assert all(C.slot_tile[sc[m]] == tidx(m, k) for m in ms)
                         assert sum(1 for p in C.pins if p) <= nslots
                     C.r.tasks += len(ms) * len(ns)
-                    C.r.schedule.extend(("gemm", m, k, nn) for m in ms for nn in ns)
+                    if record:
+                        C.r.schedule.extend(("gemm", m, k, nn) for m in ms for nn in ns)
                     for s in xs + ys:
-                        C.pins[s] -= 1
+                        C.unpin(s)
                     if not keep_ops:
                         for s in xs + ys:
                             C.forget(s)
@@ -226,41 +266,43 @@ def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
                     for nn in range(k):
                         if not keep_acc:
                             sc[m] = C.acquire(tidx(m, k))
-                            C.pins[sc[m]] += 1
+                            C.pin(sc[m])
                         sx = operand(tidx(m, nn))
-                        C.pins[sx] += 1
+                        C.pin(sx)
                         sy = operand(tidx(k, nn))
                         if check:
                             assert C.slot_tile[sc[m]] == tidx(m, k)   # V1: accumulator resident
-                        C.pins[sx] -= 1
+                        C.unpin(sx)
                         if not keep_ops:
                             C.forget(sx)
                             C.forget(sy)
                         if not keep_acc:
                             C.r.d2h_bytes += C.tile_bytes
-                            C.pins[sc[m]] -= 1
+                            C.unpin(sc[m])
                             C.forget(sc[m])
                         C.r.tasks += 1
-                        C.r.schedule.append(("gemm", m, k, nn))
+                        if record:
+                            C.r.schedule.append(("gemm", m, k, nn))
             if not keep_acc:
                 acq_accs()
             if g0 != k and not pin_diag:
                 diag = C.acquire(tidx(k, k))
-                C.pins[diag] += 1
+                C.pin(diag)
             if g0 == k:
                 diag = sc[k]
             if check:
                 assert C.slot_tile[diag] == tidx(k, k)          # L_kk resident for the TRSMs
             for m in ms:
                 t = tidx(m, k)
-                C.r.schedule.append(("potrf", k, k) if m == k else ("trsm", m, k))
+                if record:
+                    C.r.schedule.append(("potrf", k, k) if m == k else ("trsm", m, k))
                 C.r.d2h_bytes += C.tile_bytes + (bb * ELEM_BYTES[prec[t]] if prec[t] else 0)
                 C.r.written_back.append(t)
                 final.add(t)
                 if m != k:
-                    C.pins[sc[m]] -= 1
+                    C.unpin(sc[m])
             if not pin_diag:
-                C.pins[diag] -= 1
+                C.unpin(diag)
                 if not keep_ops:
                     C.forget(diag)
             if not keep_ops:
@@ -268,7 +310,7 @@ def _simulate(n, b, nslots, check, emulated, pmap, policy, future) -> SimResult:
                     if m > k:
                         C.forget(sc[m])
         if pin_diag:
-            C.pins[diag] -= 1
+            C.unpin(diag)
     if check:
         assert sorted(C.r.written_back) == list(range(T))  # every tile written back exactly once
         assert all(p == 0 for p in C.pins)

@@ -190,7 +190,7 @@ def test_ooc_tuner_times_only_the_ranked_candidates():
 def test_executed_schedules_satisfy_the_dependencies(emulated, policy):
     from paper_2410_09819_gb300.ooc_sim import left_looking_tasks, validate_schedule
     nt, b = 11, 256
-    r = simulate(nt * b, b, 24, check=True, emulated=emulated, policy=policy)
+    r = simulate(nt * b, b, 24, check=True, emulated=emulated, policy=policy, record=True)
     validate_schedule(r.schedule, nt)
     assert sum(1 for t in r.schedule if t[0] == "gemm") == r.tasks
     assert sorted(r.schedule) == sorted(left_looking_tasks(nt))     # the same tasks, regrouped
@@ -227,7 +227,7 @@ def test_validator_catches_a_corrupted_task_list(kind):
     validate_schedule(good, nt)
     with pytest.raises(ValueError):
         validate_schedule(_corrupt(kind, good), nt)
-    r = simulate(nt * 128, 128, 14, emulated=True)
+    r = simulate(nt * 128, 128, 14, emulated=True, record=True)
     with pytest.raises(ValueError):
         validate_schedule(_corrupt(kind, r.schedule), nt)
 
@@ -249,7 +249,8 @@ def test_random_configurations_keep_every_invariant():
             pm = np.random.default_rng(seed).integers(0, 4, (nt, nt))
         slots = 4 + extra
         try:
-            r = simulate(nt * b, b, slots, check=True, emulated=emulated, pmap=pm, policy=policy, eviction=eviction)
+            r = simulate(nt * b, b, slots, check=True, emulated=emulated, pmap=pm, policy=policy, eviction=eviction,
+                         record=True)
         except MemoryError:
             return
         validate_schedule(r.schedule, nt)
