@@ -262,3 +262,83 @@ def test_random_configurations_keep_every_invariant():
             assert r.misses <= lru.misses and r.requests == lru.requests
 
     check()
+
+
+class _LinearCache:
+    """The cache decisions written as plain scans over every slot (lowest free slot; else the
+    unpinned slot with the oldest use, or with the farthest next use, lowest number on ties):
+    the brute-force reference for the simulator's heap-based choice."""
+
+    def __init__(self, nslots, ntiles, tile_bytes, future=None):
+        from paper_2410_09819_gb300.ooc_sim import SimResult
+        self.slot_tile, self.pins, self.last = [-1] * nslots, [0] * nslots, [0] * nslots
+        self.next_use, self.where = [0] * nslots, [-1] * ntiles
+        self.clock, self.tile_bytes, self.load_bytes, self.future = 0, tile_bytes, None, future
+        self.r, self.requests = SimResult(), []
+
+    def acquire(self, t):
+        i = len(self.requests)
+        self.requests.append(t)
+        nxt = self.future[i] if self.future is not None else 0
+        self.clock += 1
+        if self.where[t] >= 0:
+            s = self.where[t]
+            self.r.hits += 1
+            self.last[s], self.next_use[s] = self.clock, nxt
+            return s
+        self.r.misses += 1
+        free = [s for s, tt in enumerate(self.slot_tile) if tt < 0]
+        cand = [s for s in range(len(self.slot_tile)) if self.pins[s] == 0]
+        if free:
+            v = free[0]
+        elif not cand:
+            raise MemoryError
+        elif self.future is not None:
+            v = max(cand, key=lambda s: (self.next_use[s], -s))
+        else:
+            v = min(cand, key=lambda s: (self.last[s], s))
+        if self.slot_tile[v] >= 0:
+            self.r.evictions += 1
+            self.where[self.slot_tile[v]] = -1
+        self.r.h2d_bytes += self.load_bytes(t) if self.load_bytes else self.tile_bytes
+        self.slot_tile[v], self.where[t] = t, v
+        self.last[v], self.next_use[v] = self.clock, nxt
+        return v
+
+    def pin(self, s):
+        self.pins[s] += 1
+
+    def unpin(self, s):
+        self.pins[s] -= 1
+
+    def forget(self, s):
+        if self.pins[s] == 0 and self.slot_tile[s] >= 0:
+            self.where[self.slot_tile[s]] = -1
+            self.slot_tile[s] = -1
+
+
+def test_heap_victims_equal_the_linear_scan(monkeypatch):
+    import random
+    import numpy as np
+    from paper_2410_09819_gb300 import ooc_sim
+    rng = random.Random(7)
+    compared = 0
+    for trial in range(120):
+        nt = rng.randint(2, 12)
+        b = rng.choice([128, 256])
+        emulated = rng.random() < 0.6
+        policy, eviction = rng.choice(ooc_sim.POLICIES), rng.choice(["lru", "min"])
+        slots = rng.randint(4, 4 + nt * (nt + 1) // 2)
+        pm = np.random.default_rng(trial).integers(0, 4, (nt, nt)) if emulated and rng.random() < 0.5 else None
+        args = dict(emulated=emulated, pmap=pm, policy=policy, eviction=eviction)
+        try:
+            fast = ooc_sim.simulate(nt * b, b, slots, **args)
+        except MemoryError:
+            continue
+        with monkeypatch.context() as mp:
+            mp.setattr(ooc_sim, "_Cache", _LinearCache)
+            slow = ooc_sim.simulate(nt * b, b, slots, **args)
+        key = lambda r: (r.hits, r.misses, r.evictions, r.h2d_bytes, r.d2h_bytes, r.requests)
+        assert key(fast) == key(slow), (nt, b, slots, args)
+        compared += 1
+    assert compared > 60
