@@ -6,7 +6,10 @@ cache policy (reuse on hit; on a miss the first free slot, else the least-recent
 slot that no pending task pins; the accumulator pinned through its updates (V1), the
 diagonal tile pinned until the column's TRSMs are done (V3)), so it predicts the library's
 transfer volumes and cache counters exactly without a GPU -- useful to size the device cache
-before a run.  ``check=True`` also asserts the scheduling invariants at every step.
+before a run.  ``check=True`` also asserts the scheduling invariants at every step;
+``record=True`` keeps the executed task list, which ``validate_schedule`` checks against the
+left-looking dependencies.  Victims come from heaps, so the full out-of-core configuration
+(thousands of slots, millions of requests) simulates in seconds.
 """
 from __future__ import annotations
 
