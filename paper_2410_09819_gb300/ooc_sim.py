@@ -369,3 +369,30 @@ def validate_schedule(tasks, nt: int) -> None:
     missing = tidx(nt, 0) - len(final)
     if missing:
         raise ValueError(f"{missing} lower tiles never become final")
+
+
+def main(argv=None) -> None:
+    """Command line: predict one out-of-core run's copies, e.g.
+    python -m paper_2410_09819_gb300.ooc_sim --n 262144 --tile 2048 --cap-gib 120 --eviction min"""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description=main.__doc__.splitlines()[0])
+    ap.add_argument("--n", type=int, required=True)
+    ap.add_argument("--tile", type=int, required=True)
+    ap.add_argument("--cap-gib", type=float, required=True, help="device tile-cache cap in GiB")
+    ap.add_argument("--policy", default="V3", choices=POLICIES)
+    ap.add_argument("--eviction", default="lru", choices=["lru", "min"])
+    ap.add_argument("--engine", default="emulated", choices=["emulated", "dfma"],
+                    help="emulated: FP64 updates on the tensor cores (digit planes in each slot)")
+    a = ap.parse_args(argv)
+    emulated = a.engine == "emulated"
+    nslots = slots_for_cap(int(a.cap_gib * 2**30), a.n, a.tile, emulated)
+    r = simulate(a.n, a.tile, nslots, emulated=emulated, policy=a.policy, eviction=a.eviction)
+    nt = -(-a.n // a.tile)
+    print(json.dumps({"n": a.n, "tile": a.tile, "tiles": tidx(nt, 0), "slots": nslots, "policy": a.policy,
+                      "eviction": a.eviction, "engine": a.engine, "h2d_bytes": r.h2d_bytes,
+                      "d2h_bytes": r.d2h_bytes, "hits": r.hits, "misses": r.misses, "evictions": r.evictions}))
+
+
+if __name__ == "__main__":
+    main()

@@ -342,3 +342,20 @@ def test_heap_victims_equal_the_linear_scan(monkeypatch):
         assert key(fast) == key(slow), (nt, b, slots, args)
         compared += 1
     assert compared > 60
+
+
+def test_command_line_prediction():
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-m", "paper_2410_09819_gb300.ooc_sim", "--n", "4096", "--tile", "256",
+                          "--cap-gib", "0.05", "--eviction", "min"], capture_output=True, text=True, cwd=root,
+                         timeout=120)
+    assert out.returncode == 0, out.stderr
+    d = json.loads(out.stdout)
+    from paper_2410_09819_gb300.ooc_sim import slots_for_cap
+    ns = slots_for_cap(int(0.05 * 2**30), 4096, 256, True)
+    r = simulate(4096, 256, ns, emulated=True, eviction="min")
+    assert d["slots"] == ns and d["h2d_bytes"] == r.h2d_bytes and d["misses"] == r.misses and d["tiles"] == 136
