@@ -309,7 +309,8 @@ def run_ours(args, ws, rank, local):
                         "reference": "same matrix, all-FP64 map, emulated FP64 updates, refined solve"}
 
     comparisons = None
-    if rank == 0 and not args.no_baselines:
+    # context numbers for the single-GPU line only: with N > 1 the other GPUs would sit idle
+    if rank == 0 and ws == 1 and not args.no_baselines:
         comparisons = {}
         src = Ah if not args.no_e2e else A
         if w.mixed:
