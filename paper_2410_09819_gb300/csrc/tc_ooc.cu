@@ -214,7 +214,7 @@ struct TileCache {
             wb_pending[t] = 1;
             return;
         }
-        const int p = prec.empty() ? TC_FP64 : prec[t];
+        const int p = prec.empty() ? (int)TC_FP64 : (int)prec[t];
         if (p != TC_FP64) {
             const int sp = span_begin(h, CAT_CONVERT);
             cudaMemsetAsync(amaxL + s, 0, sizeof(double), cs);
@@ -508,7 +508,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
     }
     // output precision -> operand form and update category
     auto form_of = [&](int m, int k) {
-        const int p = (m == k) ? TC_FP64 : pm[(size_t)m * nt + k];
+        const int p = (m == k) ? (int)TC_FP64 : (int)pm[(size_t)m * nt + k];
         return p == TC_FP64 ? OP_Z14 : p == TC_FP32 ? OP_Z10 : p == TC_FP16 ? OP_Q16 : OP_Q8;
     };
     static const int cat_of[OP_N] = {CAT_UPD64, CAT_UPD32, CAT_UPD16, CAT_UPD8};
@@ -517,7 +517,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
     for (int k = 0; k < nt; ++k) {
         int diag_slot = -1;
         for (int g0 = k; g0 < nt; g0 += S.group) {
-            const int g1 = std::min(nt, g0 + S.group), G = g1 - g0;
+            const int g1 = std::min(nt, g0 + S.group);
             int sc[ZG_MAX];
             // V1-V3: the accumulators stay resident (and pinned) through their updates
 #define ACQ_ACCS()                                                                            \
@@ -628,7 +628,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                         ++C.pins[sx];
                         ACQ(sy, (int)tidx(k, nn), true);
                         const int spd = span_begin(h, CAT_UPD64);   // operands are resident from here
-                        launch_dgemm_tile({C.ptr(sa), C.ptr(sx), C.ptr(sy), b, b, b, m == k ? 1 : 0}, b, h->s);
+                        launch_dgemm_tile({C.ptr(sa), C.ptr(sx), C.ptr(sy), b, b, b, m == k ? 1 : 0, nullptr}, b, h->s);
                         span_end(h, spd);
                         CK_LAUNCH();
                         ++h->upd_launches[TC_FP64];
@@ -669,7 +669,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                                          b, rows, status, h->s);
                         CK_LAUNCH();
                         const double *Pn = D + (int64_t)jb * 64 * b + (jb + 1) * 64;
-                        launch_dgemm_tile({D + (int64_t)(jb + 1) * 64 * b + (jb + 1) * 64, Pn, Pn, 64, rows, rows, 1},
+                        launch_dgemm_tile({D + (int64_t)(jb + 1) * 64 * b + (jb + 1) * 64, Pn, Pn, 64, rows, rows, 1, nullptr},
                                           b, h->s);
                         CK_LAUNCH();
                     }
@@ -758,7 +758,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
             for (int m = g0; m < g1; ++m) {
                 const int t = (int)tidx(m, k);
                 C.write_back(t, sc[m - g0]);
-                ++tiles_p[m == k ? TC_FP64 : pm[(size_t)m * nt + k]];
+                ++tiles_p[m == k ? (int)TC_FP64 : (int)pm[(size_t)m * nt + k]];
                 if (m != k) --C.pins[sc[m - g0]];
             }
             if (!pin_diag) {                         // V3 alone keeps L_kk pinned for the column
