@@ -19,6 +19,8 @@ What each function follows (sections, equations and algorithms of arXiv 2410.098
 * ``round_to`` / ``scale_exponent`` / ``to_storage`` / ``as_operand``
                         on-the-fly up/down-casting between FP64/FP32/FP16/FP8 (Section
                         IV-C and the introduction), round-to-nearest-even
+* ``mxp_update`` / ``mxp_trsm``  the update and TRSM steps of Algorithm 1 for one output
+                        tile (update in the output tile's precision, Section IV-C)
 * ``mxp_cholesky``      Algorithm 1 (left-looking tile order) executing every update in
                         the precision of the tile it writes (Section IV-C)
 * ``pack_tiles`` / ``unpack_tiles``  the lower tile-major storage of Section III-A
@@ -42,8 +44,10 @@ exponential covariance on a line, integer factors) and brute-force determinants 
 other nu, by quadrature of K_nu's integral form and by 40-digit values; a regression file
 ``tests/golden/oracle_fp64_n2048.txt`` holds reference values; the rounding helpers are
 pinned against numpy/torch casts;
-``mxp_cholesky`` is pinned by exact integer cases and by reducing to ``cholesky`` on an
-all-FP64 map.
+``mxp_cholesky`` is pinned by exact integer cases, by reducing to ``cholesky`` on an
+all-FP64 map, and by a hand-worked 6 x 6 case whose operands are narrowed (FP64 and FP16
+stored tiles feeding an FP8 output tile); ``as_operand``'s narrowing branch by hand-rounded
+values (fresh scale, subnormal range).
 """
 from __future__ import annotations
 
@@ -58,7 +62,8 @@ __all__ = [
     "FP64", "FP32", "FP16", "FP8", "UNIT_ROUNDOFF", "build",
     "matern", "matern_bessel", "cholesky", "forward", "backward", "solve", "logdet",
     "loglik", "kl_divergence", "pack_tiles", "unpack_tiles", "tile_norms", "precision_map",
-    "round_to", "scale_exponent", "to_storage", "as_operand", "mxp_cholesky", "threads",
+    "round_to", "scale_exponent", "to_storage", "as_operand", "mxp_update", "mxp_trsm", "mxp_cholesky",
+    "threads",
 ]
 
 FP64, FP32, FP16, FP8 = 0, 1, 2, 3
@@ -320,13 +325,32 @@ def as_operand(stored: np.ndarray, stored_fmt: int, fmt: int) -> np.ndarray:
 
 
 # ----------------------------------------------------- Algorithm 1, per-tile precision
+def mxp_update(A_mk: np.ndarray, X: list, Y: list, q: int) -> np.ndarray:
+    """The update step of Algorithm 1 for output tile (m, k) in precision q:
+        C = A_mk - sum_n op(X_n) op(Y_n)^T,
+    X_n = L_mn and Y_n = L_kn given as (stored tile, stored format) pairs, op = ``as_operand``
+    to q (Section IV-C: an update runs in the precision of the tile it writes).  Products
+    are accumulated in FP64."""
+    C = np.array(A_mk, dtype=np.float64)
+    for (Xn, px), (Yn, py) in zip(X, Y):
+        C -= as_operand(Xn, px, q) @ as_operand(Yn, py, q).T
+    return C
+
+
+def mxp_trsm(C: np.ndarray, Lkk: np.ndarray) -> np.ndarray:
+    """The TRSM step of Algorithm 1: X with X L_kk^T = C (Section III-A), FP64 substitution,
+    before it is stored in the tile's precision."""
+    # X L_kk^T = C  <=>  L_kk X^T = C^T
+    return forward(Lkk, np.ascontiguousarray(C.T)).T
+
+
 def mxp_cholesky(A: np.ndarray, b: int, pmap: np.ndarray):
     """Left-looking tile Cholesky (Algorithm 1) with per-tile precision.
 
     for k = 0..Nt-1, for m = k..Nt-1:
-        C = A_mk - sum_{n<k} op(L_mn) op(L_kn)^T     (op: operand in p(m, k))
+        C = A_mk - sum_{n<k} op(L_mn) op(L_kn)^T     (op: operand in p(m, k); ``mxp_update``)
         m == k: L_kk = chol(C)                        (FP64)
-        m >  k: L_mk = C L_kk^{-T}, stored in p(m, k)
+        m >  k: L_mk = C L_kk^{-T}, stored in p(m, k) (``mxp_trsm``, ``to_storage``)
     Products are accumulated in FP64 here.  Returns (dense lower L of stored values,
     info) with info the 1-based global column of a failed pivot (0 on success)."""
     n = A.shape[0]
@@ -334,22 +358,22 @@ def mxp_cholesky(A: np.ndarray, b: int, pmap: np.ndarray):
     nt = n // b
     S = {}
     L = np.zeros((n, n))
+
+    def fmt(i, j):
+        return int(pmap[i, j]) if i != j else FP64
+
     for k in range(nt):
         for m in range(k, nt):
-            q = int(pmap[m, k]) if m != k else FP64
-            C = np.array(A[m * b:(m + 1) * b, k * b:(k + 1) * b], dtype=np.float64)
-            for nn in range(k):
-                X = as_operand(S[(m, nn)], int(pmap[m, nn]) if m != nn else FP64, q)
-                Y = as_operand(S[(k, nn)], int(pmap[k, nn]) if k != nn else FP64, q)
-                C -= X @ Y.T
+            q = fmt(m, k)
+            C = mxp_update(A[m * b:(m + 1) * b, k * b:(k + 1) * b],
+                           [(S[(m, nn)], fmt(m, nn)) for nn in range(k)],
+                           [(S[(k, nn)], fmt(k, nn)) for nn in range(k)], q)
             if m == k:
                 Lkk, info = cholesky(C, return_info=True)
                 if info:
                     return L, k * b + info
                 S[(k, k)] = Lkk
             else:
-                # X L_kk^T = C  <=>  L_kk X^T = C^T
-                Xm = forward(S[(k, k)], np.ascontiguousarray(C.T)).T
-                S[(m, k)] = to_storage(Xm, q)
+                S[(m, k)] = to_storage(mxp_trsm(C, S[(k, k)]), q)
             L[m * b:(m + 1) * b, k * b:(k + 1) * b] = S[(m, k)]
     return L, 0

@@ -373,3 +373,68 @@ def test_oracle_reproduces_its_golden_values():
             assert abs(v - stored[k]) <= 1e-13, k
     # the first column is the closed form sqrt(sigma^2 + nugget), A[1,0] / L[0,0]
     assert stored["L[0,0]"] == pytest.approx(math.sqrt(1.0 + 1e-6), rel=1e-15)
+
+
+# ----------------------------------------------- narrowing casts, worked by hand
+def test_as_operand_narrowing_by_hand():
+    # An FP16-stored tile read by an FP8 update is rounded to E4M3 with a FRESH scale
+    # (Section IV-C, on-the-fly down-casting; reading: output tile's precision, RNE, new
+    # power-of-two scale).  Stored FP16 tile: amax 1 -> FP16 scale 2^-15 (65504 2^-15 >= 1),
+    # values 1, 77/256 (= 9856 2^-15, an FP16 value) and 5 2^-18 (= 0.625 2^-15).
+    s16 = np.array([1.0, 77.0 / 256.0, 5.0 * 2.0 ** -18])
+    assert np.array_equal(oracle.to_storage(s16, FP16), s16)            # it is a stored FP16 tile
+    # fresh FP8 scale: 448 2^-8 = 1.75 >= 1 > 0.875 -> e = -8; scaled: 256, 77, 5 2^-10
+    #   256 -> 256 (2^8); 77 in [64, 128), spacing 8 -> 80; 5 2^-10 is subnormal in E4M3
+    #   (below 2^-6), spacing 2^-9: 2.5 ulps, a tie, to even -> 2 2^-9 = 2^-8
+    want = np.array([1.0, 80.0 / 256.0, 2.0 ** -16])
+    got = oracle.as_operand(s16, FP16, FP8)
+    assert np.array_equal(got, want), got
+    # the mistakes this excludes: keeping the stored value (rounding to the operand's own
+    # precision, or no cast), reusing the FP16 scale (5 2^-18 2^15 = 0.625 is a normal E4M3
+    # value and would survive unrounded), or rounding without a scale (5 2^-18 -> 0)
+    assert not np.array_equal(got, s16)
+    assert oracle.round_to(np.array([5.0 * 2.0 ** -18]), FP8)[0] == 0.0
+    # an FP64-stored tile read by an FP8 update: amax 51/512, 448 2^-12 = 0.109 >= 0.0996 ->
+    # e = -12; 51/512 * 4096 = 408 in [256, 448], spacing 32 -> 416 -> 416/4096 = 13/128
+    assert oracle.as_operand(np.array([51.0 / 512.0]), FP64, FP8)[0] == 13.0 / 128.0
+    # FP64 read by an FP32 update: RNE to 24 significant bits (ulp 2^-23 at 1), no scale:
+    # 1 + 2^-24 + 2^-40 lies above the tie and rounds up; 1 + 2^-24 is a tie and goes to the
+    # even neighbour 1; 1 + 3 2^-24 is a tie between 1 + 2^-23 (odd) and 1 + 2^-22 (even)
+    v = np.array([1.0 + 2.0 ** -24 + 2.0 ** -40, 1.0 + 2.0 ** -24, 1.0 + 3.0 * 2.0 ** -24])
+    assert np.array_equal(oracle.as_operand(v, FP64, FP32), [1.0 + 2.0 ** -23, 1.0, 1.0 + 2.0 ** -22])
+    # widening is exact (operand stored narrower than the update's precision)
+    assert np.array_equal(oracle.as_operand(want, FP8, FP64), want)
+    assert np.array_equal(oracle.as_operand(want, FP8, FP16), want)
+
+
+def test_mxp_cholesky_operand_precision_by_hand():
+    # n = 6, b = 2, Nt = 3.  Map: (1,0) FP64, (2,0) FP16, (2,1) FP8.  The update of the FP8
+    # tile (2,1) reads L_20 (stored FP16) and L_10 (stored FP64); both must be rounded to FP8
+    # with fresh scales before the product (Section IV-C reading: the update runs in the
+    # output tile's precision p(2,1)).
+    A = np.zeros((6, 6))
+    A[0:2, 0:2] = np.eye(2)                                   # L_00 = I
+    A[2, 0] = 51.0 / 512.0                                    # L_10 = A_10 (L_00 = I), FP64
+    A[2:4, 2:4] = np.eye(2)
+    A[2, 2] = 1.0 + (51.0 / 512.0) ** 2                       # C_11 = A_11 - L_10 L_10^T = I exactly
+    A[4, 0], A[5, 0] = 1.0, 77.0 / 256.0                      # L_20 = A_20, FP16-exact
+    A[4, 2], A[5, 2], A[5, 3] = 7.0 / 64.0, 1.0 / 32.0, 1.0 / 64.0   # A_21
+    A[4:6, 4:6] = 4.0 * np.eye(2)
+    A = np.tril(A) + np.tril(A, -1).T
+    pm = np.array([[0, 0, 0], [FP64, 0, 0], [FP16, FP8, 0]], dtype=np.uint8)
+    L, info = oracle.mxp_cholesky(A, 2, pm)
+    assert info == 0
+    assert np.array_equal(L[0:2, 0:2], np.eye(2)) and np.array_equal(L[2:4, 2:4], np.eye(2))
+    assert L[2, 0] == 51.0 / 512.0 and L[4, 0] == 1.0 and L[5, 0] == 77.0 / 256.0
+    # op(L_20) = [1, 0.3125] (x 256: 256, 77 -> 80), op(L_10) = 13/128 (408 -> 416 at 2^-12):
+    #   C_21 = A_21 - op(L_20) op(L_10)^T = [[7/64 - 13/128, 0], [1/32 - 0.3125 * 13/128, 1/64]]
+    #        = [[2^-7, 0], [-2^-11, 2^-6]];  L_21 = C_21 (L_11 = I), stored in FP8 with scale
+    #   2^-14 (448 2^-14 >= 2^-6): 128, -8, 256 are E4M3 values, so L_21 = C_21 exactly.
+    want = np.array([[2.0 ** -7, 0.0], [-(2.0 ** -11), 2.0 ** -6]])
+    assert np.array_equal(L[4:6, 2:4], want), L[4:6, 2:4]
+    # with the operands left unrounded the same tile comes out as [[5/512, 0], [22 2^-14, 2^-6]]
+    C_exact = A[4:6, 2:4] - A[4:6, 0:2] @ A[2:4, 0:2].T
+    assert not np.array_equal(oracle.to_storage(C_exact, FP8), want)
+    # the diagonal tile (2,2) widens both stored operands exactly and runs in FP64
+    C22 = A[4:6, 4:6] - L[4:6, 0:2] @ L[4:6, 0:2].T - L[4:6, 2:4] @ L[4:6, 2:4].T
+    assert np.allclose(L[4:6, 4:6] @ L[4:6, 4:6].T, C22, rtol=0, atol=1e-15)
