@@ -35,8 +35,9 @@ METRIC = "Cholesky TFLOP/s (n^3/3) MxP vs FP64 on 1 GB300 at stated error; OOC l
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_FLOPS_PER_CLK_SM = 4.0   # GB300: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / 152 SMs / 2.07 GHz)
 NSM = 152
-CPU_SAMPLE_N = 8192
+CPU_SAMPLE_N = 12288
 OOC_MXP_EPS, OOC_MXP_BAND = 1e-9, 2
+DEFAULT_WORKLOAD = "mxp4_n131072"     # the metric's configuration: four precisions, n = 131072
 
 
 def parse_args():
@@ -45,7 +46,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="fp64_n65536", choices=sorted(inputs.WORKLOADS) + ["batched"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(inputs.WORKLOADS) + ["batched"])
     ap.add_argument("--count", type=int, default=512, help="batched workload: number of matrices")
     ap.add_argument("--fp64-mode", type=int, default=2, choices=[0, 1, 2],
                     help="FP64 updates: 0 DFMA pipe, 1 emulated on FP8 tensor cores (exact digit planes), "
@@ -60,11 +61,16 @@ def parse_args():
                     help="accuracy / performance sweep of Section V: weak, medium, strong correlation x "
                          "accuracy levels 1e-5 .. 1e-11 (one JSON object; --n sets the order, default 65536)")
     ap.add_argument("--no-baselines", action="store_true",
-                    help="skip the comparison factorizations (cuSOLVER potrf, the DFMA FP64 path)")
+                    help="skip the comparison factorizations of the FP64 workload (this library's FP64 path, "
+                         "its DFMA engine, cuSOLVER potrf); the four-precision line keeps its all-FP64 factor "
+                         "of the same matrix (accuracy reference and MxP-vs-FP64 multiple)")
     ap.add_argument("--ooc-policy", default="V3", choices=["V3", "V2", "V1", "async", "sync"],
                     help="out-of-core scheduling policy (Section III-C)")
     ap.add_argument("--ooc-eviction", default="lru", choices=["lru", "min"],
                     help="out-of-core eviction: least recently used, or Belady's MIN over the static schedule")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the dense tensor-core peaks (cuBLAS FP8 / FP16 / BF16 / TF32 / FP64 GEMMs, "
+                         "burst and sustained) and the pinned host-link rates; one JSON line")
     ap.add_argument("--ooc-mxp", action="store_true",
                     help="out-of-core workload in four precisions (map at eps_high 1e-9, FP64 band 2)")
     return ap.parse_args()
@@ -133,28 +139,119 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def kernel_source_sha() -> str:
-    src = os.path.join(ROOT, "paper_2410_09819_gb300", "csrc", "k_fp64.cu")
+def kernel_source_sha(name: str = "k_ozaki.cu") -> str:
+    """First 16 hex digits of the SHA-256 of a kernel source file (the dominant kernel's by
+    default): a committed ncu summary names the sha it was captured at."""
+    src = os.path.join(ROOT, "paper_2410_09819_gb300", "csrc", name)
     with open(src, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def profiled_traffic(kernel_tag: str, sha: str):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, if the
-    kernel source has not changed since it was captured (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    try:
-        text = open(path).read()
-    except OSError:
-        return None
-    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_tr or m_sha.group(1) != sha:
-        return None
-    return float(m_tr.group(1))
-
-
 # --------------------------------------------------------------------------- our arm
+def _tile_order(nt):
+    import numpy as np
+    i, j = np.tril_indices(nt)
+    order = np.argsort(i * (i + 1) // 2 + j)
+    return i[order], j[order]
+
+
+def tiles_matvec(P, n, b, x, dev, kind):
+    """Products with a matrix held as packed lower tiles P (tile layout, each tile column-major),
+    in harness-side torch FP64 (for the accuracy probes, outside every timed region).
+    kind "sym": the symmetric matrix (diagonal tiles symmetrised from their lower triangle);
+    "L": the lower-triangular factor; "Lt": its transpose.  P may sit in host memory (it is
+    then streamed to the device in chunks of 256 MB)."""
+    import torch
+    nt = -(-n // b)
+    ti, tj = _tile_order(nt)
+    X = torch.zeros(nt * b, dtype=torch.float64, device=dev)
+    X[:n] = x
+    X = X.view(nt, b)
+    Y = torch.zeros(nt, b, dtype=torch.float64, device=dev)
+    T = P.view(-1, b, b)                       # T[t] = tile (i, j) transposed
+    chunk = max(1, (1 << 28) // (b * b * 8))
+    for s0 in range(0, len(ti), chunk):
+        ii = torch.from_numpy(ti[s0:s0 + chunk]).to(dev)
+        jj = torch.from_numpy(tj[s0:s0 + chunk]).to(dev)
+        Tt = T[s0:s0 + chunk].to(dev, non_blocking=True)
+        diag = ii == jj
+        if bool(diag.any()):
+            Tt = Tt.clone()
+            low = torch.triu(Tt[diag])         # the tile's lower triangle, transposed
+            Tt[diag] = low + torch.triu(low, 1).transpose(1, 2) if kind == "sym" else low
+        if kind in ("sym", "L"):
+            Y.index_add_(0, ii, torch.bmm(X[jj].unsqueeze(1), Tt).squeeze(1))
+        if kind == "sym":
+            o = ~diag
+            if bool(o.any()):
+                Y.index_add_(0, jj[o], torch.bmm(Tt[o], X[ii[o]].unsqueeze(2)).squeeze(2))
+        elif kind == "Lt":
+            Y.index_add_(0, jj, torch.bmm(Tt, X[ii].unsqueeze(2)).squeeze(2))
+    return Y.reshape(-1)[:n]
+
+
+def factor_probe_berr(A, L, n, b, dev, nprobe=3, seed=5):
+    """Random-probe backward error of a factor: max over Gaussian x of
+    ||(A - L L^T) x|| / ||A x||, which estimates ||A - L L^T||_F / ||A||_F."""
+    import torch
+    g = torch.Generator(device=dev).manual_seed(seed)
+    worst = 0.0
+    for _ in range(nprobe):
+        x = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+        Ax = tiles_matvec(A, n, b, x, dev, "sym")
+        LLx = tiles_matvec(L, n, b, tiles_matvec(L, n, b, x, dev, "Lt"), dev, "L")
+        worst = max(worst, float((Ax - LLx).norm() / Ax.norm()))
+    return worst
+
+
+# Output precision -> (kernel, dtype its tensor work runs in, nominal ratio of that dtype's
+# dense peak to BF16's).  FP64 and FP32 output tiles are updated on E4M3 digit planes.
+KERNELS = {0: ("k_zgemm<14> (FP64 outputs, E4M3 digit planes)", "e4m3", 2.0),
+           1: ("k_zgemm<10> (FP32 outputs, E4M3 digit planes)", "e4m3", 2.0),
+           2: ("k_qgemm<2> (FP16 outputs)", "fp16", 1.0),
+           3: ("k_qgemm<3> (FP8 E4M3 outputs)", "e4m3", 2.0)}
+
+
+def probed_peaks() -> dict:
+    """Dense GEMM peaks measured on this machine's GB300 by ``bench.py --peaks`` (the committed
+    summary profiles/peaks_gb300.md carries them as a JSON line), or {} if absent."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "peaks_gb300.md")).read()
+        m = re.search(r"^peaks_json:\s*(\{.*\})\s*$", text, flags=re.M)
+        return json.loads(m.group(1)) if m else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def tensor_rooflines(st, t_step, fp32_updates):
+    """Per-precision tensor-core rooflines of the updates: executed tensor flops
+    (tc_stats.tensor_flops) over the CUDA-event time of that precision's update launches,
+    against the dtype's dense peak = measured BF16 (sustained: the kernels run inside a
+    seconds-long step) x the nominal ratio (FP8 2, FP16 1, TF32 1/2)."""
+    pk, pk_kind = peaks()
+    bf16 = pk.get("bf16_tflops_sustained") or pk["bf16_tflops"]
+    out = []
+    for p in range(4):
+        ms = st.t_update_ms[p]
+        if ms <= 0 or st.tensor_flops[p] <= 0:
+            continue
+        name, dt, ratio = KERNELS[p]
+        if p == 1 and fp32_updates:
+            name, dt, ratio = "k_qgemm<1> (FP32 outputs, TF32 x 3)", "tf32", 0.5
+        executed = st.tensor_flops[p] / (ms / 1e3) / 1e12
+        peak = bf16 * ratio
+        probe = probed_peaks().get(f"{dt}_sustained")
+        out.append({"precision": ["fp64", "fp32", "fp16", "fp8"][p], "kernel": name, "bound": "tensor",
+                    "achieved": executed, "peak": peak, "unit": "TFLOP/s", "frac": executed / peak,
+                    "peak_source": f"{pk_kind} bf16 sustained x nominal {dt}/bf16 ratio {ratio:g}",
+                    "peak_probe": probe, "frac_of_probe": (executed / probe) if probe else None,
+                    "algorithmic_tflops": st.update_flops[p] / (ms / 1e3) / 1e12,
+                    "executed_per_algorithmic": st.tensor_flops[p] / st.update_flops[p],
+                    "t_ms": ms, "share_of_step": (ms / 1e3) / t_step if t_step > 0 else None,
+                    "launches": st.update_launches[p]})
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
@@ -189,8 +286,9 @@ def run_ours(args, ws, rank, local):
             raise RuntimeError(f"factorization failed at column {info}")
         tc.tile_chol_solve(H.h, 1, y, n, x, n, 2, 1e-13, ss)
         if w.mixed:
-            # the mixed-precision log-likelihood through the refined solve: the plain quadratic
-            # form of an MxP factor carries its eps_high error times kappa-driven amplification
+            # Eq. 1 with the quadratic form from a refined solve: refinement in FP64 wins back
+            # the accuracy of the mixed-precision factor (its plain quadratic form is reported
+            # beside it in the accuracy block)
             ll, _ = tc.tile_chol_loglik_refined(H.h, y, 2, 1e-14)
         else:
             ll = tc.tile_chol_loglik(H.h, y)
@@ -235,37 +333,84 @@ def run_ours(args, ws, rank, local):
     flops = n ** 3 / 3.0
     value = ws * flops * args.steps / t / 1e12
     st, ss, ll = agg
+    t_step = t / args.steps
 
-    # roofline of the dominant kernel (FP64 SYRK/GEMM update on the DFMA pipe): ALU peak
-    # = 152 SMs x 4 FP64 flops per clock x the maximum SM clock
+    # rooflines: per output precision on the tensor cores (the FP64 outputs' k_zgemm is the
+    # dominant kernel), or the FP64 pipe for the DFMA engine
     pk, pk_kind = peaks()
-    fp64_peak = NSM * FP64_FLOPS_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = (upd_flops / (upd_ms / 1e3) / 1e12) if upd_ms > 0 else None
-    sha = kernel_source_sha()
-    traffic = profiled_traffic("dgemm_update_fp64_n65536", sha) if (n == 65536 and not w.mixed) else None
-    if args.fp64_mode >= 1:
-        roofline = zgemm_roofline(upd_flops, upd_ms, t)
+    by_prec = tensor_rooflines(st, t_step, args.fp32_updates) if args.fp64_mode >= 1 else []
+    if args.fp64_mode >= 1 and by_prec:
+        roofline = dict(by_prec[0])
+        roofline["traffic"] = None
+        roofline["traffic_note"] = ("DRAM bytes per launch are not captured at this size; the committed "
+                                    "ncu summary of k_zgemm gives them for its captured case")
     else:
+        fp64_peak = NSM * FP64_FLOPS_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = (upd_flops / (upd_ms / 1e3) / 1e12) if upd_ms > 0 else None
         roofline = {"kernel": "k_dgemm_update", "bound": "alu", "achieved": achieved, "peak": round(fp64_peak, 4),
-                "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": traffic,
-                "peak_source": f"ALU: 152 SMs x 4 FP64 flop/clk x {pk_kind} max SM clock",
-                "update_share_of_step": (upd_ms / 1e3) / t if t > 0 else None}
+                    "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+                    "peak_source": f"ALU: 152 SMs x 4 FP64 flop/clk x {pk_kind} max SM clock",
+                    "share_of_step": (upd_ms / 1e3) / t if t > 0 else None}
+    roofline["kernel_source_sha"] = kernel_source_sha()
 
-    # accuracy of a mixed-precision factorization against the FP64 one (outside the timed region)
+    # accuracy of a mixed-precision factorization, outside the timed region: random-probe
+    # backward error of the factor, Eq. 1 with the plain and the refined quadratic form, Eq. 3
+    # at y = 0, against the same matrix factored with an all-FP64 map (the FP64 path, whose
+    # factorization time is the MxP-vs-FP64 comparison)
     accuracy = None
+    comparisons = {} if (rank == 0 and ws == 1) else None
+    Ah = None
     if w.mixed:
         ld_mxp = tc.tile_chol_logdet(H.h)
-        ll_plain = tc.tile_chol_loglik(H.h, y)         # unrefined, for comparison (untimed)
-        ll_ref_mxp, berr_mxp = tc.tile_chol_loglik_refined(H.h, y, 5, 1e-14)
-        stash = (ld_mxp, ll_plain, ll_ref_mxp, berr_mxp)
+        ll_plain = tc.tile_chol_loglik(H.h, y)
+        ll_ref5, berr_mxp = tc.tile_chol_loglik_refined(H.h, y, 5, 1e-14)
+        # the probe needs L and A at once: A moves to pinned host memory (streamed from there)
+        Ah = torch.empty(A.numel(), dtype=torch.float64, pin_memory=True)
+        Ah.copy_(A)
+        del A
+        A = None
+        torch.cuda.empty_cache()
+        L = torch.empty(T * b * b, dtype=torch.float64, device=dev)
+        tc.tile_chol_get_factor(H.h, L)
+        probe_mxp = factor_probe_berr(Ah, L, n, b, dev)
+        del L
+        torch.cuda.empty_cache()
+        s64 = tc.tc_stats()
+        if tc.tile_chol_factor(H.h, n, b, Ah, None, s64) == 0:
+            ld64 = tc.tile_chol_logdet(H.h)
+            ll64, berr64 = tc.tile_chol_loglik_refined(H.h, y, 5, 1e-14)
+            ll64_plain = tc.tile_chol_loglik(H.h, y)
+            accuracy = {
+                "factor_berr_probe": probe_mxp,
+                "factor_berr_probe_method": "max over 3 Gaussian x of ||(A - L L^T) x|| / ||A x|| (torch FP64 "
+                                            "products with the packed tiles of A and of the factor)",
+                "accuracy_level_eps_high": w.eps_high,
+                "loglik_fp64": ll64, "loglik_mxp": ll, "loglik_rel_err": abs(ll - ll64) / abs(ll64),
+                "loglik_mxp_unrefined": ll_plain,
+                "loglik_unrefined_rel_err": abs(ll_plain - ll64) / abs(ll64),
+                "loglik_fp64_unrefined": ll64_plain,
+                "loglik_mxp_refined_5": ll_ref5, "loglik_refined_5_rel_err": abs(ll_ref5 - ll64) / abs(ll64),
+                "logdet_fp64": ld64, "logdet_mxp": ld_mxp, "logdet_rel_err": abs(ld_mxp - ld64) / abs(ld64),
+                "kl_divergence": 0.5 * (ld_mxp - ld64),
+                "solve_berr_mxp_refined": berr_mxp, "solve_berr_fp64_refined": berr64,
+                "reported_loglik": "Eq. 1 with the quadratic form of a refined solve (FP64 iterative "
+                                   "refinement on the MxP factor); the plain form is loglik_mxp_unrefined",
+                "reference": "same matrix, all-FP64 map, same engine (the FP64 path), refined solve"}
+            if comparisons is not None:
+                comparisons["fp64_same_engine"] = {
+                    "value": flops / (s64.t_ms / 1e3) / 1e12, "unit": "TFLOP/s", "t_factor_ms": s64.t_ms,
+                    "mxp_t_factor_ms": st.t_ms, "mxp_factor_speedup": s64.t_ms / st.t_ms,
+                    "what": "this library's FP64 path (all-FP64 map) on the same matrix, one factorization"}
 
     # end to end: the same step through host (pinned) buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        Ah = torch.empty(A.numel(), dtype=torch.float64, pin_memory=True)
-        Ah.copy_(A)
-        del A                          # the end-to-end step reads A from host memory only
-        torch.cuda.empty_cache()
+        if Ah is None:
+            Ah = torch.empty(A.numel(), dtype=torch.float64, pin_memory=True)
+            Ah.copy_(A)
+            del A                      # the end-to-end step reads A from host memory only
+            A = None
+            torch.cuda.empty_cache()
         yh = y.cpu().pin_memory()
         xh = torch.empty_like(yh).pin_memory()
         maph = torch.zeros(nt * nt, dtype=torch.uint8, pin_memory=True) if w.mixed else None
@@ -290,41 +435,18 @@ def run_ours(args, ws, rank, local):
         d2h = n * 8 + 8
         e2e = {"value": ws * flops / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "loglik_matches_device": bool(abs(ll_h - ll) <= 1e-9 * abs(ll))}
+    if A is None:
+        A = Ah                         # the matrix now lives in pinned host memory
 
-    if w.mixed:
-        # FP64 reference: the same matrix factored with every tile in FP64 (emulated updates)
-        src = Ah if not args.no_e2e else A          # the e2e leg moved A to pinned host memory
-        info = tc.tile_chol_factor(H.h, n, b, src, None, None)
-        if info == 0:
-            ld64 = tc.tile_chol_logdet(H.h)
-            ll64, berr64 = tc.tile_chol_loglik_refined(H.h, y, 5, 1e-14)
-            ld_mxp, ll_plain, ll_ref_mxp, berr_mxp = stash
-            accuracy = {"loglik_fp64": ll64, "loglik_mxp": ll, "loglik_rel_err": abs(ll - ll64) / abs(ll64),
-                        "loglik_mxp_unrefined": ll_plain,
-                        "loglik_unrefined_rel_err": abs(ll_plain - ll64) / abs(ll64),
-                        "loglik_mxp_refined_5": ll_ref_mxp,
-                        "loglik_refined_5_rel_err": abs(ll_ref_mxp - ll64) / abs(ll64),
-                        "logdet_fp64": ld64, "logdet_mxp": ld_mxp, "kl_divergence": 0.5 * (ld_mxp - ld64),
-                        "solve_berr_mxp": berr_mxp, "solve_berr_fp64": berr64,
-                        "reference": "same matrix, all-FP64 map, emulated FP64 updates, refined solve"}
-
-    comparisons = None
-    # context numbers for the single-GPU line only: with N > 1 the other GPUs would sit idle
-    if rank == 0 and ws == 1 and not args.no_baselines:
-        comparisons = {}
-        src = Ah if not args.no_e2e else A
-        if w.mixed:
-            # the FP64 path of this library on the same matrix (all-FP64 map, same engine)
-            s64 = tc.tc_stats()
-            if tc.tile_chol_factor(H.h, n, b, src, None, s64) == 0:
-                comparisons["fp64_same_engine"] = {"value": flops / (s64.t_ms / 1e3) / 1e12, "unit": "TFLOP/s",
-                                                   "t_factor_ms": s64.t_ms,
-                                                   "mxp_factor_speedup": s64.t_ms / st.t_ms}
-        else:
-            comparisons.update(fp64_baselines(tc, n, b, src, local, stream))
-
-    if not args.no_e2e:
-        del Ah
+    if comparisons is not None and not w.mixed and not args.no_baselines:
+        comparisons.update(fp64_baselines(tc, n, b, A, local, stream))
+    H.close()
+    del A, Ah
+    torch.cuda.empty_cache()
+    if comparisons is not None and w.mixed and not args.no_baselines:
+        # the FP64 workload (n = 65536, tile 1024): this library's FP64 path, its DFMA engine
+        # and cuSOLVER potrf on the same matrix, measured in the same run
+        comparisons["fp64_n65536"] = fp64_workload_comparisons(tc, local, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -336,10 +458,11 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": ("f64" if args.fp64_mode == 0 else "f64 (updates emulated on e4m3 tensor cores)")
-            if not w.mixed else "f64+f32/tf32+f16+e4m3",
+            if not w.mixed else "f64+f32+f16+e4m3 (f64/f32 updates on e4m3 digit planes)",
             "data": "synthetic", "impl": "ours",
             "config": workload_config(w, n, b, ws),
             "roofline": roofline,
+            "roofline_by_precision": by_prec,
             "accuracy": accuracy,
             "comparisons": comparisons,
             "cpu_baseline": cpu,
@@ -351,13 +474,38 @@ def run_ours(args, ws, rank, local):
                        "berr": ss.berr, "refine_iters": ss.refine_iters, "loglik": ll,
                        "update_tflops_by_prec": [(st.update_flops[p] / st.t_update_ms[p] / 1e9) if st.t_update_ms[p] else None
                                                  for p in range(4)],
-                       "tiles_by_prec": list(st.tiles), "kernel_source_sha": sha,
+                       "tensor_flops_by_prec": list(st.tensor_flops),
+                       "tiles_by_prec": list(st.tiles), "kernel_source_sha": kernel_source_sha(),
                        "step_ms": step_ms, "step_ms_best": min(step_ms), "step_ms_median": float(np.median(step_ms)),
                        "factor_ms_steps": factor_ms,
                        "tflops_factor_only_best": flops / (min(factor_ms) / 1e3) / 1e12},
         }
         print(json.dumps(line), flush=True)
-    H.close()
+
+
+def fp64_workload_comparisons(tc, local, stream):
+    """The FP64 workload (Matern nu = 1/2, range 0.05, n = 65536, tile 1024), outside the timed
+    region: this library's FP64 path (fp64_mode 2, one factorization after one warm-up), then
+    its DFMA engine and cuSOLVER potrf (fp64_baselines)."""
+    import torch
+    w = inputs.WORKLOADS["fp64_n65536"]
+    n, b = w.n, w.tile
+    dev = torch.device("cuda", local)
+    A = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=dev)
+    out = {"workload": w.name, "n": n, "tile": b}
+    with tc.Handle(local, stream=stream.cuda_stream, fp64_mode=2) as H:
+        tc.tc_matern_tiles(H.h, n, b, torch.from_numpy(w.points()).to(dev), w.sigma2, w.range_a, w.nu, w.nugget, A)
+        tc.tile_chol_factor(H.h, n, b, A, None, None)
+        st = tc.tc_stats()
+        if tc.tile_chol_factor(H.h, n, b, A, None, st) == 0:
+            out["fp64_path"] = {"value": n ** 3 / 3.0 / (st.t_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                                "t_factor_ms": st.t_ms,
+                                "what": "this library, fp64_mode 2 (updates and TRSM on E4M3 digit planes)"}
+    torch.cuda.empty_cache()
+    out.update(fp64_baselines(tc, n, b, A, local, stream))
+    del A
+    torch.cuda.empty_cache()
+    return out
 
 
 def workload_config(w, n, b, ws):
@@ -477,12 +625,12 @@ def zgemm_roofline(upd_flops, upd_ms, t):
     is 105 x the algorithmic flops; the roofline is the FP8 dense peak (measured BF16 x the
     nominal FP8/BF16 ratio 2), reported both as executed and as algorithmic FP64 flops."""
     pk, pk_kind = peaks()
-    fp8_peak = pk["bf16_tflops"] * 2.0
+    fp8_peak = (pk.get("bf16_tflops_sustained") or pk["bf16_tflops"]) * 2.0
     alg = (upd_flops / (upd_ms / 1e3) / 1e12) if upd_ms > 0 else None
     executed = alg * 105 if alg else None
     return {"kernel": "k_zgemm", "bound": "tensor", "achieved": executed, "peak": fp8_peak, "unit": "TFLOP/s",
             "frac": (executed / fp8_peak) if executed else None, "traffic": None,
-            "peak_source": f"{pk_kind} bf16 x nominal fp8/bf16 ratio 2",
+            "peak_source": f"{pk_kind} bf16 sustained x nominal fp8/bf16 ratio 2",
             "algorithmic_fp64_tflops": alg, "pairs_per_fp64_product": 105,
             "update_share_of_step": (upd_ms / 1e3) / t if t > 0 else None}
 
@@ -502,7 +650,8 @@ def run_batched(args, ws, rank, local):
     """Many uneven SPD Matern matrices (n log-uniform in [64, 4096], range U[0.02, 0.2], nu in
     {1/2, 3/2, 5/2}, nugget 1e-4): per-matrix precision maps (FP64 diagonal, FP16/FP8 off-diagonal
     where the criterion at eps_high = 1e-7 allows, FP64 elsewhere), one graph-replayed batched
-    factorization, 16-RHS solves refined to backward error <= 1e-13, log-likelihoods."""
+    factorization, 16-RHS solves refined to backward error <= 1e-13, log-likelihoods.  The tile
+    size and the FP64 update engine come from the autotuner (timed on this batch)."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -513,7 +662,7 @@ def run_batched(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    H = tc.Handle(local, stream=stream.cuda_stream, fp64_mode=args.fp64_mode, fp32_updates=args.fp32_updates)
+    Hgen = tc.Handle(local, stream=stream.cuda_stream)
     bw = inputs.batched_workload(args.count, 5 + 1000 * rank)
     ns = bw.ns
     pts = [torch.from_numpy(bw.points(i)).to(dev) for i in range(len(ns))]
@@ -529,7 +678,7 @@ def run_batched(args, ws, rank, local):
         maps = list(torch.split(flat, sizes))
         for i, n in enumerate(ns):
             A = torch.empty(tc.tile_count(n, b) * b * b, dtype=torch.float64, device=dev)
-            tc.tc_matern_tiles(H.h, n, b, pts[i], 1.0, bw.ranges[i], bw.nus[i], 1e-4, A)
+            tc.tc_matern_tiles(Hgen.h, n, b, pts[i], 1.0, bw.ranges[i], bw.nus[i], 1e-4, A)
             A_list.append(A)
         return A_list, maps
 
@@ -539,26 +688,37 @@ def run_batched(args, ws, rank, local):
         flat = map_store[b]
         flat[flat == tc.TC_FP32] = tc.TC_FP64
 
-    best_b, tune = autotune.pick_batched_tile(H, ns, make_inputs)
-    b = best_b
+    def make_handle(mode):
+        return tc.Handle(local, stream=stream.cuda_stream, fp64_mode=mode, fp32_updates=args.fp32_updates)
+
+    (b, mode), tune = autotune.pick_batched_config(make_handle, ns, make_inputs)
+    H = make_handle(mode)
     A_list, maps = make_inputs(b)
-    B = [torch.from_numpy(np.ascontiguousarray(inputs.gaussian(n, nrhs, 77 + i).T)).to(dev) for i, n in enumerate(ns)]
+    Bh = [inputs.gaussian(n, nrhs, 77 + i) for i, n in enumerate(ns)]
+    B = [torch.from_numpy(np.ascontiguousarray(x.T)).to(dev) for x in Bh]
     X = [torch.empty_like(x) for x in B]
     Y = [x[0].contiguous() for x in B]
     flops = sum(n ** 3 / 3.0 for n in ns)
 
-    def step():
+    def step(A_in, maps_in, B_in, X_in, Y_in, make_maps=True):
         st, ss = tc.tc_stats(), tc.tc_stats()
-        compute_maps(A_list, maps, b)
-        rc, info, ld = tc.tile_chol_factor_batched(H.h, ns, b, A_list, maps, st)
+        if make_maps:
+            compute_maps(A_in, maps_in, b)
+        rc, info, ld = tc.tile_chol_factor_batched(H.h, ns, b, A_in, maps_in, st)
         if rc:
             raise RuntimeError(f"batched factorization failed: {rc}")
-        berr = tc.tile_chol_solve_batched(H.h, nrhs, B, X, 10, 1e-13, ss)
-        ll = tc.tile_chol_loglik_batched(H.h, Y)
+        berr = tc.tile_chol_solve_batched(H.h, nrhs, B_in, X_in, 10, 1e-13, ss)
+        ll = tc.tile_chol_loglik_batched(H.h, Y_in)
         return st, ss, berr, ll
 
+    # kernels of one factorization: counted while the graph is captured (replays count none)
+    st0 = tc.tc_stats()
+    compute_maps(A_list, maps, b)
+    tc.tile_chol_factor_batched(H.h, ns, b, A_list, maps, st0)
+    factor_kernels = st0.kernel_launches
+    tensor_flops = sum(st0.tensor_flops)
     for _ in range(args.warmup):
-        step()
+        step(A_list, maps, B, X, Y)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -566,30 +726,109 @@ def run_batched(args, ws, rank, local):
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    launches = 0
+    t_factor = 0.0
     for _ in range(args.steps):
-        st, ss, berr, ll = step()
+        st, ss, berr, ll = step(A_list, maps, B, X, Y)
+        launches += factor_kernels + 2 * len(ns) + ss.kernel_launches     # maps + factor + solves
+        t_factor += st.t_ms
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
     value = ws * flops * args.steps / t / 1e12
     nlow = sum(int((m > 1).sum().item()) for m in maps)
+
+    # roofline: the whole graph-replayed factorization against the E4M3 dense peak -- its tensor
+    # work (digit planes of the FP64 tiles, FP16 / FP8 tiles) over its wall time; the launches
+    # of hundreds of small matrices, not the tensor pipe, bound it
+    pk, pk_kind = peaks()
+    bf16 = pk.get("bf16_tflops_sustained") or pk["bf16_tflops"]
+    t_f = t_factor / args.steps / 1e3
+    roofline = None
+    if tensor_flops > 0 and t_f > 0:
+        ach = tensor_flops / t_f / 1e12
+        roofline = {"kernel": "batched factorization (graph of grouped k_zgemm / k_qgemm / POTRF / TRSM launches)",
+                    "bound": "tensor", "achieved": ach, "peak": bf16 * 2.0, "unit": "TFLOP/s",
+                    "frac": ach / (bf16 * 2.0), "traffic": None,
+                    "peak_source": f"{pk_kind} bf16 sustained x nominal e4m3/bf16 ratio 2",
+                    "algorithmic_tflops": flops / t_f / 1e12, "t_factor_ms": t_f * 1e3,
+                    "kernels_per_factorization": factor_kernels,
+                    "us_per_kernel": t_f * 1e6 / max(1, factor_kernels)}
+    elif t_f > 0:
+        fp64_peak = NSM * FP64_FLOPS_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flops / t_f / 1e12
+        roofline = {"kernel": "batched factorization (FP64 pipe)", "bound": "alu", "achieved": ach,
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                    "peak_source": f"ALU: 152 SMs x 4 FP64 flop/clk x {pk_kind} max SM clock",
+                    "kernels_per_factorization": factor_kernels}
+
+    # end to end: the same step from pinned host buffers (the library stages the matrices and
+    # right-hand sides; solutions and log-likelihoods come back to host memory)
+    e2e = None
+    if not args.no_e2e:
+        Ah = [a.cpu().pin_memory() for a in A_list]
+        mh = [m.cpu().pin_memory() for m in maps]
+        Bp = [x.cpu().pin_memory() for x in B]
+        Xp = [torch.empty_like(x).pin_memory() for x in Bp]
+        Yp = [x.cpu().pin_memory() for x in Y]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(Ah, mh, Bp, Xp, Yp, make_maps=False)     # host maps: the ones computed on the device
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
+        te = max_over_ranks(te, ws, dev)
+        h2d = sum(a.numel() * 8 for a in Ah) + sum(m.numel() for m in mh) + sum(x.numel() * 8 for x in Bp) + \
+            sum(y.numel() * 8 for y in Yp)
+        d2h = sum(x.numel() * 8 for x in Xp) + 8 * len(ns)
+        e2e = {"value": ws * flops / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "note": "precision maps are inputs here (host copies of the device-computed ones)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = batched_cpu_sample(bw, 1)
     if rank == 0:
         line = common_line(ws, args, value, t, {
             "workload": "batched", "count": len(ns), "n_range": [min(ns), max(ns)], "tile": b,
-            "tile_autotune_s": {str(k): v for k, v in tune.items()}, "nugget": 1e-4, "eps_high": eps,
-            "precision": "FP64 diagonal, FP16/FP8 off-diagonal where allowed, else FP64",
+            "fp64_engine": {0: "FP64 pipe (DFMA, 64 x 64 blocks)", 2: "E4M3 digit planes (128 x 16 items)"}[mode],
+            "autotune_s": {f"b={k[0]},fp64_mode={k[1]}": v for k, v in tune.items()}, "nugget": 1e-4,
+            "eps_high": eps, "precision": "FP64 diagonal, FP16/FP8 off-diagonal where allowed, else FP64",
             "nrhs": nrhs, "l2": "total inputs larger than L2", "parallelism": f"replicas x{ws}",
             "step": "maps+graph-replayed batched factor+16-RHS refined solves+logliks"}, "f64+f16+e4m3")
-        line["roofline"] = None
-        line["e2e"] = None
-        line["cpu_baseline"] = None
+        line["roofline"] = roofline
+        line["e2e"] = e2e
+        line["cpu_baseline"] = cpu
         line["clocks"] = clk
-        line["gpu_launches"] = None
+        line["gpu_launches"] = launches
         line["detail"] = {"max_berr": max(berr), "refine_iters": ss.refine_iters, "low_precision_tiles": nlow,
                           "t_factor_ms": st.t_ms, "t_solve_ms": ss.t_ms, "flops": flops}
         print(json.dumps(line), flush=True)
     H.close()
+    Hgen.close()
+
+
+def batched_cpu_sample(bw, reps):
+    """The oracle (plain FP64 Cholesky) on the first matrices of the batch, up to 2e10 flops."""
+    import oracle
+    idx, fl = [], 0.0
+    for i, n in enumerate(bw.ns):
+        if fl > 2e10:
+            break
+        idx.append(i)
+        fl += n ** 3 / 3.0
+    mats = [oracle.matern(bw.points(i), 1.0, bw.ranges[i], bw.nus[i], 1e-4) for i in idx]
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for A in mats:
+            oracle.cholesky(A)
+    t = time.perf_counter() - t0
+    return {"value": fl * reps / t / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"first {len(idx)} matrices of the batch ({fl:.2e} flops), one oracle factorization each",
+            "seconds": t}
 
 
 def run_reference_batched(args, ws):
@@ -826,9 +1065,72 @@ def run_sweep(args, local):
     print(json.dumps(out), flush=True)
 
 
+def run_peaks(local):
+    """Dense GEMM peaks of this GPU through cuBLAS (torch.matmul, torch._scaled_mm for E4M3),
+    8192^3 (2 N^3 flops): best of 10 launches (burst) and back to back for 4 s (sustained),
+    CUDA events on the launching stream; pinned 1 GiB host<->device copies.  The rooflines
+    of the update kernels compare against these and against the driver's BF16 measurement."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = 8192
+    out = {"metric": "dense GEMM peaks (TFLOP/s) and pinned host-link rates (GB/s)", "n": N,
+           "gpu": torch.cuda.get_device_name(dev), "torch": torch.__version__}
+    torch.backends.cuda.matmul.allow_tf32 = True
+
+    def timed(fn, flops):
+        fn()
+        torch.cuda.synchronize()
+        best = 0.0
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps, t0 = 0, time.perf_counter()
+        e0.record()
+        while time.perf_counter() - t0 < 4.0:
+            for _ in range(8):
+                fn()
+            reps += 8
+            torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        return {"burst": best, "sustained": flops * reps / (e0.elapsed_time(e1) / 1e3) / 1e12}
+
+    flops = 2.0 * N ** 3
+    clk = ClockSampler(local)
+    clk.start()
+    for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16), ("tf32", torch.float32),
+                     ("fp64", torch.float64)):
+        a = torch.randn(N, N, device=dev, dtype=torch.float32).to(dt)
+        bm = torch.randn(N, N, device=dev, dtype=torch.float32).to(dt)
+        out[name] = timed(lambda: torch.matmul(a, bm), flops)
+        del a, bm
+        torch.cuda.empty_cache()
+    try:
+        a8 = torch.randn(N, N, device=dev).to(torch.float8_e4m3fn)
+        b8 = torch.randn(N, N, device=dev).to(torch.float8_e4m3fn)
+        one = torch.ones((), device=dev, dtype=torch.float32)
+        out["e4m3"] = timed(lambda: torch._scaled_mm(a8, b8.t(), scale_a=one, scale_b=one,
+                                                     out_dtype=torch.bfloat16), flops)
+        del a8, b8
+    except (RuntimeError, TypeError, AttributeError) as exc:       # pragma: no cover - torch API
+        out["e4m3"] = {"error": str(exc)[:200]}
+    out["clocks"] = clk.stop()
+    out["link_gbs"] = measure_link(dev)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     ws, rank, local = dist_info()
+    if args.peaks:
+        run_peaks(local)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return

@@ -109,7 +109,20 @@ typedef struct {
                                    1: 3 x TF32 tensor-core products with FP32 accumulation
                                    (as with fp64_mode 0: FP32-level arithmetic, the
                                    paper's FP32 tiles).  Other values: TC_ERR_ARG. */
-    int reserved[5];
+    int wait_limit_us;          /* bound, in microseconds, of every wait inside the
+                                   tensor-core update kernels (a pipeline stage that does not
+                                   arrive in time); 0 (default): 4 s.  When a wait runs out the
+                                   kernel stops issuing, lets its own copies and MMAs finish,
+                                   releases its tensor memory and returns; the call then
+                                   returns TC_ERR_TIMEOUT and the handle stays usable.
+                                   Negative: TC_ERR_ARG. */
+    int wait_test;              /* failure-detection test hook, 0 for normal use.  Non-zero: the
+                                   MMA issuer of every tensor-core update kernel first waits
+                                   on a barrier that no thread arrives at, so each launch runs
+                                   into its wait bound (pair it with a short wait_limit_us) and
+                                   the call returns TC_ERR_TIMEOUT.  Nothing faults or hangs:
+                                   the kernels take their normal teardown. */
+    int reserved[3];
 } tc_config;
 
 /* Per-call statistics (any field a call does not produce is left 0). */
@@ -132,13 +145,18 @@ typedef struct {
     double t_update_ms[4];
     double t_potrf_ms, t_trsm_ms, t_convert_ms;
     int64_t update_launches[4];
+    /* tensor-core work the updates of each output precision executed (in-core factor): on
+       digit planes (FP64 / FP32 outputs), 2 x rows x cols x K per plane pair multiplied, the
+       planes that a stored tile cannot have non-zero skipped; TF32 x 3: three passes; FP16 /
+       FP8: equal to update_flops.  0 for the FP64 pipe (fp64_mode 0). */
+    double tensor_flops[4];
 } tc_stats;
 
 /* Defaults: device 0, own stream, cap 0 (auto), prefetch 2, lookahead 1. */
 void tc_config_default(tc_config *cfg);
 
 /* Create a handle on cfg->device.  cfg may be NULL (defaults).  *out is set on TC_OK.
- * TC_ERR_ARG: fp64_mode outside 0..2 or fp32_updates outside 0..1.  (Out of core, FP32
+ * TC_ERR_ARG: fp64_mode outside 0..2, fp32_updates outside 0..1 or wait_limit_us < 0.  (Out of core, FP32
  * output tiles always take the digit-plane path.) */
 int tc_create(tc_handle *out, const tc_config *cfg);
 
@@ -147,6 +165,14 @@ void tc_destroy(tc_handle h);
 
 /* Message of the last failing call of this handle ("" if none).  Owned by the handle. */
 const char *tc_last_error(tc_handle h);
+
+/* Change the handle's cfg.wait_limit_us (bound of each wait in the tensor-core update
+ * kernels, microseconds; 0: the 4 s default) and cfg.wait_test (the failure-detection test
+ * hook, 0 for normal use) for its later calls, so that a caller can shorten the waits for a
+ * watchdog, or test the timeout path, and then restore them on the same handle.  The paper
+ * has no counterpart (it does not discuss failure detection).  TC_ERR_ARG for a NULL handle
+ * or a negative limit. */
+int tc_set_wait_limit(tc_handle h, int wait_limit_us, int wait_test);
 
 /*
  * Synthetic covariance, Eq. 2 (Section III-D): writes the lower tiles of
@@ -297,28 +323,39 @@ int tile_chol_factor_batched(tc_handle h, int count, const int64_t *n, int b, co
 int tile_chol_solve_batched(tc_handle h, int nrhs, const double *const *B, double *const *X, int max_refine,
                             double target_berr, double *berr_out, tc_stats *stats);
 
+/* Copy the factor of matrix `index` of the last batched factorization out, as
+ * tile_chol_get_factor does for a single one (tile layout of its n; upper triangles of
+ * diagonal tiles and padding written as 0).  L_tiles: host or device.  TC_ERR_ARG for an
+ * index outside the batch, TC_ERR_STATE without a successful in-core factorization. */
+int tile_chol_get_factor_batched(tc_handle h, int index, double *L_tiles);
+
 /* Eq. 1 for every matrix of the last batched factorization; y NULL: at y = 0; else y[i]
  * (n_i doubles, host or device).  loglik_out[count]. */
 int tile_chol_loglik_batched(tc_handle h, const double *const *y, double *loglik_out);
 
 /*
  * Precision map without any allocation (the paper has no counterpart: this entry point
- * exists for callers that cannot allocate device memory -- code running while a stream
- * is captured into a CUDA graph, code held to a fixed memory budget or a custom
- * allocator, real-time loops).  Same map as tile_chol_precision_map, for the current CUDA
- * device, without a handle:
- *   A_tiles: device memory, the tile layout above (read only).
- *   map_out: device memory, Nt*Nt bytes, row-major (written, upper part TC_FP64 = 0).
+ * exists for callers that cannot allocate device memory -- code held to a fixed memory
+ * budget or to a custom allocator that owns all device memory, real-time loops that cannot
+ * afford an allocation's latency or failure).  Same map as tile_chol_precision_map, for the
+ * current CUDA device, without a handle:
+ *   A_tiles: device memory of the current device, the tile layout above (read only).
+ *   map_out: device memory of the current device, Nt*Nt bytes, row-major (written, upper
+ *            part TC_FP64 = 0).
  *   stream:  cudaStream_t to run on (NULL: the legacy default stream).  The call only
  *            enqueues work; it does not wait for it.
  * The per-tile sums of squares go to a fixed scratch array inside the library (263 KB,
  * held on every GPU that loads the library until the process exits), so the size is
  * limited to Nt = ceil(n / b) <= 256 tiles per column; larger problems get TC_ERR_ARG.
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a
- * device looks up the scratch array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls on a device share the one scratch
- * array, so calls whose GPU work overlaps (different streams, no ordering) race and must
- * be serialised by the caller.  Returns TC_OK, TC_ERR_ARG or TC_ERR_CUDA.
+ * device (and the first after a device reset) looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls on a
+ * device share the one scratch array, so calls whose GPU work overlaps (different streams,
+ * no ordering) race and must be serialised by the caller.
+ * Returns TC_OK; TC_ERR_ARG for sizes or arguments out of range and for buffers that are
+ * not device memory of the current device; TC_ERR_CUDA when a launch fails, and, without
+ * launching anything or clearing it, when the CUDA runtime already holds an error from
+ * earlier work (cudaPeekAtLastError).
  */
 int tile_chol_precision_map_noalloc(int64_t n, int b, const double *A_tiles, double eps_high, int band,
                                     int prec_set, uint8_t *map_out, void *stream);

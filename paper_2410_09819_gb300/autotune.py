@@ -1,10 +1,11 @@
 """Autotuners for the two shapes that are free at run time.
 
-* In core, batched: the tile size.  The FP64 update works on 64 x 64 register blocks and the
-  tensor-core updates on fixed 128-row blocks whatever the tile, so the tile size sets the number
-  of tasks, the parallelism per column step and the padding of ragged matrices.
-  ``pick_batched_tile`` times ``tile_chol_factor_batched`` (graph replay, after one capture) for
-  each candidate on the caller's batch and returns the fastest.
+* In core, batched: the tile size and the FP64 update engine.  The tile size sets the number
+  of tasks, the parallelism per column step and the padding of ragged matrices; the engine sets
+  the kernel and block shape of the FP64 output tiles (64 x 64 FP64-pipe blocks, or 128 x 16
+  digit-plane items on the E4M3 tensor cores).  ``pick_batched_config`` times
+  ``tile_chol_factor_batched`` (graph replay, after one capture) for each candidate on the
+  caller's batch and returns the fastest.
 * Out of core: the tile size, the scheduling policy and the eviction rule under a device-cache
   cap.  The static schedule makes the copy volume of every candidate computable in advance
   (``ooc_sim`` predicts the library's counters exactly), so ``rank_ooc_candidates`` keeps the
@@ -38,6 +39,30 @@ def pick_batched_tile(H, ns, make_inputs, candidates=(128, 256), repeats=2):
         times[b] = best
         del A_list, maps
         torch.cuda.empty_cache()
+    return min(times, key=times.get), times
+
+
+def pick_batched_config(make_handle, ns, make_inputs, tiles=(128, 256), engines=(0, 2), repeats=2):
+    """Tile size and FP64 update engine of the batched factorization, by timing.
+
+    The engine fixes the kernel, and with it the block shape, of the FP64 output tiles (the
+    diagonal and every tile the map keeps in FP64): fp64_mode 0 runs them on the FP64 pipe in
+    64 x 64 register blocks, fp64_mode 2 on the E4M3 tensor cores in 128 x 16 digit-plane
+    items; FP16 / FP8 tiles always take the 128 x 128 tensor-core blocks.  make_handle(mode)
+    returns a new handle (a context manager) for an engine; make_inputs(b) -> (A_list, maps).
+    Returns ((b, mode), {(b, mode): seconds}); tile sizes the engine cannot run (the
+    digit-plane engine needs multiples of 128) are left out."""
+    times = {}
+    for mode in engines:
+        cands = [b for b in tiles if mode == 0 or b % 128 == 0]
+        if not cands:
+            continue
+        with make_handle(mode) as H:
+            _, t = pick_batched_tile(H, ns, make_inputs, cands, repeats)
+        for b, v in t.items():
+            times[(b, mode)] = v
+    if not times:
+        raise ValueError("no (tile, engine) candidate")
     return min(times, key=times.get), times
 
 

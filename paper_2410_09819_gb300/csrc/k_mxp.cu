@@ -171,7 +171,8 @@ constexpr int QBM = 128, QBN = 128, QKB = 128;          // block rows, cols, K b
 constexpr int QSTAGES = 4;
 constexpr int QA_BYTES = QBM * QKB, QB_BYTES = QBN * QKB, QSTAGE_BYTES = QA_BYTES + QB_BYTES;
 constexpr int QTHREADS = 320;
-constexpr unsigned long long QTIMEOUT_NS = 4000000000ull;  // 4 s per wait, then give up
+constexpr unsigned long long QTIMEOUT_NS = 4000000000ull;  // default bound of a pipeline wait
+constexpr unsigned long long QDRAIN_NS = 2000000000ull;    // bound of the teardown waits
 
 // In-core form: one CTA per QItem; operand n of item `it` is the packed tile it.xoff + n
 // (X) / it.yoff + n (Y), found in the pool through slot[] and scaled by exps[tile].
@@ -181,6 +182,8 @@ struct QArgs {
     const int *exps;      // scale exponents of the copies (FP16/FP8), nullptr for TF32
     int k, b;
     int *err;             // error word: set on a timed-out wait or a missing operand slot
+    unsigned long long limit_ns;   // bound of each pipeline wait
+    int stall;                     // test hook: wait first on a barrier nothing arrives at
     __device__ void tile(QItem &it) const { it = items[blockIdx.x]; }
     __device__ int xslot(const QItem &it, int n) const { return slot[it.xoff + n]; }
     __device__ int yslot(const QItem &it, int n) const { return slot[it.yoff + n]; }
@@ -198,6 +201,8 @@ struct QGroupArgs {
     const int *exps;
     int k, b;
     int *err;
+    unsigned long long limit_ns;
+    int stall;
     __device__ void tile(QItem &it) const {
         const int nbm = b / QBM, per = nbm * (b / QBN);
         const int g = blockIdx.x / per, r = blockIdx.x % per;
@@ -241,15 +246,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false when the phase did not complete within QTIMEOUT_NS or another role
-// of the CTA gave up (abort flag in shared memory).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+// Bounded wait: false when the phase did not complete within limit_ns or another role of
+// the CTA gave up (abort flag in shared memory).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > QTIMEOUT_NS) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
@@ -332,6 +338,8 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
     uint64_t *done = acce + 2;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    volatile int *never = abort_flag + 1;        // nothing sets it: waits that must not be cut short
+    const unsigned long long lim = args.limit_ns;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QItem it;
@@ -354,6 +362,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
         }
         mbar_init(done, 1);
         *abort_flag = 0;
+        *never = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -375,7 +384,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
             int issued = 0;
             for (int s = 0; s < total_steps; ++s) {
                 const int stage = s % QSTAGES, round = s / QSTAGES;
-                if (!mbar_wait(empty + stage, (round & 1) ^ 1, abort_flag)) {
+                if (!mbar_wait(empty + stage, (round & 1) ^ 1, abort_flag, lim)) {
                     *abort_flag = 1;
                     atomicExch(args.err, 1);
                     break;
@@ -400,27 +409,29 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
                 tma_load_2d(sb, mb, x, sy * b + it.bn * QBN, full + stage);
                 ++issued;
             }
-            if (*abort_flag) {
-                // the consumer stopped early: let the copies still in flight land before exit
-                static __shared__ int never;
-                never = 0;
-                for (int s = issued - QSTAGES < 0 ? 0 : issued - QSTAGES; s < issued; ++s)
-                    mbar_wait(full + s % QSTAGES, (s / QSTAGES) & 1, &never);
-            }
+            // Every copy lands before the shared memory goes away, whichever role gave up and
+            // whenever: only the last QSTAGES copies can still be in flight (each earlier one was
+            // consumed before its stage was refilled), and each is the latest phase of its
+            // stage's full barrier.  Without an abort they end as soon as those copies land.
+            for (int s = issued - QSTAGES < 0 ? 0 : issued - QSTAGES; s < issued; ++s)
+                if (!mbar_wait(full + s % QSTAGES, (s / QSTAGES) & 1, never, QDRAIN_NS)) atomicExch(args.err, 3);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = make_idesc<KIND>();
             bool ok = true;
+            // test hook: `done` completes only after the final commit below, so this wait runs
+            // into the bound and takes the abort path
+            if (args.stall && !mbar_wait(done, 0, abort_flag, lim)) ok = false;
             for (int n = 0; n < nsrc && ok; ++n) {
                 const int a = n & 1, use = n >> 1;
-                if (!mbar_wait(acce + a, (use & 1) ^ 1, abort_flag)) { ok = false; break; }
+                if (!mbar_wait(acce + a, (use & 1) ^ 1, abort_flag, lim)) { ok = false; break; }
                 tc_fence_after();
                 for (int j = 0; j < steps_per_src; ++j) {
                     const int s = n * steps_per_src + j;
                     const int stage = s % QSTAGES, round = s / QSTAGES;
-                    if (!mbar_wait(full + stage, round & 1, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait(full + stage, round & 1, abort_flag, lim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + stage * QSTAGE_BYTES);
                     const uint32_t sb = sa + QA_BYTES;
@@ -437,9 +448,10 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
                 *abort_flag = 1;
                 atomicExch(args.err, 1);
             }
-            // all issued MMAs complete before the TMEM is released
+            // all issued MMAs complete before the TMEM is released: this wait is not cut short
+            // by the abort flag (the MMAs depend on nothing outside the CTA, so it ends)
             mma_commit(done);
-            mbar_wait(done, 0, abort_flag);
+            if (!mbar_wait(done, 0, never, QDRAIN_NS)) atomicExch(args.err, 3);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -461,7 +473,7 @@ k_qgemm(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUten
         bool ok = true;
         for (int n = 0; n < nsrc; ++n) {
             const int a = n & 1, use = n >> 1;
-            if (!mbar_wait(accf + a, use & 1, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(accf + a, use & 1, abort_flag, lim)) { ok = false; break; }
             tc_fence_after();
             float sc = 1.f;
             if (KIND != 1) sc = ldexpf(1.f, args.xexp(it, n) + args.yexp(it, n) - eref);
@@ -547,9 +559,9 @@ static void launch_q(const CUtensorMap &a0, const CUtensorMap &a1, const CUtenso
 
 void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                   const CUtensorMap &b1, const QItem *items, int nitems, const int *slot, const int *exps,
-                  int k, int b, int *err, cudaStream_t s) {
+                  int k, int b, int *err, cudaStream_t s, unsigned long long limit_ns, int stall) {
     if (nitems <= 0) return;
-    QArgs args{items, slot, exps, k, b, err};
+    QArgs args{items, slot, exps, k, b, err, limit_ns ? limit_ns : QTIMEOUT_NS, stall};
     if (kind == 1) launch_q<1>(a0, a1, b0, b1, args, nitems, s);
     else if (kind == 2) launch_q<2>(a0, a1, b0, b1, args, nitems, s);
     else launch_q<3>(a0, a1, b0, b1, args, nitems, s);
@@ -558,7 +570,7 @@ void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const 
 // FP16 (kind 2) or FP8 (kind 3) updates of up to QG_MAX out-of-core tiles; the operand
 // copies sit in the cache-slot pool mapped by `mx` / `my` (slot s at rows s*b .. s*b+b-1).
 void launch_qgemm_group(int kind, const CUtensorMap &mx, const CUtensorMap &my, const QGroup &g, const int *exps,
-                        int b, int *err, cudaStream_t s) {
+                        int b, int *err, cudaStream_t s, unsigned long long limit_ns, int stall) {
     if (g.ntiles <= 0 || g.k <= 0) return;
     QGroupArgs a;
     memset(&a, 0, sizeof a);
@@ -571,6 +583,8 @@ void launch_qgemm_group(int kind, const CUtensorMap &mx, const CUtensorMap &my, 
     a.k = g.k;
     a.b = b;
     a.err = err;
+    a.limit_ns = limit_ns ? limit_ns : QTIMEOUT_NS;
+    a.stall = stall;
     const int nitems = g.ntiles * (b / QBM) * (b / QBN);
     if (kind == 2) launch_q<2>(mx, mx, my, my, a, nitems, s);
     else launch_q<3>(mx, mx, my, my, a, nitems, s);
@@ -578,7 +592,11 @@ void launch_qgemm_group(int kind, const CUtensorMap &mx, const CUtensorMap &my, 
 
 void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, double *amax, cudaStream_t s,
                       const double *alt) {
-    if (ntiles > 0) k_tile_amax<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, amax, alt);
+    // one grid row per listed tile, at most 65535 rows per launch
+    for (int t0 = 0; t0 < ntiles; t0 += 65535) {
+        const int nt = ntiles - t0 < 65535 ? ntiles - t0 : 65535;
+        k_tile_amax<<<dim3(64, nt), 256, 0, s>>>(W, b, tiles + t0, amax, alt ? alt + (int64_t)t0 * b * b : nullptr);
+    }
 }
 void launch_store_round(double *W, int b, const int *tiles, int ntiles, const uint8_t *prec, const double *amaxL,
                         double *amaxS, cudaStream_t s) {

@@ -34,7 +34,8 @@ constexpr int ZX_BYTES = ZBM * ZKB;    // 16 KB: one X plane block
 constexpr int ZY_BYTES = ZBN * ZKB;    // 2 KB: one Y plane block
 constexpr int ZYSET = ZS * ZY_BYTES;   // 28 KB: all Y planes of a K block
 constexpr int ZTHREADS = 192;          // producer, MMA, 4 drain warps
-constexpr unsigned long long ZTIMEOUT_NS = 4000000000ull;
+constexpr unsigned long long ZLIMIT_NS = 4000000000ull;   // default bound of a pipeline wait
+constexpr unsigned long long ZDRAIN_NS = 2000000000ull;   // bound of the teardown waits
 
 // ------------------------------------------------------------------- digit planes
 // Digits of one element in integer arithmetic (GB300 runs FP64 at 2 operations per clock per
@@ -126,9 +127,15 @@ struct ZArgs {
     const ZItem *items;
     int nitems;
     const int *exps;
+    const uint8_t *planes;          // leading planes each digit slot can have non-zero (SKIP form)
+    const double *oamax;            // SKIP form: input amax of every output tile, or nullptr
+    int rref, margin;               // SKIP form: pair budget relative to the output's scale
+    unsigned long long *pair_count; // SKIP form: plane pairs multiplied (added at the end)
     int k, b;
     int *err;
     int assign;         // 0: C -= sum X Y^T;  1: C = sum X Y^T
+    unsigned long long limit_ns;    // bound of each pipeline wait
+    int stall;                      // test hook: wait first on a barrier nothing arrives at
     __device__ int count() const { return nitems; }
     __device__ bool tile(int i, ZItem &it) const {
         it = items[i];
@@ -147,10 +154,16 @@ struct ZGroupArgs {
     uint16_t xs[ZG_MAX][ZK_MAX];   // X_n of tile g: digit slot xs[g][n]
     uint16_t ys[ZK_MAX];           // Y_n (shared by the group): digit slot ys[n]
     const int *exps;
+    const uint8_t *planes;
+    const double *oamax;
+    int rref, margin;
+    unsigned long long *pair_count;
     int k, b, ntiles;
     int *err;
     int assign;
     uint32_t lower;                // bit g: tile g is a diagonal tile
+    unsigned long long limit_ns;
+    int stall;
     __device__ int count() const { return ntiles * (b / ZBM) * (b / ZBN); }
     __device__ bool tile(int i, ZItem &it) const {
         const int nbm = b / ZBM, per = nbm * (b / ZBN);
@@ -191,13 +204,16 @@ __device__ __forceinline__ bool z_try(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool z_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+// Bounded wait: false when the phase did not complete within limit_ns or another role of
+// the CTA gave up (abort flag in shared memory).
+__device__ __forceinline__ bool z_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                       unsigned long long limit_ns) {
     if (z_try(bar, parity)) return true;
     const uint64_t t0 = z_timer();
     for (;;) {
         if (z_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (z_timer() - t0 > ZTIMEOUT_NS) return false;
+        if (z_timer() - t0 > limit_ns) return false;
     }
 }
 __device__ __forceinline__ void z_tma(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
@@ -239,6 +255,117 @@ __device__ __forceinline__ void z_ld16(uint32_t taddr, float (&v)[16]) {
 // deliver the short planes' stages back to back.
 template <int SU>
 __device__ __forceinline__ int plane_order(int i) { return (i & 1) ? SU - 1 - (i >> 1) : (i >> 1); }
+__device__ __forceinline__ int plane_order_n(int i, int S) { return (i & 1) ? S - 1 - (i >> 1) : (i >> 1); }
+
+// Plane counts (SKIP form, mixed-precision updates): a source tile stored in FP8 (E4M3 with a
+// power-of-two scale 2^e8) holds multiples of 2^(e8 - 9) below 2^(e8 + 9), so relative to its
+// digit exponent at most 18 bits are set and digit planes 6..14 are zero; FP16 (scale 2^e16)
+// holds multiples of 2^(e16 - 24) below 2^(e16 + 16): planes 11..14 are zero.  planes[slot]
+// gives the leading planes that can be non-zero; the kernel multiplies only those, which
+// changes no bit of the result (the skipped products are exact zeros).
+// Smallest e with amax <= 2^e (0 for amax <= 0): a tile's digit exponent.
+__device__ __forceinline__ int z_digit_exp(double amax) {
+    if (!(amax > 0.0)) return 0;
+    int ex;
+    const double f = frexp(amax, &ex);
+    return (f == 0.5) ? ex - 1 : ex;
+}
+
+// Plane counts of one source (SKIP form): SU_n, the budget of plane pairs s + t < SU_n, and the
+// X / Y planes multiplied.  With out-of-scale truncation (oamax set), a pair whose scale
+// 2^(e_x + e_y) lies d binary orders below the output tile's input scale 2^e_out drops
+// floor((d - 4 margin) / 4) planes from the reference count rref: the terms it drops stay below
+// 16^-margin of what the reference count drops for a pair at the output's own scale, and a pair
+// above the output's scale keeps more planes (up to SU).  SU_n is rounded up to an even count
+// and the plane counts to {5, 10, 14} (clipped to SU_n): the counts the issue code is unrolled
+// for.  Rounding up only adds terms.
+struct ZShape {
+    int sx, sy, su;
+};
+template <int SU, class Args>
+__device__ __forceinline__ ZShape z_shape(const Args &a, int eo, int xt, int yt) {
+    int su = a.rref;
+    if (a.oamax) {
+        const int d = eo - a.exps[xt] - a.exps[yt] - 4 * a.margin;
+        const int j = d >= 0 ? d / 4 : -((3 - d) / 4);        // floor(d / 4)
+        su = a.rref - j;
+    }
+    su = su < 1 ? 1 : (su > SU ? SU : su);
+    su = (su + 1) & ~1;
+    if (su > SU) su = SU;
+    const int px = a.planes[xt], py = a.planes[yt];
+    int sx = px <= 5 ? 5 : (px <= 10 ? 10 : 14), sy = py <= 5 ? 5 : (py <= 10 ? 10 : 14);
+    sx = sx < su ? sx : su;
+    sy = sy < su ? sy : su;
+    return {sx, sy, su};
+}
+__device__ __forceinline__ int z_pairs(const ZShape &z) {
+    int p = 0;
+    for (int s = 0; s < z.sx; ++s) p += z.sy < z.su - s ? z.sy : z.su - s;
+    return p;
+}
+
+// Order of the X planes of one K block (producer and MMA issuer agree on it): interleaved
+// long / short planes, except in the first K block of a source whose Y partners stop short of
+// SU (SY < SU), which runs in ascending order so that every group is started by its own first
+// MMA (see the SKIP note at k_zgemm).
+__device__ __forceinline__ int plane_at(int i, int sx, int sy, int su, int kb) {
+    return (sy < su && kb == 0) ? i : plane_order_n(i, sx);
+}
+
+// The MMAs of one K block for a source with SX X planes and SY Y planes (compile-time, fully
+// unrolled: the single issuing thread must keep the tensor pipe fed).  Pairs (s, t) with
+// s < SX, t < SY, s + t < SU; plane s multiplies its partners t = 0 .. min(SY, SU - s) - 1 in
+// one MMA whose column block t lands on accumulator group s + t.  Returns false if a stage did
+// not arrive within the wait bound.
+template <int SU, int SX, int SY>
+__device__ __forceinline__ bool z_issue_kblock(int kb, uint64_t xdesc_base, uint64_t yd, uint32_t dbase,
+                                               uint64_t *xfull, uint64_t *xempty, int &xst, int &xph,
+                                               volatile int *abort_flag, unsigned long long lim) {
+    constexpr uint32_t idesc0 = (1u << 4) | ((uint32_t)(ZBM >> 4) << 24);
+    const bool asc = SY < SU && kb == 0;
+#pragma unroll
+    for (int i0 = 0; i0 < SX; i0 += ZPG) {
+        const int cnt = (SX - i0) < ZPG ? (SX - i0) : ZPG;
+        int st = xst, ph = xph;
+        bool ready = true;
+#pragma unroll
+        for (int h = 0; h < ZPG; ++h)
+            if (h < cnt) {
+                ready = ready && z_wait(xfull + st, ph, abort_flag, lim);
+                if (++st == ZXS) { st = 0; ph ^= 1; }
+            }
+        if (!ready) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int h = 0; h < ZPG; ++h)
+            if (h < cnt) {
+                const int i = i0 + h;
+                const int s = asc ? i : ((i & 1) ? SX - 1 - (i >> 1) : (i >> 1));
+                const int np = SY < SU - s ? SY : SU - s;
+                const uint64_t xd = xdesc_base + (uint64_t)((xst * ZX_BYTES) >> 4);
+                const uint32_t idesc = idesc0 | ((uint32_t)((np * ZBN) >> 3) << 17);
+                const uint32_t d = dbase + (uint32_t)(s * ZBN);
+                if (kb > 0) {
+                    z_mma(d, xd, yd, idesc, 1u);
+                } else if (s == 0) {
+                    z_mma(d, xd, yd, idesc, 0u);                    // starts groups 0 .. np-1
+                } else if (asc && np == SY) {
+                    // groups s .. s+np-2 are running; group s+np-1 starts here
+                    if (np > 1) z_mma(d, xd, yd, idesc0 | ((uint32_t)(((np - 1) * ZBN) >> 3) << 17), 1u);
+                    z_mma(d + (uint32_t)((np - 1) * ZBN), xd, yd + (uint64_t)(((np - 1) * ZY_BYTES) >> 4),
+                          idesc0 | ((uint32_t)(ZBN >> 3) << 17), 0u);
+                } else {
+                    z_mma(d, xd, yd, idesc, 1u);                    // all its groups are running
+                }
+#pragma unroll
+                for (int kk = 1; kk < ZKB / 32; ++kk) z_mma(d, xd + 2 * kk, yd + 2 * kk, idesc, 1u);
+                z_commit(xempty + xst);
+                if (++xst == ZXS) { xst = 0; xph ^= 1; }
+            }
+    }
+    return true;
+}
 
 // Persistent update kernel: C -= sum_{n<k} X_n Y_n^T for 128 x ZBN output blocks, X_n the
 // tiles (m, n) and Y_n the tiles (k, n), through their first SU digit planes (SU = 14 for
@@ -257,7 +384,20 @@ __device__ __forceinline__ int plane_order(int i) { return (i & 1) ? SU - 1 - (i
 // The accumulators are double-buffered in TMEM (2 x SU x ZBN <= 512 columns), so the drain
 // of source q overlaps the MMAs of source q + 1, and the item stream never stops between
 // items (no per-item prologue).
-template <int SU, class Args>
+//
+// SKIP (mixed-precision updates): a source multiplies only the SX X planes and SY Y planes its
+// stored formats can have non-zero (pairs s < SX, t < SY, s + t < SU).  Plane 0 then starts
+// groups 0 .. SY-1 only, so in the first K block the planes run in ascending order and plane
+// s >= 1 starts the one group it reaches first (s + SY - 1) with a separate MMA for K step 0;
+// every group the source writes is thus initialised by its own first MMA, and the drain reads
+// only those (the others hold an earlier source's sums).
+//
+// Failure handling: every pipeline wait gives up after args.limit_ns (or when another role
+// set the abort flag), and the CTA then sets *err and stops issuing.  Before the TMEM is
+// released and the CTA exits, the MMA issuer waits for all of its issued MMAs and the
+// producer for all of its issued copies; those waits ignore the abort flag (the operations
+// depend on nothing outside the CTA, so they end) and are bounded by ZDRAIN_NS.
+template <int SU, bool SKIP, class Args>
 __global__ void __launch_bounds__(ZTHREADS, 1)
 k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
         const __grid_constant__ Args args) {
@@ -275,6 +415,8 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
     uint64_t *done = acce + 2;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    volatile int *never = abort_flag + 1;             // nothing sets it: waits that must not be cut short
+    const unsigned long long lim = args.limit_ns;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = args.k, b = args.b;
@@ -296,6 +438,7 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
         }
         z_init(done, 1);
         *abort_flag = 0;
+        *never = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -318,19 +461,22 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 ZItem it;
                 if (!args.tile(item, it)) continue;
+                const int eo = (SKIP && args.oamax) ? z_digit_exp(args.oamax[it.ct]) : 0;
                 for (int n = 0; n < k && ok; ++n) {
                     const int xt = args.xsrc(it, n), yt = args.ysrc(it, n);
+                    const ZShape zs = SKIP ? z_shape<SU>(args, eo, xt, yt) : ZShape{SU, SU, SU};
+                    const int sx = zs.sx, sy = zs.sy;
                     for (int kb = 0; kb < kblocks && ok; ++kb) {
-                        if (!z_wait(yempty + yst, yph, abort_flag)) { ok = false; break; }
-                        z_expect(yfull + yst, SU * ZY_BYTES);
-                        for (int t = 0; t < SU; ++t)
+                        if (!z_wait(yempty + yst, yph, abort_flag, lim)) { ok = false; break; }
+                        z_expect(yfull + yst, sy * ZY_BYTES);
+                        for (int t = 0; t < sy; ++t)
                             z_tma(ybuf + yst * ZYSET + t * ZY_BYTES, &mapY, kb * ZKB, (yt * ZS + t) * b + it.bn * ZBN,
                                   yfull + yst);
                         ++issued_y;
                         if (++yst == ZYS) { yst = 0; yph ^= 1; }
-                        for (int i = 0; i < SU; ++i) {
-                            const int s = plane_order<SU>(i);
-                            if (!z_wait(xempty + xst, xph, abort_flag)) { ok = false; break; }
+                        for (int i = 0; i < sx; ++i) {
+                            const int s = SKIP ? plane_at(i, sx, sy, zs.su, kb) : plane_order<SU>(i);
+                            if (!z_wait(xempty + xst, xph, abort_flag, lim)) { ok = false; break; }
                             z_expect(xfull + xst, ZX_BYTES);
                             z_tma(xbuf + xst * ZX_BYTES, &mapX, kb * ZKB, (xt * ZS + s) * b + it.bm * ZBM, xfull + xst);
                             ++issued_x;
@@ -342,14 +488,16 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
             if (!ok) {
                 *abort_flag = 1;
                 atomicExch(args.err, 1);
-                // let the copies still in flight land before the shared memory goes away
-                static __shared__ int never;
-                never = 0;
-                for (int q = issued_x - ZXS < 0 ? 0 : issued_x - ZXS; q < issued_x; ++q)
-                    z_wait(xfull + q % ZXS, (q / ZXS) & 1, &never);
-                for (int q = issued_y - ZYS < 0 ? 0 : issued_y - ZYS; q < issued_y; ++q)
-                    z_wait(yfull + q % ZYS, (q / ZYS) & 1, &never);
             }
+            // Every copy lands before the shared memory goes away, whichever role gave up and
+            // whenever: only the last ZXS (ZYS) copies of a ring can still be in flight (each
+            // earlier one was consumed before its stage was refilled), and each is the latest
+            // phase of its stage's full barrier.  Without an abort they end as soon as those
+            // copies land.
+            for (int q = issued_x - ZXS < 0 ? 0 : issued_x - ZXS; q < issued_x; ++q)
+                if (!z_wait(xfull + q % ZXS, (q / ZXS) & 1, never, ZDRAIN_NS)) atomicExch(args.err, 3);
+            for (int q = issued_y - ZYS < 0 ? 0 : issued_y - ZYS; q < issued_y; ++q)
+                if (!z_wait(yfull + q % ZYS, (q / ZYS) & 1, never, ZDRAIN_NS)) atomicExch(args.err, 3);
         }
     } else if (warp == 1) {
         // --------------------------------------------------------------- MMA issuer
@@ -360,52 +508,100 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
             // 16-byte units); stage indices and phases run as counters (no division)
             const uint64_t xdesc_base = z_desc(z_smem(xbuf)), ydesc_base = z_desc(z_smem(ybuf));
             int xst = 0, xph = 0, yst = 0, yph = 0, q = 0;   // q: sources issued so far (all items)
+            unsigned long long pairs_done = 0;
             bool ok = true;
+            // test hook: `done` completes only after the final commit below, so this wait runs
+            // into the bound and takes the abort path
+            if (args.stall && !z_wait(done, 0, abort_flag, lim)) ok = false;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 ZItem it;
                 if (!args.tile(item, it)) continue;
+                const int eo = (SKIP && args.oamax) ? z_digit_exp(args.oamax[it.ct]) : 0;
                 for (int n = 0; n < k && ok; ++n, ++q) {
                     const int a = q & 1;
-                    if (!z_wait(acce + a, ((q >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    if (!z_wait(acce + a, ((q >> 1) & 1) ^ 1, abort_flag, lim)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t dbase = tmem + (uint32_t)(a * SU * ZBN);
+                    const ZShape zs = SKIP ? z_shape<SU>(args, eo, args.xsrc(it, n), args.ysrc(it, n)) : ZShape{SU, SU, SU};
+                    if (SKIP) pairs_done += (unsigned long long)z_pairs(zs);
                     for (int kb = 0; kb < kblocks && ok; ++kb) {
-                        if (!z_wait(yfull + yst, yph, abort_flag)) { ok = false; break; }
+                        if (!z_wait(yfull + yst, yph, abort_flag, lim)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint64_t yd = ydesc_base + (uint64_t)((yst * ZYSET) >> 4);
-                        // planes in groups of ZPG: one wait-and-fence round per group keeps the
-                        // MMA queue fed across the issue gaps (pairs: +30 %, measured)
+                        if constexpr (!SKIP) {
+                            // planes in groups of ZPG: one wait-and-fence round per group keeps the
+                            // MMA queue fed across the issue gaps (pairs: +30 %, measured)
 #pragma unroll
-                        for (int i0 = 0; i0 < SU; i0 += ZPG) {
-                            const int cnt = (SU - i0) < ZPG ? (SU - i0) : ZPG;
-                            int st = xst, ph = xph;
-                            bool ready = true;
+                            for (int i0 = 0; i0 < SU; i0 += ZPG) {
+                                const int cnt = (SU - i0) < ZPG ? (SU - i0) : ZPG;
+                                int st = xst, ph = xph;
+                                bool ready = true;
 #pragma unroll
-                            for (int h = 0; h < ZPG; ++h)
-                                if (h < cnt) {
-                                    ready = ready && z_wait(xfull + st, ph, abort_flag);
-                                    if (++st == ZXS) { st = 0; ph ^= 1; }
+                                for (int h = 0; h < ZPG; ++h)
+                                    if (h < cnt) {
+                                        ready = ready && z_wait(xfull + st, ph, abort_flag, lim);
+                                        if (++st == ZXS) { st = 0; ph ^= 1; }
+                                    }
+                                if (!ready) {
+                                    ok = false;
+                                    break;
                                 }
-                            if (!ready) {
-                                ok = false;
-                                break;
+                                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                                for (int h = 0; h < ZPG; ++h)
+                                    if (h < cnt) {
+                                        const int s = plane_order<SU>(i0 + h);
+                                        const uint64_t xd = xdesc_base + (uint64_t)((xst * ZX_BYTES) >> 4);
+                                        const uint32_t idesc = idesc0 | ((uint32_t)(((SU - s) * ZBN) >> 3) << 17);
+                                        const uint32_t d = dbase + (uint32_t)(s * ZBN);
+                                        // plane 0 comes first in every K block and covers all groups,
+                                        // so it alone starts the accumulators of a source tile
+                                        z_mma(d, xd, yd, idesc, (kb > 0 || i0 + h > 0) ? 1u : 0u);
+#pragma unroll
+                                        for (int kk = 1; kk < ZKB / 32; ++kk) z_mma(d, xd + 2 * kk, yd + 2 * kk, idesc, 1u);
+                                        z_commit(xempty + xst);
+                                        if (++xst == ZXS) { xst = 0; xph ^= 1; }
+                                    }
                             }
-                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                            for (int h = 0; h < ZPG; ++h)
-                                if (h < cnt) {
-                                    const int s = plane_order<SU>(i0 + h);
-                                    const uint64_t xd = xdesc_base + (uint64_t)((xst * ZX_BYTES) >> 4);
-                                    const uint32_t idesc = idesc0 | ((uint32_t)(((SU - s) * ZBN) >> 3) << 17);
-                                    const uint32_t d = dbase + (uint32_t)(s * ZBN);
-                                    // plane 0 comes first in every K block and covers all groups,
-                                    // so it alone starts the accumulators of a source tile
-                                    z_mma(d, xd, yd, idesc, (kb > 0 || i0 + h > 0) ? 1u : 0u);
-#pragma unroll
-                                    for (int kk = 1; kk < ZKB / 32; ++kk) z_mma(d, xd + 2 * kk, yd + 2 * kk, idesc, 1u);
-                                    z_commit(xempty + xst);
-                                    if (++xst == ZXS) { xst = 0; xph ^= 1; }
-                                }
+                        } else {
+                            // dispatch on the source's plane budget and plane counts (z_shape's values)
+                            bool r = false;
+                            switch (zs.su * 256 + zs.sx * 16 + zs.sy) {
+                            case 3669: r = z_issue_kblock<14, 5, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3674: r = z_issue_kblock<14, 5, 10>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3678: r = z_issue_kblock<14, 5, 14>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3749: r = z_issue_kblock<14, 10, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3754: r = z_issue_kblock<14, 10, 10>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3758: r = z_issue_kblock<14, 10, 14>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3813: r = z_issue_kblock<14, 14, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3818: r = z_issue_kblock<14, 14, 10>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3822: r = z_issue_kblock<14, 14, 14>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3157: r = z_issue_kblock<12, 5, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3162: r = z_issue_kblock<12, 5, 10>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3164: r = z_issue_kblock<12, 5, 12>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3237: r = z_issue_kblock<12, 10, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3242: r = z_issue_kblock<12, 10, 10>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3244: r = z_issue_kblock<12, 10, 12>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3269: r = z_issue_kblock<12, 12, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3274: r = z_issue_kblock<12, 12, 10>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 3276: r = z_issue_kblock<12, 12, 12>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 2645: r = z_issue_kblock<10, 5, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 2650: r = z_issue_kblock<10, 5, 10>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 2725: r = z_issue_kblock<10, 10, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 2730: r = z_issue_kblock<10, 10, 10>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 2133: r = z_issue_kblock<8, 5, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 2136: r = z_issue_kblock<8, 5, 8>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 2181: r = z_issue_kblock<8, 8, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 2184: r = z_issue_kblock<8, 8, 8>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 1621: r = z_issue_kblock<6, 5, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 1622: r = z_issue_kblock<6, 5, 6>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 1637: r = z_issue_kblock<6, 6, 5>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 1638: r = z_issue_kblock<6, 6, 6>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 1092: r = z_issue_kblock<4, 4, 4>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            case 546: r = z_issue_kblock<2, 2, 2>(kb, xdesc_base, yd, dbase, xfull, xempty, xst, xph, abort_flag, lim); break;
+                            default: atomicExch(args.err, 2); break;   // not produced by z_shape
+                            }
+                            if (!r) ok = false;
                         }
                         if (!ok) break;
                         z_commit(yempty + yst);
@@ -418,8 +614,10 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 *abort_flag = 1;
                 atomicExch(args.err, 1);
             }
+            if (SKIP && args.pair_count && pairs_done) atomicAdd(args.pair_count, pairs_done);
+            // every issued MMA completes before the TMEM is released and the CTA exits
             z_commit(done);
-            z_wait(done, 0, abort_flag);
+            if (!z_wait(done, 0, never, ZDRAIN_NS)) atomicExch(args.err, 3);
         }
     } else {
         // --------------------------------------------------------------- drain + epilogue
@@ -429,14 +627,22 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             ZItem it;
             if (!args.tile(item, it)) continue;
+            const int eo = (SKIP && args.oamax) ? z_digit_exp(args.oamax[it.ct]) : 0;
             double run[ZBN];
 #pragma unroll
             for (int j = 0; j < ZBN; ++j) run[j] = 0.0;
             for (int n = 0; n < k; ++n, ++q) {
                 const int a = q & 1;
-                if (!z_wait(accf + a, (q >> 1) & 1, abort_flag)) { ok = false; break; }
+                if (!z_wait(accf + a, (q >> 1) & 1, abort_flag, lim)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int E = args.exps[args.xsrc(it, n)] + args.exps[args.ysrc(it, n)];
+                const int xt = args.xsrc(it, n), yt = args.ysrc(it, n);
+                const int E = args.exps[xt] + args.exps[yt];
+                // groups this source wrote (SKIP: the others hold an earlier source's sums)
+                int G = SU;
+                if constexpr (SKIP) {
+                    const ZShape zs = z_shape<SU>(args, eo, xt, yt);
+                    G = zs.sx + zs.sy - 1 < zs.su ? zs.sx + zs.sy - 1 : zs.su;
+                }
                 // hi holds groups 0 .. min(SU, 7) - 1, lo the rest (weights 16^-(g+2))
                 const double s_hi = ldexp(1.0, E - 4 * ((SU < 7 ? SU : 7) + 1)), s_lo = ldexp(1.0, E - 4 * (SU + 1));
                 const uint32_t lanebase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * SU * ZBN);
@@ -445,7 +651,12 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 for (int j = 0; j < ZBN; ++j) hi[j] = lo[j] = 0;
                 for (int g = 0; g < SU; ++g) {
                     float v[16];
-                    z_ld16(lanebase + (uint32_t)(g * ZBN), v);
+                    if (!SKIP || g < G) {
+                        z_ld16(lanebase + (uint32_t)(g * ZBN), v);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+                    }
                     // group sums are exact integers below 2^24 in magnitude: a 32-bit
                     // conversion (a 64-bit one would run on the FP64 pipe)
                     if (g < 7) {
@@ -596,39 +807,51 @@ void launch_add_tiles(double *W, int b, const int *tiles, int ntiles, const doub
     if (ntiles > 0) k_add_tiles<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, src);
 }
 
+template <int SU, bool SKIP, class Args>
+static void set_zgemm_smem(size_t smem) {
+    cudaFuncSetAttribute(k_zgemm<SU, SKIP, Args>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
-                  int b, int *err, cudaStream_t s, int planes, int assign) {
+                  int b, int *err, cudaStream_t s, int planes, int assign, const ZPlanes *mixed,
+                  unsigned long long limit_ns, int stall) {
     if (nitems <= 0 || k <= 0) return;
     static std::atomic<unsigned long long> attr{0};
     const size_t smem = zgemm_smem_bytes();
     if (attrs_pending(attr)) {
-        cudaFuncSetAttribute(k_zgemm<14, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<10, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<7, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<6, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<4, ZArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set_zgemm_smem<14, false, ZArgs>(smem);
+        set_zgemm_smem<10, false, ZArgs>(smem);
+        set_zgemm_smem<7, false, ZArgs>(smem);
+        set_zgemm_smem<6, false, ZArgs>(smem);
+        set_zgemm_smem<4, false, ZArgs>(smem);
+        set_zgemm_smem<14, true, ZArgs>(smem);
         mark_attrs_set(attr);
     }
-    ZArgs a{items, nitems, exps, k, b, err, assign};
+    const bool skip = mixed && mixed->src_planes_tab && (planes == 14 || planes == 10);
+    ZArgs a{items, nitems, exps, skip ? mixed->src_planes_tab : nullptr, skip ? mixed->out_amax : nullptr,
+            skip ? mixed->rref : planes, skip ? mixed->margin : 0, skip ? mixed->pair_count : nullptr,
+            k, b, err, assign, limit_ns ? limit_ns : ZLIMIT_NS, stall};
     const int grid = nitems < sm_count() ? nitems : sm_count();      // persistent: one CTA per SM
-    if (planes == 10) k_zgemm<10><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
-    else if (planes == 7) k_zgemm<7><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
-    else if (planes == 6) k_zgemm<6><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
-    else if (planes == 4) k_zgemm<4><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
-    else k_zgemm<14><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    // mixed precision: FP64 and FP32 outputs share the 14-group form (rref 14 / 10 planes)
+    if (skip) k_zgemm<14, true><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 10) k_zgemm<10, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 7) k_zgemm<7, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 6) k_zgemm<6, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 4) k_zgemm<4, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else k_zgemm<14, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
 }
 
 void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGroup &g, const int *exps, int b,
-                        int *err, cudaStream_t s, int planes) {
+                        int *err, cudaStream_t s, int planes, unsigned long long limit_ns, int stall) {
     if (g.ntiles <= 0 || g.k <= 0) return;
     static std::atomic<unsigned long long> attr{0};
     const size_t smem = zgemm_smem_bytes();
     if (attrs_pending(attr)) {
-        cudaFuncSetAttribute(k_zgemm<14, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<10, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<7, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<6, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_zgemm<4, ZGroupArgs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        set_zgemm_smem<14, false, ZGroupArgs>(smem);
+        set_zgemm_smem<10, false, ZGroupArgs>(smem);
+        set_zgemm_smem<7, false, ZGroupArgs>(smem);
+        set_zgemm_smem<6, false, ZGroupArgs>(smem);
+        set_zgemm_smem<4, false, ZGroupArgs>(smem);
         mark_attrs_set(attr);
     }
     ZGroupArgs a;
@@ -640,18 +863,24 @@ void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGro
     }
     for (int n = 0; n < g.k; ++n) a.ys[n] = (uint16_t)g.ys[n];
     a.exps = exps;
+    a.planes = nullptr;              // cache slots: every operand form keeps all 14 planes
+    a.oamax = nullptr;
+    a.rref = planes;
+    a.pair_count = nullptr;
     a.k = g.k;
     a.b = b;
     a.ntiles = g.ntiles;
     a.err = err;
     a.assign = g.assign;
+    a.limit_ns = limit_ns ? limit_ns : ZLIMIT_NS;
+    a.stall = stall;
     const int items = g.ntiles * (b / ZBM) * (b / ZBN);
     const int grid = items < sm_count() ? items : sm_count();        // persistent: one CTA per SM
-    if (planes == 10) k_zgemm<10><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
-    else if (planes == 7) k_zgemm<7><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
-    else if (planes == 6) k_zgemm<6><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
-    else if (planes == 4) k_zgemm<4><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
-    else k_zgemm<14><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    if (planes == 10) k_zgemm<10, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 7) k_zgemm<7, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 6) k_zgemm<6, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else if (planes == 4) k_zgemm<4, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
+    else k_zgemm<14, false><<<grid, ZTHREADS, smem, s>>>(mx, my, a);
 }
 
 }  // namespace tc

@@ -59,10 +59,31 @@ struct Plan {
     int64_t Ttot = 0;
     int max_parts = 0, ntmax = 0;
     double update_flops[4] = {0, 0, 0, 0};
+    double tensor_flops[4] = {0, 0, 0, 0};   // executed tensor-core work of the updates
     double trsm_flops = 0, potrf_flops = 0;
 };
 
+// Leading digit planes a final tile (i, j) can have non-zero: its stored format bounds them
+// (E4M3 with a power-of-two scale: 5; FP16 with a scale: 10; FP32, FP64: all 14).
+inline int stored_planes(const MatDesc &M, int i, int j) {
+    if (!M.mixed || i == j) return 14;
+    const int p = M.map[(size_t)i * M.nt + j];
+    return p == TC_FP8 ? 5 : p == TC_FP16 ? 10 : 14;
+}
+// Plane pairs (s, t), s < sx, t < sy, s + t < su, that one emulated product multiplies.
+inline int plane_pairs(int sx, int sy, int su) {
+    sx = std::min(sx, su);
+    sy = std::min(sy, su);
+    int n = 0;
+    for (int s = 0; s < sx; ++s) n += std::min(sy, su - s);
+    return n;
+}
+
 constexpr int kTargetItems = 8 * 2 * NSM;   // >= 8 waves of 2 CTAs per SM before splitting K
+// Mixed-precision digit-plane updates: a source pair 4 (m + j) binary orders below the output
+// tile's scale keeps j planes fewer than the reference count, m = kPlaneMargin; the terms it
+// drops then stay below 16^-m of those a pair at the output's own scale drops.
+constexpr int kPlaneMargin = 2;
 
 // Emit the items of one job: every 64 x 64 output block (lower ones only for a diagonal
 // SYRK), split along K into `splits` ranges when asked (the reduction then subtracts the
@@ -132,8 +153,11 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
                         for (int bn = 0; bn < b / Z_BN; ++bn)
                             for (int bm = 0; bm < b / 128; ++bm)
-                                P.zitems32.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn});
+                                P.zitems32.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn, (int)(M.tile0 + tidx(m, k))});
                         P.update_flops[TC_FP32] += 2.0 * (double)b * b * K;
+                        for (int nn = 0; nn < k; ++nn)
+                            P.tensor_flops[TC_FP32] += 2.0 * (double)b * b * b *
+                                                       plane_pairs(stored_planes(M, m, nn), stored_planes(M, k, nn), 10);
                         continue;
                     }
                     if (!fp64) continue;
@@ -141,11 +165,17 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                         // emulated FP64: 128 x 32 blocks (the diagonal SYRK keeps blocks reaching the lower part)
                         double *Cp = T(M, m, k);
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
+                        int items = 0;
                         for (int bn = 0; bn < b / Z_BN; ++bn)
                             for (int bm = 0; bm < b / 128; ++bm)
-                                if (m != k || bm * 128 + 127 >= bn * Z_BN)
-                                    P.zitems.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn});
+                                if (m != k || bm * 128 + 127 >= bn * Z_BN) {
+                                    P.zitems.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn, (int)(M.tile0 + tidx(m, k))});
+                                    ++items;
+                                }
                         P.update_flops[TC_FP64] += (m == k ? 1.0 : 2.0) * (double)b * b * K;
+                        for (int nn = 0; nn < k; ++nn)
+                            P.tensor_flops[TC_FP64] += 2.0 * 128.0 * Z_BN * b * items *
+                                                       plane_pairs(stored_planes(M, m, nn), stored_planes(M, k, nn), 14);
                         continue;
                     }
                     jobs_here.push_back((int)P.jobs.size());
@@ -401,7 +431,7 @@ int mxp_updates(tc_handle h, const MxpPlan &M, const MxpDev &D, int k, bool span
         const CUtensorMap &a1 = q == 1 ? h->map_lo : a0;
         const int sp = spans ? span_begin(h, CAT_UPD64 + q) : -1;
         launch_qgemm(q, a0, a1, a0, a1, D.qitems + C.q0[q - 1], C.nq[q - 1], D.slot[q - 1],
-                     q == 2 ? D.exps16 : q == 3 ? D.exps8 : nullptr, k, h->b, err, h->s);
+                     q == 2 ? D.exps16 : q == 3 ? D.exps8 : nullptr, k, h->b, err, h->s, wait_limit_ns(h), wait_test(h));
         span_end(h, sp);
         CK_LAUNCH();
         ++h->upd_launches[q];
@@ -442,6 +472,10 @@ struct PlanDev {
     double *zamax2 = nullptr;
     double *zamax3 = nullptr;    // refinement: amax of L_kk, X0 and R (3 x Ttot)
     const int *dtiles = nullptr;
+    const uint8_t *zplanes = nullptr;   // leading non-zero digit planes per tile (mixed maps), else null
+    double *oamax = nullptr;            // mixed: input amax of every tile (plane budgets of the updates)
+    const int *alltiles = nullptr;      // mixed: 0 .. Ttot-1 (the tile list of that amax)
+    unsigned long long *pairs = nullptr;   // mixed: plane pairs multiplied, FP64 / FP32 outputs
     int *zexps = nullptr;
     double *zamax = nullptr;
     MxpDev mx{};
@@ -472,6 +506,7 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
     D.pentries = reinterpret_cast<const PEntry *>(base + op);
     D.lentries = reinterpret_cast<const LEntry *>(base + ol);
     if ((rc = ensure(h, h->partials, (size_t)std::max(1, P.max_parts) * 4096 * sizeof(double)))) return rc;
+    h->pairs_dev = nullptr;
     if (!P.zitems.empty() || !P.zitems32.empty() || !P.zinv.empty() || !P.dtiles.empty()) {
         // digit planes (14 per tile), exponents, amax, the Z items and the digit tile lists
         const int64_t Tt = P.Ttot;
@@ -483,7 +518,9 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
         const size_t ovr = align_up(ovc + P.zinvc.size() * sizeof(ZItem));
         const size_t od = align_up(ovr + P.zref.size() * sizeof(ZItem)), oe = align_up(od + P.dtiles.size() * 4);
         const size_t oa = align_up(oe + Tt * 4), oa2 = align_up(oa + Tt * 8), oa3 = align_up(oa2 + Tt * 8);
-        const size_t zt = align_up(oa3 + (P.inv_refine ? 3 * Tt * 8 : 0));
+        const size_t opl = align_up(oa3 + (P.inv_refine ? 3 * Tt * 8 : 0));
+        const size_t ooa = align_up(opl + Tt), oall = align_up(ooa + Tt * 8), opc = align_up(oall + Tt * 4);
+        const size_t zt = align_up(opc + 2 * sizeof(unsigned long long));
         if ((rc = ensure(h, h->ztab, zt))) return rc;
         std::vector<char> zh(zt, 0);
         if (!P.zitems.empty()) memcpy(zh.data() + oz, P.zitems.data(), P.zitems.size() * sizeof(ZItem));
@@ -492,6 +529,25 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
         if (!P.zinvc.empty()) memcpy(zh.data() + ovc, P.zinvc.data(), P.zinvc.size() * sizeof(ZItem));
         if (!P.zref.empty()) memcpy(zh.data() + ovr, P.zref.data(), P.zref.size() * sizeof(ZItem));
         if (!P.dtiles.empty()) memcpy(zh.data() + od, P.dtiles.data(), P.dtiles.size() * 4);
+        // digit planes a stored tile can have non-zero: E4M3 with its power-of-two scale 2^e holds
+        // multiples of 2^(e-9) below 2^(e+9) (18 bits: planes 1..5), FP16 multiples of 2^(e-24)
+        // below 2^(e+16) (40 bits: planes 1..10); FP32 and FP64 use all 14
+        bool any_mixed = false;
+        for (const MatDesc &Md : h->mats) any_mixed |= Md.mixed;
+        if (any_mixed) {
+            int *all = reinterpret_cast<int *>(zh.data() + oall);
+            for (int64_t t = 0; t < Tt; ++t) all[t] = (int)t;
+            uint8_t *pl = reinterpret_cast<uint8_t *>(zh.data() + opl);
+            memset(pl, 14, Tt);
+            for (const MatDesc &Md : h->mats) {
+                if (!Md.mixed) continue;
+                for (int i = 0; i < Md.nt; ++i)
+                    for (int j = 0; j < i; ++j) {
+                        const int p = Md.map[(size_t)i * Md.nt + j];
+                        pl[Md.tile0 + tidx(i, j)] = (uint8_t)(p == TC_FP8 ? 5 : p == TC_FP16 ? 10 : 14);
+                    }
+            }
+        }
         CK(cudaMemcpy(h->ztab.p, zh.data(), zt, cudaMemcpyHostToDevice));
         char *zb = static_cast<char *>(h->ztab.p);
         D.zitems = reinterpret_cast<const ZItem *>(zb + oz);
@@ -504,6 +560,13 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
         D.dtiles = reinterpret_cast<const int *>(zb + od);
         D.zexps = reinterpret_cast<int *>(zb + oe);
         D.zamax = reinterpret_cast<double *>(zb + oa);
+        D.zplanes = any_mixed ? reinterpret_cast<const uint8_t *>(zb + opl) : nullptr;
+        if (any_mixed) {
+            D.oamax = reinterpret_cast<double *>(zb + ooa);
+            D.alltiles = reinterpret_cast<const int *>(zb + oall);
+            D.pairs = reinterpret_cast<unsigned long long *>(zb + opc);
+        }
+        h->pairs_dev = D.pairs;
         if (make_digit_map(&h->map_zx, h->dpool.p, Tt * 14 * h->b, h->b, 128) ||
             make_digit_map(&h->map_zy, h->dpool.p, Tt * 14 * h->b, h->b, Z_BN))
             return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the digit planes");
@@ -531,6 +594,23 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
     if (D.zamax) CK(cudaMemsetAsync(D.zamax, 0, P.Ttot * sizeof(double), h->s));
     if (D.zamax2) CK(cudaMemsetAsync(D.zamax2, 0, P.Ttot * sizeof(double), h->s));
     if (D.zamax3) CK(cudaMemsetAsync(D.zamax3, 0, 3 * P.Ttot * sizeof(double), h->s));
+    if (D.oamax) {
+        // scale of every output tile before its updates: the reference of its plane budgets
+        CK(cudaMemsetAsync(D.oamax, 0, P.Ttot * sizeof(double), h->s));
+        CK(cudaMemsetAsync(D.pairs, 0, 2 * sizeof(unsigned long long), h->s));
+        launch_tile_amax(W, b, D.alltiles, (int)P.Ttot, D.oamax, h->s);
+        CK_LAUNCH();
+    }
+    // mixed-precision digit-plane updates: per-source plane budgets relative to the output
+    // tile's input scale (FP64 outputs: 14 reference planes; FP32 outputs: 10), margin 2 planes
+    ZPlanes zp64, zp32;
+    zp64.src_planes_tab = zp32.src_planes_tab = D.zplanes;
+    zp64.out_amax = zp32.out_amax = D.oamax;
+    zp64.rref = 14;
+    zp32.rref = 10;
+    zp64.margin = zp32.margin = kPlaneMargin;
+    zp64.pair_count = D.pairs;
+    zp32.pair_count = D.pairs ? D.pairs + 1 : nullptr;
     if (M) {
         CK(cudaMemsetAsync(D.mx.amaxL, 0, M->T * sizeof(double), h->s));
         CK(cudaMemsetAsync(D.mx.amaxS, 0, M->T * sizeof(double), h->s));
@@ -552,14 +632,16 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
         }
         if (C.nz) {
             const int sp = spans ? span_begin(h, CAT_UPD64) : -1;
-            launch_zgemm(h->map_zx, h->map_zy, D.zitems + C.z0, C.nz, D.zexps, k, b, status + 1, h->s, 14);
+            launch_zgemm(h->map_zx, h->map_zy, D.zitems + C.z0, C.nz, D.zexps, k, b, status + 1, h->s, 14, 0,
+                         D.zplanes ? &zp64 : nullptr, wait_limit_ns(h), wait_test(h));
             span_end(h, sp);
             CK_LAUNCH();
             ++h->upd_launches[TC_FP64];
         }
         if (C.ny) {
             const int sp = spans ? span_begin(h, CAT_UPD32) : -1;
-            launch_zgemm(h->map_zx, h->map_zy, D.zitems32 + C.y0, C.ny, D.zexps, k, b, status + 1, h->s, 10);
+            launch_zgemm(h->map_zx, h->map_zy, D.zitems32 + C.y0, C.ny, D.zexps, k, b, status + 1, h->s, 10, 0,
+                         D.zplanes ? &zp32 : nullptr, wait_limit_ns(h), wait_test(h));
             span_end(h, sp);
             CK_LAUNCH();
             ++h->upd_launches[TC_FP32];
@@ -611,7 +693,7 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
                 int off = C.v0;
                 for (int p = 0; p < 4; ++p) {
                     launch_zgemm(h->map_zx, h->map_zy, D.zinv + off, C.nvp[p], D.zexps, 1, b, status + 1, h->s,
-                                 ZTRSM_PLANES[p], 1);
+                                 ZTRSM_PLANES[p], 1, nullptr, wait_limit_ns(h), wait_test(h));
                     CK_LAUNCH();
                     off += C.nvp[p];
                 }
@@ -626,19 +708,22 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
                 CK_LAUNCH();
                 launch_digits_src(Lkk, b, 0, gl, am_l + gl, pool, D.zexps, h->s);
                 CK_LAUNCH();
-                launch_zgemm(h->map_zx, h->map_zy, D.zinvc + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1);
+                launch_zgemm(h->map_zx, h->map_zy, D.zinvc + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 1, nullptr,
+                             wait_limit_ns(h), wait_test(h));
                 CK_LAUNCH();
                 launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, am_x, h->s, X0);
                 CK_LAUNCH();
                 launch_digits(W, b, D.dtiles + C.dg0, C.ndg, am_x, pool, D.zexps, h->s, X0);
                 CK_LAUNCH();
-                launch_zgemm(h->map_zx, h->map_zy, D.zref + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 0);
+                launch_zgemm(h->map_zx, h->map_zy, D.zref + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, 14, 0, nullptr,
+                             wait_limit_ns(h), wait_test(h));
                 CK_LAUNCH();
                 launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, am_r, h->s);
                 CK_LAUNCH();
                 launch_digits(W, b, D.dtiles + C.dg0, C.ndg, am_r, pool, D.zexps, h->s);
                 CK_LAUNCH();
-                launch_zgemm(h->map_zx, h->map_zy, D.zinv + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, ZREF_PLANES, 1);
+                launch_zgemm(h->map_zx, h->map_zy, D.zinv + C.v0, C.nv, D.zexps, 1, b, status + 1, h->s, ZREF_PLANES, 1,
+                             nullptr, wait_limit_ns(h), wait_test(h));
                 CK_LAUNCH();
                 launch_add_tiles(W, b, D.dtiles + C.dg0, C.ndg, X0, h->s);
                 CK_LAUNCH();
@@ -677,6 +762,8 @@ int collect_results(tc_handle h, int *first_bad, int *err_word) {
     h->logdets.assign(nmat, 0.0);
     CK(cudaMemcpyAsync(st.data(), h->status.p, st.size() * sizeof(int), cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(h->logdets.data(), h->scratch.p, nmat * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    h->pairs_exec[0] = h->pairs_exec[1] = 0;
+    if (h->pairs_dev) CK(cudaMemcpyAsync(h->pairs_exec, h->pairs_dev, sizeof h->pairs_exec, cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
     h->infos.assign(st.begin() + 2, st.end());
     *err_word = st[1];
@@ -698,6 +785,18 @@ void fill_stats(tc_handle h, const Plan &P, const MxpPlan *M, tc_stats *stats, d
     if (M)
         for (int p = 1; p < 4; ++p) stats->update_flops[p] = M->flops[p];
     stats->update_flops[1] += P.update_flops[1];
+    for (int p = 0; p < 4; ++p) stats->tensor_flops[p] = P.tensor_flops[p];
+    if (h->pairs_dev) {
+        // mixed precision: the plane pairs the update kernels counted as they issued them
+        const double per_pair = 2.0 * 128.0 * Z_BN * h->b;
+        stats->tensor_flops[TC_FP64] = per_pair * (double)h->pairs_exec[0];
+        stats->tensor_flops[TC_FP32] = per_pair * (double)h->pairs_exec[1];
+    }
+    if (M) {
+        stats->tensor_flops[TC_FP32] += 3.0 * M->flops[TC_FP32];     // TF32 x 3 (when FP32 runs there)
+        stats->tensor_flops[TC_FP16] += M->flops[TC_FP16];
+        stats->tensor_flops[TC_FP8] += M->flops[TC_FP8];
+    }
     stats->trsm_flops = P.trsm_flops;
     stats->potrf_flops = P.potrf_flops;
     stats->kernel_launches = h->launches - launches0;
@@ -806,7 +905,8 @@ int tc_create(tc_handle *out, const tc_config *cfg) {
     tc_handle h = new tc_handle_s();
     if (cfg) h->cfg = *cfg;
     else tc_config_default(&h->cfg);
-    if (h->cfg.fp64_mode < 0 || h->cfg.fp64_mode > 2 || h->cfg.fp32_updates < 0 || h->cfg.fp32_updates > 1) {
+    if (h->cfg.fp64_mode < 0 || h->cfg.fp64_mode > 2 || h->cfg.fp32_updates < 0 || h->cfg.fp32_updates > 1 ||
+        h->cfg.wait_limit_us < 0) {
         delete h;
         return TC_ERR_ARG;
     }
@@ -858,6 +958,14 @@ void tc_destroy(tc_handle h) {
 }
 
 const char *tc_last_error(tc_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+int tc_set_wait_limit(tc_handle h, int wait_limit_us, int wait_test) {
+    if (!h) return TC_ERR_ARG;
+    if (wait_limit_us < 0) return set_err(h, TC_ERR_ARG, "wait_limit_us must be >= 0");
+    h->cfg.wait_limit_us = wait_limit_us;
+    h->cfg.wait_test = wait_test;
+    return TC_OK;
+}
 
 int tc_matern_tiles(tc_handle h, int64_t n, int b, const double *points, double sigma2, double range_a,
                     double nu, double nugget, double *A_tiles) {
@@ -1202,11 +1310,28 @@ int tile_chol_loglik_refined(tc_handle h, const double *y, int max_refine, doubl
     return TC_OK;
 }
 
+static int copy_factor(tc_handle h, const double *src, int64_t n, int nt, double *L_tiles);
+
 int tile_chol_get_factor(tc_handle h, double *L_tiles) {
     if (!h || !L_tiles) return TC_ERR_ARG;
     if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");
     CK(cudaSetDevice(h->device));
-    const int nt = h->nt, b = h->b;
+    return copy_factor(h, h->ooc ? h->host_factor : static_cast<const double *>(h->W.p), h->n, h->nt, L_tiles);
+}
+
+int tile_chol_get_factor_batched(tc_handle h, int index, double *L_tiles) {
+    if (!h || !L_tiles) return TC_ERR_ARG;
+    if (!h->factored || h->ooc) return set_err(h, TC_ERR_STATE, "no successful in-core factorization");
+    if (index < 0 || index >= (int)h->mats.size()) return set_err(h, TC_ERR_ARG, "index outside the last batch");
+    CK(cudaSetDevice(h->device));
+    const MatDesc &M = h->mats[index];
+    return copy_factor(h, static_cast<const double *>(h->W.p) + M.tile0 * (int64_t)h->b * h->b, M.n, M.nt, L_tiles);
+}
+
+// The factor tiles at src (device, or the out-of-core host factor) into L_tiles (host or
+// device), with upper triangles of diagonal tiles and padding written as 0.
+static int copy_factor(tc_handle h, const double *src, int64_t n, int nt, double *L_tiles) {
+    const int b = h->b;
     const size_t bytes = (size_t)nt * (nt + 1) / 2 * b * b * sizeof(double);
     double *dst = L_tiles;
     DevBuf tmp;
@@ -1216,9 +1341,8 @@ int tile_chol_get_factor(tc_handle h, double *L_tiles) {
         if (rc) return rc;
         dst = static_cast<double *>(tmp.p);
     }
-    CK(cudaMemcpyAsync(dst, h->ooc ? static_cast<const void *>(h->host_factor) : h->W.p, bytes, cudaMemcpyDefault,
-                       h->s));
-    launch_zero_upper_diag(dst, nt, b, h->n, h->s);
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->s));
+    launch_zero_upper_diag(dst, nt, b, n, h->s);
     CK_LAUNCH();
     if (!dev) CK(cudaMemcpyAsync(L_tiles, dst, bytes, cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));

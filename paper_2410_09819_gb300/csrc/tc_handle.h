@@ -77,6 +77,8 @@ struct tc_handle_s {
     size_t hcompact_bytes = 0;
     int64_t launches = 0;
     int64_t upd_launches[4] = {0, 0, 0, 0};
+    unsigned long long *pairs_dev = nullptr;   // plane-pair counters of the mixed digit-plane updates
+    unsigned long long pairs_exec[2] = {0, 0}; // their values after the last factorization
 
     // CUDA-event spans of the last factorization, by category (see Cat)
     std::vector<cudaEvent_t> events;
@@ -204,5 +206,13 @@ inline int check_nb(tc_handle h, int64_t n, int b) {
 }
 
 int ooc_subst(tc_handle h, double *R, int64_t ldr, int nrhs, bool back, int64_t *h2d_bytes);
+
+// Bound of the tensor-core kernels' pipeline waits for this handle (0: the kernels' default).
+inline unsigned long long wait_limit_ns(tc_handle h) {
+    return h->cfg.wait_limit_us > 0 ? (unsigned long long)h->cfg.wait_limit_us * 1000ull : 0ull;
+}
+// Failure-detection test hook (tc_config.wait_test): the tensor-core kernels first wait on a
+// barrier that nothing arrives at.
+inline int wait_test(tc_handle h) { return h->cfg.wait_test != 0; }
 
 }  // namespace tc

@@ -177,6 +177,7 @@ struct ZItem {
     double *C;
     int xoff, yoff;
     uint16_t bm, bn;
+    int ct = -1;        // global index of the output tile (plane counts relative to its scale)
 };
 
 // One grouped out-of-core update launch: tiles C[t] -= sum_{n<k} X_{t,n} Y_n^T, the operands
@@ -216,7 +217,7 @@ void launch_round_slot(double *T, int b, int p, const double *amaxL, int *e_out,
 void launch_pack_compact(const double *T, int b, int p, const int *e, void *dst, cudaStream_t s);
 void launch_unpack_compact(const void *src, int b, int p, const int *e, double *T, cudaStream_t s);
 void launch_qgemm_group(int kind, const CUtensorMap &mx, const CUtensorMap &my, const QGroup &g, const int *exps,
-                        int b, int *err, cudaStream_t s);
+                        int b, int *err, cudaStream_t s, unsigned long long limit_ns = 0, int stall = 0);
 
 // ------------------------------------------------------------------ launchers (k_ozaki.cu)
 size_t zgemm_smem_bytes();
@@ -225,10 +226,26 @@ void launch_digits(const double *W, int b, const int *tiles, int ntiles, const d
 void launch_lower_only(double *T, int b, cudaStream_t s);
 void launch_add_tiles(double *W, int b, const int *tiles, int ntiles, const double *src, cudaStream_t s);
 void launch_add_tile(double *dst, const double *src, int b, cudaStream_t s);     // dst += src, one b x b tile
+// planes: digit planes of the output precision (14 FP64, 10 FP32, fewer for TRSM products);
+// src_planes_tab: per digit slot, the leading planes that can be non-zero (nullptr: all);
+// limit_ns: bound of each pipeline wait (0: 4 s), after which *err is set and the call ends;
+// stall != 0: the failure-detection test hook (the MMA issuer waits on a barrier nothing arrives at).
+// Plane counts of a mixed-precision update launch (k_zgemm's SKIP form): per source, the X / Y
+// planes its stored formats can have non-zero (src_planes_tab), and a pair budget relative to
+// the output tile's scale: su = rref - floor((e_out - e_x - e_y - 4 margin) / 4), within
+// [1, 14], e_out the digit exponent of the output tile's input amax (out_amax[it.ct]).  The
+// launch adds the plane pairs it multiplies to *pair_count.
+struct ZPlanes {
+    const uint8_t *src_planes_tab = nullptr;
+    const double *out_amax = nullptr;
+    int rref = 14, margin = 2;
+    unsigned long long *pair_count = nullptr;
+};
 void launch_zgemm(const CUtensorMap &mx, const CUtensorMap &my, const ZItem *items, int nitems, const int *exps, int k,
-                  int b, int *err, cudaStream_t s, int planes = 14, int assign = 0);
+                  int b, int *err, cudaStream_t s, int planes = 14, int assign = 0,
+                  const ZPlanes *mixed = nullptr, unsigned long long limit_ns = 0, int stall = 0);
 void launch_zgemm_group(const CUtensorMap &mx, const CUtensorMap &my, const ZGroup &g, const int *exps, int b,
-                        int *err, cudaStream_t s, int planes = 14);
+                        int *err, cudaStream_t s, int planes = 14, unsigned long long limit_ns = 0, int stall = 0);
 void launch_digits_src(const double *src, int b, int transpose, int dst, const double *amax, uint8_t *pool, int *exps,
                        cudaStream_t s);
 void launch_amax_ptr(const double *src, int64_t count, double *out, cudaStream_t s);
@@ -240,7 +257,7 @@ int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize
 size_t qgemm_smem_bytes();
 void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                   const CUtensorMap &b1, const QItem *items, int nitems, const int *slot, const int *exps,
-                  int k, int b, int *err, cudaStream_t s);
+                  int k, int b, int *err, cudaStream_t s, unsigned long long limit_ns = 0, int stall = 0);
 void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, double *amax, cudaStream_t s,
                       const double *alt = nullptr);
 void launch_store_round(double *W, int b, const int *tiles, int ntiles, const uint8_t *prec, const double *amaxL,

@@ -582,14 +582,14 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                             zg.ntiles = cnt;
                             zg.k = kc;
                             for (int q = 0; q < kc; ++q) zg.ys[q] = ys[q];
-                            launch_zgemm_group(C.mx, C.my, zg, C.exps, b, status + 1, h->s, f == OP_Z14 ? 14 : 10);
+                            launch_zgemm_group(C.mx, C.my, zg, C.exps, b, status + 1, h->s, f == OP_Z14 ? 14 : 10, wait_limit_ns(h), wait_test(h));
                         } else {
                             qg.ntiles = cnt;
                             qg.k = kc;
                             for (int q = 0; q < kc; ++q) qg.ys[q] = ys[q];
                             launch_qgemm_group(f == OP_Q16 ? 2 : 3, f == OP_Q16 ? C.m16 : C.m8,
                                                f == OP_Q16 ? C.m16 : C.m8, qg, f == OP_Q16 ? C.e16 : C.e8, b,
-                                               status + 1, h->s);
+                                               status + 1, h->s, wait_limit_ns(h), wait_test(h));
                         }
                         span_end(h, spz);
                         CK_LAUNCH();
@@ -723,7 +723,7 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                     if (refine) ref[nref++] = i;
                 }
                 for (int p = 0; p < 4; ++p)
-                    launch_zgemm_group(C.mx, C.my, z1[p], C.exps, b, status + 1, h->s, ZTRSM_PLANES[p]);
+                    launch_zgemm_group(C.mx, C.my, z1[p], C.exps, b, status + 1, h->s, ZTRSM_PLANES[p], wait_limit_ns(h), wait_test(h));
                 if (nref) {
                     ZGroup z2, z3;
                     z2.ntiles = z3.ntiles = nref;
@@ -738,9 +738,9 @@ extern "C" int tile_chol_factor_ooc(tc_handle h, int64_t n, int b, double *A_til
                         z2.C[r] = z3.C[r] = C.ptr(so[i]);
                         z2.xs[r][0] = z3.xs[r][0] = so[i];
                     }
-                    launch_zgemm_group(C.mx, C.my, z2, C.exps, b, status + 1, h->s);  // R = C - X0 L^T
+                    launch_zgemm_group(C.mx, C.my, z2, C.exps, b, status + 1, h->s, 14, wait_limit_ns(h), wait_test(h));  // R = C - X0 L^T
                     for (int r = 0; r < nref; ++r) C.planes_of(C.ptr(so[ref[r]]), so[ref[r]]);
-                    launch_zgemm_group(C.mx, C.my, z3, C.exps, b, status + 1, h->s, ZREF_PLANES);  // R L^{-T}
+                    launch_zgemm_group(C.mx, C.my, z3, C.exps, b, status + 1, h->s, ZREF_PLANES, wait_limit_ns(h), wait_test(h));  // R L^{-T}
                     for (int r = 0; r < nref; ++r)
                         launch_add_tile(C.ptr(so[ref[r]]), inv + (int64_t)(1 + ref[r]) * C.bb, b, h->s);
                 }

@@ -18,11 +18,13 @@ __all__ = [
     "tile_chol_precision_map", "tile_chol_factor", "tile_chol_factor_ooc", "tile_chol_solve", "tile_chol_logdet",
     "tile_chol_loglik", "tile_chol_loglik_refined", "tile_chol_get_factor", "tile_chol_precision_map_noalloc", "tile_chol_factor_batched",
     "tile_chol_solve_batched", "tile_chol_loglik_batched", "Handle", "ntiles",
-    "tile_count",
+    "tile_count", "tc_set_wait_limit", "tile_chol_get_factor_batched",
 ]
 
 TC_FP64, TC_FP32, TC_FP16, TC_FP8 = 0, 1, 2, 3
 TC_OK = 0
+TC_ERR_ARG, TC_ERR_STATE, TC_ERR_CUDA, TC_ERR_OOM, TC_ERR_TIMEOUT, TC_ERR_HOSTMEM, TC_ERR_UNSUPPORTED = (
+    -1, -2, -100, -101, -102, -103, -104)
 ERRORS = {-1: "TC_ERR_ARG", -2: "TC_ERR_STATE", -100: "TC_ERR_CUDA", -101: "TC_ERR_OOM",
           -102: "TC_ERR_TIMEOUT", -103: "TC_ERR_HOSTMEM", -104: "TC_ERR_UNSUPPORTED"}
 
@@ -39,7 +41,8 @@ class tc_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("ooc", ctypes.c_int),
                 ("device_cap_bytes", ctypes.c_int64), ("prefetch_depth", ctypes.c_int),
                 ("lookahead", ctypes.c_int), ("fp64_mode", ctypes.c_int), ("ooc_eviction", ctypes.c_int),
-                ("fp32_updates", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("fp32_updates", ctypes.c_int), ("wait_limit_us", ctypes.c_int),
+                ("wait_test", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class tc_stats(ctypes.Structure):
@@ -51,7 +54,7 @@ class tc_stats(ctypes.Structure):
                 ("info", ctypes.c_int), ("ooc", ctypes.c_int),
                 ("t_update_ms", ctypes.c_double * 4), ("t_potrf_ms", ctypes.c_double),
                 ("t_trsm_ms", ctypes.c_double), ("t_convert_ms", ctypes.c_double),
-                ("update_launches", ctypes.c_int64 * 4)]
+                ("update_launches", ctypes.c_int64 * 4), ("tensor_flops", ctypes.c_double * 4)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -79,6 +82,7 @@ def lib() -> ctypes.CDLL:
         "tc_create": (ci, [ctypes.POINTER(H), ctypes.POINTER(tc_config)]),
         "tc_destroy": (None, [H]),
         "tc_last_error": (ctypes.c_char_p, [H]),
+        "tc_set_wait_limit": (ci, [H, ci, ci]),
         "tc_matern_tiles": (ci, [H, i64, ci, vp, cd, cd, cd, cd, vp]),
         "tile_chol_precision_map": (ci, [H, i64, ci, vp, cd, ci, ci, vp, vp]),
         "tile_chol_factor": (ci, [H, i64, ci, vp, vp, ctypes.POINTER(tc_stats)]),
@@ -87,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "tile_chol_logdet": (ci, [H, ctypes.POINTER(cd)]),
         "tile_chol_loglik": (ci, [H, vp, ctypes.POINTER(cd)]),
         "tile_chol_get_factor": (ci, [H, vp]),
+        "tile_chol_get_factor_batched": (ci, [H, ci, vp]),
         "tile_chol_loglik_refined": (ci, [H, vp, ci, cd, ctypes.POINTER(cd), ctypes.POINTER(cd)]),
         "tile_chol_precision_map_noalloc": (ci, [i64, ci, vp, cd, ci, ci, vp, vp]),
         "tile_chol_factor_batched": (ci, [H, ci, vp, ci, vp, vp, vp, vp, ctypes.POINTER(tc_stats)]),
@@ -182,6 +187,10 @@ def tc_last_error(h) -> str:
     return lib().tc_last_error(h).decode()
 
 
+def tc_set_wait_limit(h, wait_limit_us: int, wait_test: int = 0) -> None:
+    _check(h, lib().tc_set_wait_limit(h, wait_limit_us, wait_test))
+
+
 def tc_matern_tiles(h, n, b, points, sigma2, range_a, nu, nugget, A_tiles) -> None:
     _need(points, "float64", 2 * n if isinstance(n, (int, np.integer)) and n >= 1 else None, "points")
     _need_tiles(n, b, A_tiles)
@@ -243,6 +252,11 @@ def tile_chol_loglik_refined(h, y, max_refine=5, target_berr=1e-14):
 def tile_chol_get_factor(h, L_tiles) -> None:
     _need(L_tiles, "float64", None, "L_tiles")
     _check(h, lib().tile_chol_get_factor(h, _ptr(L_tiles)))
+
+
+def tile_chol_get_factor_batched(h, index: int, L_tiles) -> None:
+    _need(L_tiles, "float64", None, "L_tiles")
+    _check(h, lib().tile_chol_get_factor_batched(h, index, _ptr(L_tiles)))
 
 
 def _ptr_array(items):

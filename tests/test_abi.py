@@ -57,3 +57,15 @@ def test_null_handle_is_rejected_without_touching_a_gpu(lib):
     assert L.tile_chol_factor(None, 10, 64, None, None, None) == -1
     assert L.tile_chol_logdet(None, None) == -1
     assert L.tc_last_error(None) == b"null handle"
+    assert L.tc_set_wait_limit(None, 5, 0) == -1
+
+
+def test_config_struct_matches_the_header():
+    # the binding's tc_config mirrors include/tile_chol.h field by field
+    from paper_2410_09819_gb300 import tile_chol
+    names = [f[0] for f in tile_chol.tc_config._fields_]
+    text = open(os.path.join(ROOT, "include", "tile_chol.h")).read()
+    body = text[text.index("typedef struct {"):text.index("} tc_config;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    declared = re.findall(r"\b([a-z_][a-z0-9_]*)\s*(?:\[\d+\])?;", body)
+    assert names == declared, (names, declared)

@@ -35,7 +35,7 @@ def test_both_arms_share_the_workload_config():
     sys.path.insert(0, ROOT)
     import bench
     from paper_2410_09819_gb300 import inputs
-    w = inputs.WORKLOADS["fp64_n65536"]
+    w = inputs.WORKLOADS[bench.DEFAULT_WORKLOAD]
     d = run_reference()
     cfg = dict(d["config"])
     cfg.pop("sample_n")

@@ -80,3 +80,36 @@ def test_dfma_roofline_is_an_alu_peak(monkeypatch):
     peak = 152 * 4 * 2070e6 / 1e12                       # 152 SMs x 2 DFMA per clock x 2.07 GHz
     assert r["bound"] == "alu" and r["peak"] == pytest.approx(peak, rel=1e-4)
     assert r["achieved"] == pytest.approx(1.2) and r["frac"] == pytest.approx(1.2 / peak)
+
+
+def test_accuracy_probe_products_against_dense():
+    # bench.py's harness-side products with packed tiles (used by the factor backward-error
+    # probe of the four-precision line), on the CPU against dense numpy, ragged n
+    import numpy as np
+    import torch
+
+    import oracle
+    n, b = 300, 128
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((n, n))
+    S = M @ M.T + n * np.eye(n)
+    nt = -(-n // b)
+    N = nt * b
+    Sp = np.eye(N)
+    Sp[:n, :n] = S
+    P = torch.from_numpy(oracle.pack_tiles(Sp, b).reshape(-1).copy())
+    Lo = np.linalg.cholesky(Sp)
+    Lp = torch.from_numpy(oracle.pack_tiles(np.tril(Lo) + np.triu(rng.standard_normal((N, N)), 1), b)
+                          .reshape(-1).copy())              # garbage above the diagonal is ignored
+    x = rng.standard_normal(n)
+    xt = torch.from_numpy(x)
+    assert np.allclose(bench.tiles_matvec(P, n, b, xt, "cpu", "sym").numpy(), S @ x, rtol=1e-12, atol=1e-10)
+    L = Lo[:n, :n]
+    assert np.allclose(bench.tiles_matvec(Lp, n, b, xt, "cpu", "L").numpy(), L @ x, rtol=1e-12, atol=1e-10)
+    assert np.allclose(bench.tiles_matvec(Lp, n, b, xt, "cpu", "Lt").numpy(), L.T @ x, rtol=1e-12, atol=1e-10)
+    # the probe: an exact factor gives FP64 rounding, a perturbed one its perturbation
+    assert bench.factor_probe_berr(P, Lp, n, b, "cpu") < 1e-14
+    Lq = Lo.copy()
+    Lq[:n, :n] *= 1.0 + 1e-6
+    Lqp = torch.from_numpy(oracle.pack_tiles(np.tril(Lq), b).reshape(-1).copy())
+    assert 1e-6 < bench.factor_probe_berr(P, Lqp, n, b, "cpu") < 4e-6
