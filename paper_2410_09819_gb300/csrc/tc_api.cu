@@ -70,6 +70,23 @@ inline int stored_planes(const MatDesc &M, int i, int j) {
     const int p = M.map[(size_t)i * M.nt + j];
     return p == TC_FP8 ? 5 : p == TC_FP16 ? 10 : 14;
 }
+// Order of the 128 x Z_BN work items of one output tile for the persistent emulated-update
+// kernel.  Its 152 CTAs take items c, c + 152, ..., so each run of 152 consecutive items runs
+// at once, and every item walks all its sources: an X slab (row block bm) is read by the
+// items of its bm in the same run, a Y slab (column block bn) by those of its bn.  Runs of
+// kItemRowBlocks row blocks x ~152/kItemRowBlocks column blocks keep both sets small (each
+// slab is fetched from DRAM once per run that uses it: about (nbn / 38 + nbm / 4) times per
+// tile instead of nbn * nbm / 152 times for X with row-block-fastest runs).
+constexpr int kItemRowBlocks = 4;
+template <class F>
+void for_tile_items(int b, bool lower_only, F &&emit) {
+    const int nbm = b / 128, nbn = b / Z_BN;
+    for (int bm0 = 0; bm0 < nbm; bm0 += kItemRowBlocks)
+        for (int bn = 0; bn < nbn; ++bn)
+            for (int bm = bm0; bm < std::min(nbm, bm0 + kItemRowBlocks); ++bm)
+                if (!lower_only || bm * 128 + 127 >= bn * Z_BN) emit(bm, bn);
+}
+
 // Plane pairs (s, t), s < sx, t < sy, s + t < su, that one emulated product multiplies.
 inline int plane_pairs(int sx, int sy, int su) {
     sx = std::min(sx, su);
@@ -151,9 +168,10 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                         // FP32 output: 10 digit planes of each operand, FP64 running sums
                         double *Cp = T(M, m, k);
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
-                        for (int bn = 0; bn < b / Z_BN; ++bn)
-                            for (int bm = 0; bm < b / 128; ++bm)
-                                P.zitems32.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn, (int)(M.tile0 + tidx(m, k))});
+                        const int ct = (int)(M.tile0 + tidx(m, k));
+                        for_tile_items(b, false, [&](int bm, int bn) {
+                            P.zitems32.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn, ct});
+                        });
                         P.update_flops[TC_FP32] += 2.0 * (double)b * b * K;
                         for (int nn = 0; nn < k; ++nn)
                             P.tensor_flops[TC_FP32] += 2.0 * (double)b * b * b *
@@ -162,16 +180,15 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                     }
                     if (!fp64) continue;
                     if (zmode) {
-                        // emulated FP64: 128 x 32 blocks (the diagonal SYRK keeps blocks reaching the lower part)
+                        // emulated FP64: 128 x 16 blocks (the diagonal SYRK keeps blocks reaching the lower part)
                         double *Cp = T(M, m, k);
                         const int xo = (int)(M.tile0 + tidx(m, 0)), yo = (int)(M.tile0 + tidx(k, 0));
                         int items = 0;
-                        for (int bn = 0; bn < b / Z_BN; ++bn)
-                            for (int bm = 0; bm < b / 128; ++bm)
-                                if (m != k || bm * 128 + 127 >= bn * Z_BN) {
-                                    P.zitems.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn, (int)(M.tile0 + tidx(m, k))});
-                                    ++items;
-                                }
+                        const int ct = (int)(M.tile0 + tidx(m, k));
+                        for_tile_items(b, m == k, [&](int bm, int bn) {
+                            P.zitems.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn, ct});
+                            ++items;
+                        });
                         P.update_flops[TC_FP64] += (m == k ? 1.0 : 2.0) * (double)b * b * K;
                         for (int nn = 0; nn < k; ++nn)
                             P.tensor_flops[TC_FP64] += 2.0 * 128.0 * Z_BN * b * items *
@@ -218,14 +235,13 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 double *Cp = T(M, m, k);
                 double *Cs = P.inv_refine ? inv_scratch + (int64_t)(m - k) * bb : nullptr;
                 const int sx = (int)(M.tile0 + tidx(m, k));
-                for (int bn = 0; bn < b / Z_BN; ++bn)
-                    for (int bm = 0; bm < b / 128; ++bm) {
-                        P.zinv.push_back({Cp, sx, sinv, (uint16_t)bm, (uint16_t)bn});
-                        if (P.inv_refine) {
-                            P.zinvc.push_back({Cs, sx, sinv, (uint16_t)bm, (uint16_t)bn});
-                            P.zref.push_back({Cp, sx, sl, (uint16_t)bm, (uint16_t)bn});
-                        }
+                for_tile_items(b, false, [&](int bm, int bn) {
+                    P.zinv.push_back({Cp, sx, sinv, (uint16_t)bm, (uint16_t)bn});
+                    if (P.inv_refine) {
+                        P.zinvc.push_back({Cs, sx, sinv, (uint16_t)bm, (uint16_t)bn});
+                        P.zref.push_back({Cp, sx, sl, (uint16_t)bm, (uint16_t)bn});
                     }
+                });
                 C.nvp[p] += (int)(P.zinv.size() - before);
             }
         }
