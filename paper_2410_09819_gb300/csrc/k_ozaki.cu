@@ -27,9 +27,20 @@ namespace tc {
 constexpr int ZS = 14;                 // digit planes per tile
 constexpr int ZBM = 128, ZBN = Z_BN;   // work item: 128 rows x 16 columns
 constexpr int ZKB = 128;               // K bytes (= E4M3 elements) per stage
-constexpr int ZXS = 10;                // X-plane stages
-constexpr int ZYS = 2;                 // Y-set stages
-constexpr int ZPG = 2;                 // X planes per MMA issue round (4: no better)
+// Pipeline depth (shared memory: ZXS x 16 KB + ZYS x 28 KB <= 227 KB).  Compile-time knobs
+// for tuning sweeps; the defaults are the measured best.
+#ifndef ZGEMM_XS
+#define ZGEMM_XS 10
+#endif
+#ifndef ZGEMM_YS
+#define ZGEMM_YS 2
+#endif
+#ifndef ZGEMM_PG
+#define ZGEMM_PG 2
+#endif
+constexpr int ZXS = ZGEMM_XS;          // X-plane stages
+constexpr int ZYS = ZGEMM_YS;          // Y-set stages
+constexpr int ZPG = ZGEMM_PG;          // X planes per MMA issue round (4: no better)
 constexpr int ZX_BYTES = ZBM * ZKB;    // 16 KB: one X plane block
 constexpr int ZY_BYTES = ZBN * ZKB;    // 2 KB: one Y plane block
 constexpr int ZYSET = ZS * ZY_BYTES;   // 28 KB: all Y planes of a K block
