@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--n", type=int, default=0, help="override n (smaller quick runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy probes after the timed region (the all-FP64 reference factor of the "
+                         "four-precision line among them): a launch list then holds the timed step's kernels only")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_N)
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy / performance sweep of Section V: weak, medium, strong correlation x "
@@ -212,6 +215,24 @@ KERNELS = {0: ("k_zgemm<14> (FP64 outputs, E4M3 digit planes)", "e4m3", 2.0),
            3: ("k_qgemm<3> (FP8 E4M3 outputs)", "e4m3", 2.0)}
 
 
+def committed_profile(tag: str) -> dict:
+    """The committed ncu summary profiles/<tag>.md of the dominant kernel: the kernel-source
+    sha it was captured at (compared with the current source) and its per-launch figures."""
+    path = os.path.join(ROOT, "profiles", f"{tag}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return {"file": f"profiles/{tag}.md", "present": False}
+    m = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    out = {"file": f"profiles/{tag}.md", "present": True, "kernel_source_sha": m.group(1) if m else None}
+    out["matches_current_source"] = bool(m) and m.group(1) == kernel_source_sha()
+    for key in ("dram_bytes_per_launch", "l2_to_sm_bytes_per_launch", "tensor_active_pct", "launch_ms"):
+        mm = re.search(rf"{key}:\s*([0-9.eE+-]+)", text)
+        if mm:
+            out[key] = float(mm.group(1))
+    return out
+
+
 def probed_peaks() -> dict:
     """Dense GEMM peaks measured on this machine's GB300 by ``bench.py --peaks`` (the committed
     summary profiles/peaks_gb300.md carries them as a JSON line), or {} if absent."""
@@ -352,6 +373,7 @@ def run_ours(args, ws, rank, local):
                     "peak_source": f"ALU: 152 SMs x 4 FP64 flop/clk x {pk_kind} max SM clock",
                     "share_of_step": (upd_ms / 1e3) / t if t > 0 else None}
     roofline["kernel_source_sha"] = kernel_source_sha()
+    roofline["profile"] = committed_profile("zgemm_mxp4_n32768" if w.mixed else "zgemm_fp64_n16384")
 
     # accuracy of a mixed-precision factorization, outside the timed region: random-probe
     # backward error of the factor, Eq. 1 with the plain and the refined quadratic form, Eq. 3
@@ -360,7 +382,19 @@ def run_ours(args, ws, rank, local):
     accuracy = None
     comparisons = {} if (rank == 0 and ws == 1) else None
     Ah = None
-    if w.mixed:
+    if not w.mixed and not args.no_accuracy:
+        # the FP64 line states its factor's backward error too (A and L both fit on the device)
+        L = torch.empty(T * b * b, dtype=torch.float64, device=dev)
+        tc.tile_chol_get_factor(H.h, L)
+        accuracy = {"factor_berr_probe": factor_probe_berr(A, L, n, b, dev),
+                    "factor_berr_probe_method": "max over 3 Gaussian x of ||(A - L L^T) x|| / ||A x|| (torch FP64 "
+                                                "products with the packed tiles of A and of the factor)",
+                    "solve_berr_refined": ss.berr,
+                    "meaning": "normwise backward error of the factor; the emulated FP64 updates are normwise "
+                               "FP64 (relative to each tile pair's scale)"}
+        del L
+        torch.cuda.empty_cache()
+    if w.mixed and not args.no_accuracy:
         ld_mxp = tc.tile_chol_logdet(H.h)
         ll_plain = tc.tile_chol_loglik(H.h, y)
         ll_ref5, berr_mxp = tc.tile_chol_loglik_refined(H.h, y, 5, 1e-14)

@@ -181,14 +181,16 @@ k_matern(double *A, int64_t n, int b, const double *__restrict__ pts, double sig
 
 // Sum of squares of the valid (row, column < n) elements of every tile; one CTA per tile,
 // fixed reduction order.
-__global__ void __launch_bounds__(256) k_tile_sumsq(const double *A, int b, int64_t n, double *out) {
+// Sum of squares of tile t0 + blockIdx.x (global packed index; the tile itself at
+// A + blockIdx.x b^2), padding excluded.
+__global__ void __launch_bounds__(256) k_tile_sumsq(const double *A, int b, int64_t n, double *out, int t0) {
     __shared__ double red[256];
-    const int t = blockIdx.x;
+    const int t = t0 + (int)blockIdx.x;
     int i = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
     while ((int64_t)i * (i + 1) / 2 > t) --i;
     while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
     const int j = t - i * (i + 1) / 2;
-    const double *T = A + (int64_t)t * b * b;
+    const double *T = A + (int64_t)blockIdx.x * b * b;
     const int64_t bb = (int64_t)b * b;
     const int nvr = (int)((n - (int64_t)i * b) < b ? (n - (int64_t)i * b) : b);
     const int nvc = (int)((n - (int64_t)j * b) < b ? (n - (int64_t)j * b) : b);
@@ -219,7 +221,10 @@ void launch_matern(double *A, int64_t n, int b, int nt, const double *pts, doubl
 
 void launch_tile_sumsq(const double *A, int nt, int b, int64_t n, double *out, cudaStream_t s) {
     const int T = nt * (nt + 1) / 2;
-    k_tile_sumsq<<<T, 256, 0, s>>>(A, b, n, out);
+    k_tile_sumsq<<<T, 256, 0, s>>>(A, b, n, out, 0);
+}
+void launch_tile_sumsq_range(const double *A_first, int t0, int count, int b, int64_t n, double *out, cudaStream_t s) {
+    if (count > 0) k_tile_sumsq<<<count, 256, 0, s>>>(A_first, b, n, out, t0);
 }
 
 }  // namespace tc

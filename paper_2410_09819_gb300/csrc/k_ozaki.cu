@@ -660,14 +660,9 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 long long hi[ZBN], lo[ZBN];
 #pragma unroll
                 for (int j = 0; j < ZBN; ++j) hi[j] = lo[j] = 0;
-                for (int g = 0; g < SU; ++g) {
+                for (int g = 0; g < G; ++g) {
                     float v[16];
-                    if (!SKIP || g < G) {
-                        z_ld16(lanebase + (uint32_t)(g * ZBN), v);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] = 0.f;
-                    }
+                    z_ld16(lanebase + (uint32_t)(g * ZBN), v);
                     // group sums are exact integers below 2^24 in magnitude: a 32-bit
                     // conversion (a 64-bit one would run on the FP64 pipe)
                     if (g < 7) {
@@ -682,8 +677,24 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) z_arrive(acce + a);
+                // groups G .. SU-1 are zero: the Horner steps they would take are shifts
+                constexpr int NH = SU < 7 ? SU : 7;            // groups of hi
+                if (G < SU) {
+                    const long long m_hi = 1LL << (G < NH ? 4 * (NH - G) : 0);
+                    const long long m_lo = 1LL << (G > NH ? 4 * (SU - G) : 0);
 #pragma unroll
-                for (int j = 0; j < ZBN; ++j) run[j] = fma((double)lo[j], s_lo, fma((double)hi[j], s_hi, run[j]));
+                    for (int j = 0; j < ZBN; ++j) {
+                        hi[j] *= m_hi;
+                        lo[j] *= m_lo;
+                    }
+                }
+                if (G > NH) {
+#pragma unroll
+                    for (int j = 0; j < ZBN; ++j) run[j] = fma((double)lo[j], s_lo, fma((double)hi[j], s_hi, run[j]));
+                } else {                                        // no lo groups: lo == 0
+#pragma unroll
+                    for (int j = 0; j < ZBN; ++j) run[j] = fma((double)hi[j], s_hi, run[j]);
+                }
             }
             if (!ok) break;
             const int row = it.bm * ZBM + quarter * 32 + lane;

@@ -1033,19 +1033,28 @@ int tile_chol_precision_map(tc_handle h, int64_t n, int b, const double *A_tiles
     CK(cudaSetDevice(h->device));
     const int nt = (int)((n + b - 1) / b);
     const int64_t T = (int64_t)nt * (nt + 1) / 2;
-    const double *dA = A_tiles;
-    DevBuf tmp;
-    if (!on_device(A_tiles)) {
-        const size_t bytes = (size_t)T * b * b * sizeof(double);
-        rc = ensure(h, tmp, bytes);
-        if (rc) return rc;
-        CK(cudaMemcpyAsync(tmp.p, A_tiles, bytes, cudaMemcpyHostToDevice, h->s));
-        dA = static_cast<const double *>(tmp.p);
-    }
     rc = ensure(h, h->sumsq, (size_t)T * sizeof(double));
-    if (rc) { release(tmp); return rc; }
-    launch_tile_sumsq(dA, nt, b, n, static_cast<double *>(h->sumsq.p), h->s);
-    CK_LAUNCH();
+    if (rc) return rc;
+    double *ssd = static_cast<double *>(h->sumsq.p);
+    DevBuf tmp;
+    if (on_device(A_tiles)) {
+        launch_tile_sumsq(A_tiles, nt, b, n, ssd, h->s);
+        CK_LAUNCH();
+    } else {
+        // a host matrix streams through a bounded staging buffer (about 1 GiB of tiles), so the
+        // map needs no device copy of A beside what the handle already holds
+        const size_t tile_bytes = (size_t)b * b * sizeof(double);
+        const int64_t per = std::max<int64_t>(1, std::min<int64_t>(T, ((int64_t)1 << 30) / (int64_t)tile_bytes));
+        rc = ensure(h, tmp, (size_t)per * tile_bytes);
+        if (rc) return rc;
+        for (int64_t t0 = 0; t0 < T; t0 += per) {
+            const int64_t cnt = std::min<int64_t>(per, T - t0);
+            CK(cudaMemcpyAsync(tmp.p, A_tiles + t0 * (int64_t)b * b, (size_t)cnt * tile_bytes, cudaMemcpyHostToDevice,
+                               h->s));
+            launch_tile_sumsq_range(static_cast<const double *>(tmp.p), (int)t0, (int)cnt, b, n, ssd, h->s);
+            CK_LAUNCH();
+        }
+    }
     std::vector<double> ss(T);
     CK(cudaMemcpyAsync(ss.data(), h->sumsq.p, T * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));

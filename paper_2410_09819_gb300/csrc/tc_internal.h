@@ -171,6 +171,8 @@ void launch_dots_g(const SMax *m, int nm, const double *u, const double *v, doub
 void launch_matern(double *A, int64_t n, int b, int nt, const double *pts, double sigma2,
                    double a, int nu2, double nu, double nugget, cudaStream_t s);
 void launch_tile_sumsq(const double *A, int nt, int b, int64_t n, double *out, cudaStream_t s);
+// tiles t0 .. t0+count-1 of the packed layout, the first of them at A_first
+void launch_tile_sumsq_range(const double *A_first, int t0, int count, int b, int64_t n, double *out, cudaStream_t s);
 
 // Emulated-FP64 update of one 128 x 32 block of an FP64 output tile (k_ozaki.cu).
 struct ZItem {
