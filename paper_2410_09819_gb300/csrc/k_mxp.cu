@@ -528,19 +528,25 @@ static EncodeTiledFn encode_fn() {
 
 // 2-D map over a pool: rows = nslots * b, columns = b elements of esize bytes; box of
 // (128 bytes) x box_rows with 128-byte swizzle.
-int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows) {
+// rows of b elements; box: box_k_bytes (128 or 64, swizzled to match) x box_rows
+int make_pool_map_k(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows, int box_k_bytes) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return -1;
+    if (box_k_bytes != 128 && box_k_bytes != 64) return -1;
     const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
     cuuint64_t dims[2] = {(cuuint64_t)b, (cuuint64_t)(nslots * b)};
     cuuint64_t strides[1] = {(cuuint64_t)b * esize};
-    cuuint32_t box[2] = {(cuuint32_t)(QKB / esize), (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(box_k_bytes / esize), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, dt, 2, pool, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    box_k_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : (int)r;
+}
+int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows) {
+    return make_pool_map_k(map, pool, nslots, b, esize, box_rows, QKB);
 }
 
 size_t qgemm_smem_bytes() { return (size_t)QSTAGES * QSTAGE_BYTES + 1024 + 256; }

@@ -27,21 +27,25 @@ namespace tc {
 constexpr int ZS = 14;                 // digit planes per tile
 constexpr int ZBM = 128, ZBN = Z_BN;   // work item: 128 rows x 16 columns
 constexpr int ZKB = 128;               // K bytes (= E4M3 elements) per stage
-// Pipeline depth (shared memory: ZXS x 16 KB + ZYS x 28 KB <= 227 KB).  Compile-time knobs
-// for tuning sweeps; the defaults are the measured best.
+// Pipeline (shared memory: ZXS x ZXP x 16 KB + ZYS x 28 KB <= 227 KB).  The single MMA-issuing
+// thread is the limit on GB300: a tcgen05.mma of N <= 128 occupies the tensor pipe for only ~69
+// cycles, while each mbarrier wait in the issue stream leaves it idle for ~200-300 cycles, so X
+// planes travel in stages of ZXP = 2 (one wait, one fence and one commit per two planes; +15-22 %
+// over one plane per stage, measured for plane budgets 2..14).  Compile-time knobs for sweeps.
 #ifndef ZGEMM_XS
-#define ZGEMM_XS 10
+#define ZGEMM_XS 5
 #endif
 #ifndef ZGEMM_YS
 #define ZGEMM_YS 2
 #endif
-#ifndef ZGEMM_PG
-#define ZGEMM_PG 2
+#ifndef ZGEMM_XP
+#define ZGEMM_XP 2
 #endif
-constexpr int ZXS = ZGEMM_XS;          // X-plane stages
+constexpr int ZXS = ZGEMM_XS;          // X stages of ZXP planes
 constexpr int ZYS = ZGEMM_YS;          // Y-set stages
-constexpr int ZPG = ZGEMM_PG;          // X planes per MMA issue round (4: no better)
 constexpr int ZX_BYTES = ZBM * ZKB;    // 16 KB: one X plane block
+constexpr int ZXP = ZGEMM_XP;          // X planes per stage
+constexpr int ZXSTAGE = ZXP * ZX_BYTES;
 constexpr int ZY_BYTES = ZBN * ZKB;    // 2 KB: one Y plane block
 constexpr int ZYSET = ZS * ZY_BYTES;   // 28 KB: all Y planes of a K block
 constexpr int ZTHREADS = 192;          // producer, MMA, 4 drain warps
@@ -248,6 +252,26 @@ __device__ __forceinline__ void z_mma(uint32_t d, uint64_t a, uint64_t bdesc, ui
         "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
         "l"(a), "l"(bdesc), "r"(idesc), "r"(acc));
 }
+// The 4 MMAs of one 128-byte K block in one asm block: the first K step takes the accumulate
+// predicate, the others accumulate; A and B advance by 32 bytes (2 descriptor units) per step.
+__device__ __forceinline__ void z_mma4(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %5, %6, %3, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %7, %8, %3, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %9, %10, %3, q;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc), "l"(a + 2), "l"(b + 2), "l"(a + 4), "l"(b + 4), "l"(a + 6), "l"(b + 6));
+}
+// K steps 1..3 of a K block (all accumulate)
+__device__ __forceinline__ void z_mma3(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.eq.b32 q, %3, %3;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %4, %5, %3, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %6, %7, %3, q;\n\t}\n" ::"r"(d),
+        "l"(a + 2), "l"(b + 2), "r"(idesc), "l"(a + 4), "l"(b + 4), "l"(a + 6), "l"(b + 6));
+}
 __device__ __forceinline__ void z_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
     asm volatile(
@@ -336,44 +360,35 @@ __device__ __forceinline__ bool z_issue_kblock(int kb, uint64_t xdesc_base, uint
     constexpr uint32_t idesc0 = (1u << 4) | ((uint32_t)(ZBM >> 4) << 24);
     const bool asc = SY < SU && kb == 0;
 #pragma unroll
-    for (int i0 = 0; i0 < SX; i0 += ZPG) {
-        const int cnt = (SX - i0) < ZPG ? (SX - i0) : ZPG;
-        int st = xst, ph = xph;
-        bool ready = true;
-#pragma unroll
-        for (int h = 0; h < ZPG; ++h)
-            if (h < cnt) {
-                ready = ready && z_wait(xfull + st, ph, abort_flag, lim);
-                if (++st == ZXS) { st = 0; ph ^= 1; }
-            }
-        if (!ready) return false;
+    for (int i0 = 0; i0 < SX; i0 += ZXP) {
+        if (!z_wait(xfull + xst, xph, abort_flag, lim)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t xsd = xdesc_base + (uint64_t)((xst * ZXSTAGE) >> 4);
 #pragma unroll
-        for (int h = 0; h < ZPG; ++h)
-            if (h < cnt) {
+        for (int h = 0; h < ZXP; ++h)
+            if (i0 + h < SX) {
                 const int i = i0 + h;
                 const int s = asc ? i : ((i & 1) ? SX - 1 - (i >> 1) : (i >> 1));
                 const int np = SY < SU - s ? SY : SU - s;
-                const uint64_t xd = xdesc_base + (uint64_t)((xst * ZX_BYTES) >> 4);
+                const uint64_t xd = xsd + (uint64_t)((h * ZX_BYTES) >> 4);
                 const uint32_t idesc = idesc0 | ((uint32_t)((np * ZBN) >> 3) << 17);
                 const uint32_t d = dbase + (uint32_t)(s * ZBN);
                 if (kb > 0) {
-                    z_mma(d, xd, yd, idesc, 1u);
+                    z_mma4(d, xd, yd, idesc, 1u);
                 } else if (s == 0) {
-                    z_mma(d, xd, yd, idesc, 0u);                    // starts groups 0 .. np-1
+                    z_mma4(d, xd, yd, idesc, 0u);                   // starts groups 0 .. np-1
                 } else if (asc && np == SY) {
-                    // groups s .. s+np-2 are running; group s+np-1 starts here
+                    // groups s .. s+np-2 are running; group s+np-1 starts here (K step 0)
                     if (np > 1) z_mma(d, xd, yd, idesc0 | ((uint32_t)(((np - 1) * ZBN) >> 3) << 17), 1u);
                     z_mma(d + (uint32_t)((np - 1) * ZBN), xd, yd + (uint64_t)(((np - 1) * ZY_BYTES) >> 4),
                           idesc0 | ((uint32_t)(ZBN >> 3) << 17), 0u);
+                    z_mma3(d, xd, yd, idesc);
                 } else {
-                    z_mma(d, xd, yd, idesc, 1u);                    // all its groups are running
+                    z_mma4(d, xd, yd, idesc, 1u);                   // all its groups are running
                 }
-#pragma unroll
-                for (int kk = 1; kk < ZKB / 32; ++kk) z_mma(d, xd + 2 * kk, yd + 2 * kk, idesc, 1u);
-                z_commit(xempty + xst);
-                if (++xst == ZXS) { xst = 0; xph ^= 1; }
             }
+        z_commit(xempty + xst);
+        if (++xst == ZXS) { xst = 0; xph ^= 1; }
     }
     return true;
 }
@@ -384,11 +399,12 @@ __device__ __forceinline__ bool z_issue_kblock(int kb, uint64_t xdesc_base, uint
 // scale, for FP32 outputs: with 8 planes the truncation, which is relative to the operand
 // tile's largest entry, cost 50x in the factor's backward error at eps_high = 1e-9).
 //   warp 0  TMA producer: per source and 128-byte K block, the SU Y planes of the block's ZBN
-//           columns (back to back, one stage of the Y ring) and the SU X planes (one stage
-//           each of the X ring), in the interleaved plane order;
-//   warp 1  MMA issuer: per X plane s, one tcgen05.mma with N = ZBN (SU - s) multiplies it by
-//           all its partners Y_0 .. Y_{SU-1-s} at once; column block t lands on accumulator
-//           group s + t, so the grouping by weight comes from the TMEM address;
+//           columns (back to back, one stage of the Y ring) and the SU X planes (two per stage
+//           of the X ring), in the interleaved plane order;
+//   warp 1  MMA issuer: per X plane s, one tcgen05.mma per 32-byte K step with N = ZBN (SU - s)
+//           multiplies it by all its partners Y_0 .. Y_{SU-1-s} at once (the four K steps in one
+//           asm block); column block t lands on accumulator group s + t, so the grouping by
+//           weight comes from the TMEM address;
 //   warps 2-5 drain: the SU group sums of a source leave TMEM (exact FP32 integers), are
 //           recombined by int64 Horner steps and added, scaled by 2^(e_x + e_y), to FP64
 //           running sums; C is written once per item.
@@ -412,11 +428,11 @@ template <int SU, bool SKIP, class Args>
 __global__ void __launch_bounds__(ZTHREADS, 1)
 k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
         const __grid_constant__ Args args) {
-    static_assert(SU <= ZS && ZPG <= ZXS, "an issue round waits for ZPG stages at once");
+    static_assert(SU <= ZS, "at most 14 digit planes");
     extern __shared__ __align__(1024) uint8_t zsmem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(zsmem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *xbuf = smem;                             // ZXS x 16 KB
-    uint8_t *ybuf = smem + ZXS * ZX_BYTES;            // ZYS x (SU x ZBN rows x 128 B)
+    uint8_t *ybuf = smem + ZXS * ZXSTAGE;             // ZYS x (SU x ZBN rows x 128 B)
     uint64_t *xfull = reinterpret_cast<uint64_t *>(ybuf + ZYS * ZYSET);
     uint64_t *xempty = xfull + ZXS;
     uint64_t *yfull = xempty + ZXS;
@@ -485,11 +501,15 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                                   yfull + yst);
                         ++issued_y;
                         if (++yst == ZYS) { yst = 0; yph ^= 1; }
-                        for (int i = 0; i < sx; ++i) {
-                            const int s = SKIP ? plane_at(i, sx, sy, zs.su, kb) : plane_order<SU>(i);
+                        for (int i0 = 0; i0 < sx; i0 += ZXP) {
                             if (!z_wait(xempty + xst, xph, abort_flag, lim)) { ok = false; break; }
-                            z_expect(xfull + xst, ZX_BYTES);
-                            z_tma(xbuf + xst * ZX_BYTES, &mapX, kb * ZKB, (xt * ZS + s) * b + it.bm * ZBM, xfull + xst);
+                            const int cnt = sx - i0 < ZXP ? sx - i0 : ZXP;
+                            z_expect(xfull + xst, (uint32_t)(cnt * ZX_BYTES));
+                            for (int h = 0; h < cnt; ++h) {
+                                const int s = SKIP ? plane_at(i0 + h, sx, sy, zs.su, kb) : plane_order<SU>(i0 + h);
+                                z_tma(xbuf + xst * ZXSTAGE + h * ZX_BYTES, &mapX, kb * ZKB, (xt * ZS + s) * b + it.bm * ZBM,
+                                      xfull + xst);
+                            }
                             ++issued_x;
                             if (++xst == ZXS) { xst = 0; xph ^= 1; }
                         }
@@ -540,39 +560,28 @@ k_zgemm(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtens
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint64_t yd = ydesc_base + (uint64_t)((yst * ZYSET) >> 4);
                         if constexpr (!SKIP) {
-                            // planes in groups of ZPG: one wait-and-fence round per group keeps the
-                            // MMA queue fed across the issue gaps (pairs: +30 %, measured)
+                            // planes in stages of ZXP: one wait, one fence and one commit per stage
 #pragma unroll
-                            for (int i0 = 0; i0 < SU; i0 += ZPG) {
-                                const int cnt = (SU - i0) < ZPG ? (SU - i0) : ZPG;
-                                int st = xst, ph = xph;
-                                bool ready = true;
-#pragma unroll
-                                for (int h = 0; h < ZPG; ++h)
-                                    if (h < cnt) {
-                                        ready = ready && z_wait(xfull + st, ph, abort_flag, lim);
-                                        if (++st == ZXS) { st = 0; ph ^= 1; }
-                                    }
-                                if (!ready) {
+                            for (int i0 = 0; i0 < SU; i0 += ZXP) {
+                                if (!z_wait(xfull + xst, xph, abort_flag, lim)) {
                                     ok = false;
                                     break;
                                 }
                                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                                const uint64_t xsd = xdesc_base + (uint64_t)((xst * ZXSTAGE) >> 4);
 #pragma unroll
-                                for (int h = 0; h < ZPG; ++h)
-                                    if (h < cnt) {
+                                for (int h = 0; h < ZXP; ++h)
+                                    if (i0 + h < SU) {
                                         const int s = plane_order<SU>(i0 + h);
-                                        const uint64_t xd = xdesc_base + (uint64_t)((xst * ZX_BYTES) >> 4);
+                                        const uint64_t xd = xsd + (uint64_t)((h * ZX_BYTES) >> 4);
                                         const uint32_t idesc = idesc0 | ((uint32_t)(((SU - s) * ZBN) >> 3) << 17);
                                         const uint32_t d = dbase + (uint32_t)(s * ZBN);
                                         // plane 0 comes first in every K block and covers all groups,
                                         // so it alone starts the accumulators of a source tile
-                                        z_mma(d, xd, yd, idesc, (kb > 0 || i0 + h > 0) ? 1u : 0u);
-#pragma unroll
-                                        for (int kk = 1; kk < ZKB / 32; ++kk) z_mma(d, xd + 2 * kk, yd + 2 * kk, idesc, 1u);
-                                        z_commit(xempty + xst);
-                                        if (++xst == ZXS) { xst = 0; xph ^= 1; }
+                                        z_mma4(d, xd, yd, idesc, (kb > 0 || i0 + h > 0) ? 1u : 0u);
                                     }
+                                z_commit(xempty + xst);
+                                if (++xst == ZXS) { xst = 0; xph ^= 1; }
                             }
                         } else {
                             // dispatch on the source's plane budget and plane counts (z_shape's values)
@@ -798,7 +807,7 @@ int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_ro
     return make_pool_map(map, pool, rows / b, b, 1, box_rows);
 }
 
-size_t zgemm_smem_bytes() { return (size_t)ZXS * ZX_BYTES + ZYS * ZYSET + 1024 + 256; }
+size_t zgemm_smem_bytes() { return (size_t)ZXS * ZXSTAGE + ZYS * ZYSET + 1024 + 256; }
 
 static int sm_count() {            // per device, cached
     static std::atomic<int> cache[64];

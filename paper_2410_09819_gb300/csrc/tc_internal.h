@@ -174,7 +174,7 @@ void launch_tile_sumsq(const double *A, int nt, int b, int64_t n, double *out, c
 // tiles t0 .. t0+count-1 of the packed layout, the first of them at A_first
 void launch_tile_sumsq_range(const double *A_first, int t0, int count, int b, int64_t n, double *out, cudaStream_t s);
 
-// Emulated-FP64 update of one 128 x 32 block of an FP64 output tile (k_ozaki.cu).
+// Emulated-FP64 update of one 128 x Z_BN block of an FP64 or FP32 output tile (k_ozaki.cu).
 struct ZItem {
     double *C;
     int xoff, yoff;
@@ -256,6 +256,7 @@ int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_ro
 
 // ------------------------------------------------------------------ launchers (k_mxp.cu)
 int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows);
+int make_pool_map_k(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows, int box_k_bytes);
 size_t qgemm_smem_bytes();
 void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                   const CUtensorMap &b1, const QItem *items, int nitems, const int *slot, const int *exps,
