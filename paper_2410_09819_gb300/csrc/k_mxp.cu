@@ -545,6 +545,17 @@ int make_pool_map_k(CUtensorMap *map, void *pool, int64_t nslots, int b, int esi
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : (int)r;
 }
+int make_plane_map3(CUtensorMap *map, void *pool, int64_t nplanes, int b, int box_rows, int depth) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return -1;
+    cuuint64_t dims[3] = {(cuuint64_t)b, (cuuint64_t)b, (cuuint64_t)nplanes};
+    cuuint64_t strides[2] = {(cuuint64_t)b, (cuuint64_t)b * b};
+    cuuint32_t box[3] = {128, (cuuint32_t)box_rows, (cuuint32_t)depth};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, pool, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : (int)r;
+}
 int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows) {
     return make_pool_map_k(map, pool, nslots, b, esize, box_rows, QKB);
 }

@@ -54,6 +54,9 @@ struct Plan {
     std::vector<LEntry> lentries;
     std::vector<ZItem> zitems, zitems32, zinv, zinvc, zref;
     bool inv_trsm = false, inv_refine = false;
+    // columns of the update work items (zitems, zitems32): 128 x Z64_BN blocks for the
+    // mixed-precision kernel when any matrix has a mixed map, else 128 x Z_BN
+    int zwidth = Z_BN;
     std::vector<int> dtiles;
     std::vector<ColPlan> cols;
     int64_t Ttot = 0;
@@ -79,12 +82,12 @@ inline int stored_planes(const MatDesc &M, int i, int j) {
 // tile instead of nbn * nbm / 152 times for X with row-block-fastest runs).
 constexpr int kItemRowBlocks = 4;
 template <class F>
-void for_tile_items(int b, bool lower_only, F &&emit) {
-    const int nbm = b / 128, nbn = b / Z_BN;
+void for_tile_items(int b, bool lower_only, F &&emit, int width = Z_BN) {
+    const int nbm = b / 128, nbn = b / width;
     for (int bm0 = 0; bm0 < nbm; bm0 += kItemRowBlocks)
         for (int bn = 0; bn < nbn; ++bn)
             for (int bm = bm0; bm < std::min(nbm, bm0 + kItemRowBlocks); ++bm)
-                if (!lower_only || bm * 128 + 127 >= bn * Z_BN) emit(bm, bn);
+                if (!lower_only || bm * 128 + 127 >= bn * width) emit(bm, bn);
 }
 
 // Plane pairs (s, t), s < sx, t < sy, s + t < su, that one emulated product multiplies.
@@ -133,6 +136,9 @@ Plan build_plan(tc_handle h, double *W, int *status) {
     }
     P.cols.resize(P.ntmax);
     const bool zmode = h->cfg.fp64_mode >= 1;
+    for (const MatDesc &M : h->mats)
+        if (M.mixed && zmode) P.zwidth = Z64_BN;
+    const int zw = P.zwidth;
     // explicit-inverse TRSM (fp64_mode 2, single matrix: one scratch).  Mixed precision takes
     // L_mk = C_mk L_kk^{-T} as it is (its error, kappa(L_kk) u, is far below the accuracy level
     // of a mixed-precision factorization); an all-FP64 factorization adds one refinement step
@@ -171,7 +177,7 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                         const int ct = (int)(M.tile0 + tidx(m, k));
                         for_tile_items(b, false, [&](int bm, int bn) {
                             P.zitems32.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn, ct});
-                        });
+                        }, zw);
                         P.update_flops[TC_FP32] += 2.0 * (double)b * b * K;
                         for (int nn = 0; nn < k; ++nn)
                             P.tensor_flops[TC_FP32] += 2.0 * (double)b * b * b *
@@ -188,10 +194,10 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                         for_tile_items(b, m == k, [&](int bm, int bn) {
                             P.zitems.push_back({Cp, xo, yo, (uint16_t)bm, (uint16_t)bn, ct});
                             ++items;
-                        });
+                        }, zw);
                         P.update_flops[TC_FP64] += (m == k ? 1.0 : 2.0) * (double)b * b * K;
                         for (int nn = 0; nn < k; ++nn)
-                            P.tensor_flops[TC_FP64] += 2.0 * 128.0 * Z_BN * b * items *
+                            P.tensor_flops[TC_FP64] += 2.0 * 128.0 * zw * b * items *
                                                        plane_pairs(stored_planes(M, m, nn), stored_planes(M, k, nn), 14);
                         continue;
                     }
@@ -586,6 +592,8 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
         if (make_digit_map(&h->map_zx, h->dpool.p, Tt * 14 * h->b, h->b, 128) ||
             make_digit_map(&h->map_zy, h->dpool.p, Tt * 14 * h->b, h->b, Z_BN))
             return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the digit planes");
+        if (P.zwidth == Z64_BN && make_zgemm64_maps(&h->maps64, h->dpool.p, Tt * 14, h->b))
+            return set_err(h, TC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the digit planes (3D maps)");
     }
     D.mixed = M != nullptr;
     if (M && (rc = setup_mxp(h, *M, D.mx))) return rc;
@@ -648,16 +656,24 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
         }
         if (C.nz) {
             const int sp = spans ? span_begin(h, CAT_UPD64) : -1;
-            launch_zgemm(h->map_zx, h->map_zy, D.zitems + C.z0, C.nz, D.zexps, k, b, status + 1, h->s, 14, 0,
-                         D.zplanes ? &zp64 : nullptr, wait_limit_ns(h), wait_test(h));
+            if (P.zwidth == Z64_BN)
+                launch_zgemm64(h->maps64, D.zitems + C.z0, C.nz, D.zexps, k, b, status + 1, h->s, zp64, 0,
+                               wait_limit_ns(h), wait_test(h));
+            else
+                launch_zgemm(h->map_zx, h->map_zy, D.zitems + C.z0, C.nz, D.zexps, k, b, status + 1, h->s, 14, 0,
+                             D.zplanes ? &zp64 : nullptr, wait_limit_ns(h), wait_test(h));
             span_end(h, sp);
             CK_LAUNCH();
             ++h->upd_launches[TC_FP64];
         }
         if (C.ny) {
             const int sp = spans ? span_begin(h, CAT_UPD32) : -1;
-            launch_zgemm(h->map_zx, h->map_zy, D.zitems32 + C.y0, C.ny, D.zexps, k, b, status + 1, h->s, 10, 0,
-                         D.zplanes ? &zp32 : nullptr, wait_limit_ns(h), wait_test(h));
+            if (P.zwidth == Z64_BN)
+                launch_zgemm64(h->maps64, D.zitems32 + C.y0, C.ny, D.zexps, k, b, status + 1, h->s, zp32, 0,
+                               wait_limit_ns(h), wait_test(h));
+            else
+                launch_zgemm(h->map_zx, h->map_zy, D.zitems32 + C.y0, C.ny, D.zexps, k, b, status + 1, h->s, 10, 0,
+                             D.zplanes ? &zp32 : nullptr, wait_limit_ns(h), wait_test(h));
             span_end(h, sp);
             CK_LAUNCH();
             ++h->upd_launches[TC_FP32];
@@ -804,7 +820,7 @@ void fill_stats(tc_handle h, const Plan &P, const MxpPlan *M, tc_stats *stats, d
     for (int p = 0; p < 4; ++p) stats->tensor_flops[p] = P.tensor_flops[p];
     if (h->pairs_dev) {
         // mixed precision: the plane pairs the update kernels counted as they issued them
-        const double per_pair = 2.0 * 128.0 * Z_BN * h->b;
+        const double per_pair = 2.0 * 128.0 * P.zwidth * h->b;
         stats->tensor_flops[TC_FP64] = per_pair * (double)h->pairs_exec[0];
         stats->tensor_flops[TC_FP32] = per_pair * (double)h->pairs_exec[1];
     }

@@ -57,6 +57,7 @@ struct tc_handle_s {
     DevBuf dpool, ztab, invbuf;
     DevBuf stab;       // grouped batched-solve task tables
     CUtensorMap map_zx{}, map_zy{};
+    tc::Z64Maps maps64{};                // 3D digit-plane maps of the mixed-precision update kernel
     // matrices of the last (batched) factorization
     std::vector<MatDesc> mats;
     std::vector<double> logdets;

@@ -186,6 +186,13 @@ struct ZItem {
 // given by digit-pool slot (ZG_MAX tiles and ZK_MAX sources at most per launch).
 constexpr int ZG_MAX = 16, ZK_MAX = 256;
 constexpr int Z_BN = 16;     // columns of one emulated-update work item (rows: 128)
+constexpr int Z64_BN = 64;   // columns of a work item of the mixed-precision update kernel (k_ozaki64.cu)
+// 3D maps over the digit-plane pool (K bytes, rows of a plane, plane index) for k_zgemm64:
+// x[d-1] boxes of d X planes (128 rows), y[d-1] boxes of d Y planes (64 rows)
+struct Z64Maps {
+    CUtensorMap x[2];
+    CUtensorMap y[5];
+};
 // Digit planes of the correction product R L^{-T} of the refined TRSM.  Truncation is
 // relative to each operand's largest entry, so a product's relative error is amplified by
 // A ~ K max|C| max|L^{-1}| / |X| (cancellation; A ~ 200 on Matern tiles).  X0 = C L^{-T} and
@@ -257,6 +264,13 @@ int make_digit_map(CUtensorMap *map, void *pool, int64_t rows, int b, int box_ro
 // ------------------------------------------------------------------ launchers (k_mxp.cu)
 int make_pool_map(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows);
 int make_pool_map_k(CUtensorMap *map, void *pool, int64_t nslots, int b, int esize, int box_rows, int box_k_bytes);
+// 3D map over nplanes byte planes of b x b (row-major, K innermost): box 128 bytes x box_rows x depth
+int make_plane_map3(CUtensorMap *map, void *pool, int64_t nplanes, int b, int box_rows, int depth);
+int make_zgemm64_maps(Z64Maps *m, void *pool, int64_t nplanes, int b);
+// Mixed-precision digit-plane updates over 128 x Z64_BN items (k_ozaki64.cu); mixed.rref is the
+// reference plane count of the outputs (14 FP64, 10 FP32)
+void launch_zgemm64(const Z64Maps &maps, const ZItem *items, int nitems, const int *exps, int k, int b, int *err,
+                    cudaStream_t s, const ZPlanes &mixed, int assign, unsigned long long limit_ns, int stall);
 size_t qgemm_smem_bytes();
 void launch_qgemm(int kind, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                   const CUtensorMap &b1, const QItem *items, int nitems, const int *slot, const int *exps,

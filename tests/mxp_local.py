@@ -131,7 +131,11 @@ def check_factor(A, Lg, b, pm, engine, trsm):
                     ex, ey = digit_exp(np.abs(xo).max()), digit_exp(np.abs(yo).max())
                     su = plane_budget(eo, ex, ey, rref) if mixed else rref
                     dC += b * plane_truncation(su) * 2.0 ** (ex + ey)
-                dC += (j + 1) * 2.0 ** -52 * absprod            # FP64 running sums of the products
+                # FP64 running sums of the products: one rounding per accumulator pass of a
+                # source (two for the FP64 path's 128 x 16 kernel, at most four passes for the
+                # mixed-precision 128 x 64 kernel) and the final subtraction
+                rounds = 4 if mixed else 2
+                dC += (rounds * j + 2) * U64 * absprod
             elif q == FP64:                                     # DFMA
                 dC += (K + 2) * U64 * absprod
             elif q == FP32:                                     # TF32 x 3, FP32 accumulation
