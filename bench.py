@@ -215,9 +215,10 @@ KERNELS = {0: ("k_zgemm<14> (FP64 outputs, E4M3 digit planes)", "e4m3", 2.0),
            3: ("k_qgemm<3> (FP8 E4M3 outputs)", "e4m3", 2.0)}
 
 
-def committed_profile(tag: str) -> dict:
+def committed_profile(tag: str, source: str = "k_ozaki.cu") -> dict:
     """The committed ncu summary profiles/<tag>.md of the dominant kernel: the kernel-source
-    sha it was captured at (compared with the current source) and its per-launch figures."""
+    sha it was captured at (compared with the current sha of its source file) and its
+    per-launch figures."""
     path = os.path.join(ROOT, "profiles", f"{tag}.md")
     try:
         text = open(path).read()
@@ -225,7 +226,7 @@ def committed_profile(tag: str) -> dict:
         return {"file": f"profiles/{tag}.md", "present": False}
     m = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
     out = {"file": f"profiles/{tag}.md", "present": True, "kernel_source_sha": m.group(1) if m else None}
-    out["matches_current_source"] = bool(m) and m.group(1) == kernel_source_sha()
+    out["matches_current_source"] = bool(m) and m.group(1) == kernel_source_sha(source)
     for key in ("dram_bytes_per_launch", "l2_to_sm_bytes_per_launch", "tensor_active_pct", "launch_ms"):
         mm = re.search(rf"{key}:\s*([0-9.eE+-]+)", text)
         if mm:
@@ -244,7 +245,11 @@ def probed_peaks() -> dict:
         return {}
 
 
-def tensor_rooflines(st, t_step, fp32_updates):
+MIXED_KERNELS = {0: "k_zgemm64 (FP64 outputs of a mixed map, 128 x 64 items, E4M3 digit planes)",
+                 1: "k_zgemm64 (FP32 outputs of a mixed map, 128 x 64 items, E4M3 digit planes)"}
+
+
+def tensor_rooflines(st, t_step, fp32_updates, mixed=False):
     """Per-precision tensor-core rooflines of the updates: executed tensor flops
     (tc_stats.tensor_flops) over the CUDA-event time of that precision's update launches,
     against the dtype's dense peak = measured BF16 (sustained: the kernels run inside a
@@ -257,6 +262,8 @@ def tensor_rooflines(st, t_step, fp32_updates):
         if ms <= 0 or st.tensor_flops[p] <= 0:
             continue
         name, dt, ratio = KERNELS[p]
+        if mixed and p in MIXED_KERNELS:
+            name = MIXED_KERNELS[p]
         if p == 1 and fp32_updates:
             name, dt, ratio = "k_qgemm<1> (FP32 outputs, TF32 x 3)", "tf32", 0.5
         executed = st.tensor_flops[p] / (ms / 1e3) / 1e12
@@ -359,7 +366,7 @@ def run_ours(args, ws, rank, local):
     # rooflines: per output precision on the tensor cores (the FP64 outputs' k_zgemm is the
     # dominant kernel), or the FP64 pipe for the DFMA engine
     pk, pk_kind = peaks()
-    by_prec = tensor_rooflines(st, t_step, args.fp32_updates) if args.fp64_mode >= 1 else []
+    by_prec = tensor_rooflines(st, t_step, args.fp32_updates, w.mixed) if args.fp64_mode >= 1 else []
     if args.fp64_mode >= 1 and by_prec:
         roofline = dict(by_prec[0])
         roofline["traffic"] = None
@@ -372,8 +379,10 @@ def run_ours(args, ws, rank, local):
                     "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
                     "peak_source": f"ALU: 152 SMs x 4 FP64 flop/clk x {pk_kind} max SM clock",
                     "share_of_step": (upd_ms / 1e3) / t if t > 0 else None}
-    roofline["kernel_source_sha"] = kernel_source_sha()
-    roofline["profile"] = committed_profile("zgemm_mxp4_n32768" if w.mixed else "zgemm_fp64_n16384")
+    ksrc = "k_ozaki64.cu" if w.mixed else "k_ozaki.cu"
+    roofline["kernel_source"] = f"csrc/{ksrc}"
+    roofline["kernel_source_sha"] = kernel_source_sha(ksrc)
+    roofline["profile"] = committed_profile("zgemm_mxp4_n32768" if w.mixed else "zgemm_fp64_n16384", ksrc)
 
     # accuracy of a mixed-precision factorization, outside the timed region: random-probe
     # backward error of the factor, Eq. 1 with the plain and the refined quadratic form, Eq. 3
@@ -509,7 +518,7 @@ def run_ours(args, ws, rank, local):
                        "update_tflops_by_prec": [(st.update_flops[p] / st.t_update_ms[p] / 1e9) if st.t_update_ms[p] else None
                                                  for p in range(4)],
                        "tensor_flops_by_prec": list(st.tensor_flops),
-                       "tiles_by_prec": list(st.tiles), "kernel_source_sha": kernel_source_sha(),
+                       "tiles_by_prec": list(st.tiles), "kernel_source_sha": kernel_source_sha(ksrc),
                        "step_ms": step_ms, "step_ms_best": min(step_ms), "step_ms_median": float(np.median(step_ms)),
                        "factor_ms_steps": factor_ms,
                        "tflops_factor_only_best": flops / (min(factor_ms) / 1e3) / 1e12},
