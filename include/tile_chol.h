@@ -290,6 +290,15 @@ int tile_chol_loglik_refined(tc_handle h, const double *y, int max_refine, doubl
                              double *loglik_out, double *berr_out);
 
 /*
+ * Eq. 1 with the quadratic form y^T Sigma^{-1} y = y^T x from a solution the caller already
+ * has (x from tile_chol_solve of the same right-hand side y on the current factor: the
+ * likelihood of Section III-D needs one solve, and this evaluates it without a second one);
+ * log|A| comes from the factor.  y, x: n doubles each, host or device.  Returns TC_ERR_STATE
+ * without a successful factorization, TC_ERR_ARG for null pointers.
+ */
+int tile_chol_loglik_solved(tc_handle h, const double *y, const double *x, double *loglik_out);
+
+/*
  * Copy the last factor out as FP64 values of the stored tiles (tile layout; upper
  * triangles of diagonal tiles and padding are written as 0).  L_tiles: host or device.
  */

@@ -1351,6 +1351,38 @@ int tile_chol_loglik_refined(tc_handle h, const double *y, int max_refine, doubl
     return TC_OK;
 }
 
+int tile_chol_loglik_solved(tc_handle h, const double *y, const double *x, double *loglik_out) {
+    if (!h || !y || !x || !loglik_out) return TC_ERR_ARG;
+    if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");
+    CK(cudaSetDevice(h->device));
+    const int64_t n = h->n;
+    const double *yd = y, *xd = x;
+    DevBuf tmp;
+    if (!on_device(y) || !on_device(x)) {
+        const int rc = ensure(h, tmp, (size_t)2 * n * sizeof(double));
+        if (rc) return rc;
+        double *t = static_cast<double *>(tmp.p);
+        if (!on_device(y)) {
+            CK(cudaMemcpyAsync(t, y, n * sizeof(double), cudaMemcpyDefault, h->s));
+            yd = t;
+        }
+        if (!on_device(x)) {
+            CK(cudaMemcpyAsync(t + n, x, n * sizeof(double), cudaMemcpyDefault, h->s));
+            xd = t + n;
+        }
+    }
+    double *sc = static_cast<double *>(h->scratch.p);
+    launch_dot(yd, xd, n, sc, h->s);
+    CK_LAUNCH();
+    double quad = 0.0;
+    CK(cudaMemcpyAsync(&quad, sc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    release(tmp);
+    const double two_pi = 6.283185307179586476925286766559;
+    *loglik_out = -0.5 * (double)n * std::log(two_pi) - 0.5 * h->logdet - 0.5 * quad;
+    return TC_OK;
+}
+
 static int copy_factor(tc_handle h, const double *src, int64_t n, int nt, double *L_tiles);
 
 int tile_chol_get_factor(tc_handle h, double *L_tiles) {

@@ -16,7 +16,7 @@ __all__ = [
     "TC_FP64", "TC_FP32", "TC_FP16", "TC_FP8", "TC_OK", "TileCholError", "tc_config", "tc_stats",
     "lib", "tc_config_default", "tc_create", "tc_destroy", "tc_last_error", "tc_matern_tiles",
     "tile_chol_precision_map", "tile_chol_factor", "tile_chol_factor_ooc", "tile_chol_solve", "tile_chol_logdet",
-    "tile_chol_loglik", "tile_chol_loglik_refined", "tile_chol_get_factor", "tile_chol_precision_map_noalloc", "tile_chol_factor_batched",
+    "tile_chol_loglik", "tile_chol_loglik_refined", "tile_chol_loglik_solved", "tile_chol_get_factor", "tile_chol_precision_map_noalloc", "tile_chol_factor_batched",
     "tile_chol_solve_batched", "tile_chol_loglik_batched", "Handle", "ntiles",
     "tile_count", "tc_set_wait_limit", "tile_chol_get_factor_batched",
 ]
@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "tile_chol_get_factor": (ci, [H, vp]),
         "tile_chol_get_factor_batched": (ci, [H, ci, vp]),
         "tile_chol_loglik_refined": (ci, [H, vp, ci, cd, ctypes.POINTER(cd), ctypes.POINTER(cd)]),
+        "tile_chol_loglik_solved": (ci, [H, vp, vp, ctypes.POINTER(cd)]),
         "tile_chol_precision_map_noalloc": (ci, [i64, ci, vp, cd, ci, ci, vp, vp]),
         "tile_chol_factor_batched": (ci, [H, ci, vp, ci, vp, vp, vp, vp, ctypes.POINTER(tc_stats)]),
         "tile_chol_solve_batched": (ci, [H, ci, vp, vp, ci, cd, vp, ctypes.POINTER(tc_stats)]),
@@ -247,6 +248,15 @@ def tile_chol_loglik_refined(h, y, max_refine=5, target_berr=1e-14):
     _need(y, "float64", None, "y")
     _check(h, lib().tile_chol_loglik_refined(h, _ptr(y), max_refine, target_berr, ctypes.byref(out), ctypes.byref(be)))
     return out.value, be.value
+
+
+def tile_chol_loglik_solved(h, y, x) -> float:
+    """Eq. 1 with y^T Sigma^{-1} y = y^T x, x the solution of Sigma x = y from tile_chol_solve."""
+    out = ctypes.c_double()
+    _need(y, "float64", None, "y")
+    _need(x, "float64", None, "x")
+    _check(h, lib().tile_chol_loglik_solved(h, _ptr(y), _ptr(x), ctypes.byref(out)))
+    return out.value
 
 
 def tile_chol_get_factor(h, L_tiles) -> None:

@@ -180,3 +180,31 @@ def test_refined_loglik_recovers_fp64_quadratic_form(H):
     assert abs(quad(ll_ref, ld) - q64) <= 1e-10 * abs(q64)
     assert berr <= 1e-14
     assert abs(quad(ll_plain, ld) - q64) > abs(quad(ll_ref, ld) - q64)
+
+
+def test_loglik_from_solution_matches_refined_and_oracle(H):
+    """Eq. 1 from an existing refined solve (tile_chol_loglik_solved, host and device buffers)
+    equals the refined log-likelihood and the oracle's FP64 quadratic form."""
+    import torch
+    n, b = 1024, 128
+    pts = inputs.uniform_points(n, 31, morton=True)
+    A = oracle.matern(pts, 1.0, 0.02, 0.5, 1e-4)
+    nt = n // b
+    At = to_dev(pack_padded(A, b))
+    pm = np.empty(nt * nt, dtype=np.uint8)
+    tc.tile_chol_precision_map(H.h, n, b, At, 1e-5, 1, 4, pm)
+    assert tc.tile_chol_factor(H.h, n, b, At, pm) == 0
+    y = inputs.gaussian(n, 1, seed=12)[:, 0].copy()
+    yd = to_dev(y)
+    xd = torch.empty_like(yd)
+    tc.tile_chol_solve(H.h, 1, yd, n, xd, n, 10, 1e-14, None)
+    ll_dev = tc.tile_chol_loglik_solved(H.h, yd, xd)
+    ll_host = tc.tile_chol_loglik_solved(H.h, y, xd.cpu().numpy())
+    ll_ref, _ = tc.tile_chol_loglik_refined(H.h, yd, 10, 1e-14)
+    assert ll_dev == ll_host
+    assert abs(ll_dev - ll_ref) <= 1e-13 * abs(ll_ref)
+    ld = tc.tile_chol_logdet(H.h)
+    Lo = oracle.cholesky(A)
+    quad = lambda ll, l: -2.0 * (ll + 0.5 * n * math.log(2 * math.pi) + 0.5 * l)  # noqa: E731
+    q64 = quad(oracle.loglik(Lo, y), oracle.logdet(Lo))
+    assert abs(quad(ll_dev, ld) - q64) <= 1e-10 * abs(q64)
