@@ -59,8 +59,8 @@ struct Args {
     const ZItem *items;
     int nitems;
     const int *exps;
-    const uint8_t *planes;          // leading planes each digit slot can have non-zero
-    const double *oamax;            // input amax of every output tile
+    const uint8_t *planes;          // leading planes each digit slot can have non-zero, or null (all 14)
+    const double *oamax;            // input amax of every output tile, or null (rref planes for every source)
     int rref, margin;               // pair budget relative to the output's scale
     unsigned long long *pair_count; // plane pairs multiplied (added at the end)
     int k, b;
@@ -77,12 +77,17 @@ struct Args {
 struct Shape {
     int sx, sy, su;
 };
+// Without output scales (oamax null) every source runs on rref planes; without a plane table
+// (planes null) every operand may use all 14.
 __device__ __forceinline__ Shape shape(const Args &a, int eo, int xt, int yt) {
-    const int d = eo - a.exps[xt] - a.exps[yt] - 4 * a.margin;
-    const int j = d >= 0 ? d / 4 : -((3 - d) / 4);            // floor(d / 4)
-    int su = a.rref - j;
+    int su = a.rref;
+    if (a.oamax) {
+        const int d = eo - a.exps[xt] - a.exps[yt] - 4 * a.margin;
+        const int j = d >= 0 ? d / 4 : -((3 - d) / 4);        // floor(d / 4)
+        su = a.rref - j;
+    }
     su = su < 1 ? 1 : (su > ZS ? ZS : su);
-    int sx = a.planes[xt], sy = a.planes[yt];
+    int sx = a.planes ? a.planes[xt] : ZS, sy = a.planes ? a.planes[yt] : ZS;
     sx = sx < su ? sx : su;
     sy = sy < su ? sy : su;
     return {sx, sy, su};
@@ -221,7 +226,7 @@ k_zgemm64(const __grid_constant__ Z64Maps maps, const __grid_constant__ A args) 
             };
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const ZItem it = args.items[item];
-                const int eo = z_digit_exp(args.oamax[it.ct]);
+                const int eo = args.oamax ? z_digit_exp(args.oamax[it.ct]) : 0;
                 for (int n = 0; n < k && ok; ++n) {
                     const int xt = it.xoff + n, yt = it.yoff + n;
                     const Shape zs = shape(args, eo, xt, yt);
@@ -265,7 +270,7 @@ k_zgemm64(const __grid_constant__ Z64Maps maps, const __grid_constant__ A args) 
             if (args.stall && !z_wait(done, 0, abort_flag, lim)) ok = false;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const ZItem it = args.items[item];
-                const int eo = z_digit_exp(args.oamax[it.ct]);
+                const int eo = args.oamax ? z_digit_exp(args.oamax[it.ct]) : 0;
                 for (int n = 0; n < k && ok; ++n) {
                     const Shape zs = shape(args, eo, it.xoff + n, it.yoff + n);
                     const int G = groups(zs), P = npass(G);
@@ -339,7 +344,7 @@ k_zgemm64(const __grid_constant__ Z64Maps maps, const __grid_constant__ A args) 
         int q = 0;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             const ZItem it = args.items[item];
-            const int eo = z_digit_exp(args.oamax[it.ct]);
+            const int eo = args.oamax ? z_digit_exp(args.oamax[it.ct]) : 0;
             double run[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) run[j] = 0.0;

@@ -241,13 +241,14 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 double *Cp = T(M, m, k);
                 double *Cs = P.inv_refine ? inv_scratch + (int64_t)(m - k) * bb : nullptr;
                 const int sx = (int)(M.tile0 + tidx(m, k));
+                // mixed maps: the products run on the 128 x 64 kernel (fixed plane counts)
                 for_tile_items(b, false, [&](int bm, int bn) {
                     P.zinv.push_back({Cp, sx, sinv, (uint16_t)bm, (uint16_t)bn});
                     if (P.inv_refine) {
                         P.zinvc.push_back({Cs, sx, sinv, (uint16_t)bm, (uint16_t)bn});
                         P.zref.push_back({Cp, sx, sl, (uint16_t)bm, (uint16_t)bn});
                     }
-                });
+                }, P.inv_refine ? Z_BN : zw);
                 C.nvp[p] += (int)(P.zinv.size() - before);
             }
         }
@@ -724,8 +725,19 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
                 // the product's truncation stays below the rounding to each stored precision
                 int off = C.v0;
                 for (int p = 0; p < 4; ++p) {
-                    launch_zgemm(h->map_zx, h->map_zy, D.zinv + off, C.nvp[p], D.zexps, 1, b, status + 1, h->s,
-                                 ZTRSM_PLANES[p], 1, nullptr, wait_limit_ns(h), wait_test(h));
+                    if (P.zwidth == Z64_BN) {
+                        ZPlanes fixed;                  // every source on the precision's plane count
+                        fixed.src_planes_tab = nullptr;
+                        fixed.out_amax = nullptr;
+                        fixed.rref = ZTRSM_PLANES[p];
+                        fixed.margin = 0;
+                        fixed.pair_count = nullptr;
+                        launch_zgemm64(h->maps64, D.zinv + off, C.nvp[p], D.zexps, 1, b, status + 1, h->s, fixed, 1,
+                                       wait_limit_ns(h), wait_test(h));
+                    } else {
+                        launch_zgemm(h->map_zx, h->map_zy, D.zinv + off, C.nvp[p], D.zexps, 1, b, status + 1, h->s,
+                                     ZTRSM_PLANES[p], 1, nullptr, wait_limit_ns(h), wait_test(h));
+                    }
                     CK_LAUNCH();
                     off += C.nvp[p];
                 }
