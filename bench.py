@@ -835,7 +835,7 @@ def run_batched(args, ws, rank, local):
     if rank == 0:
         line = common_line(ws, args, value, t, {
             "workload": "batched", "count": len(ns), "n_range": [min(ns), max(ns)], "tile": b,
-            "fp64_engine": {0: "FP64 pipe (DFMA, 64 x 64 blocks)", 2: "E4M3 digit planes (128 x 16 items)"}[mode],
+            "fp64_engine": {0: "FP64 pipe (DFMA, 64 x 64 blocks)", 2: "E4M3 digit planes (128 x 64 items, mixed maps)"}[mode],
             "autotune_s": {f"b={k[0]},fp64_mode={k[1]}": v for k, v in tune.items()}, "nugget": 1e-4,
             "eps_high": eps, "precision": "FP64 diagonal, FP16/FP8 off-diagonal where allowed, else FP64",
             "nrhs": nrhs, "l2": "total inputs larger than L2", "parallelism": f"replicas x{ws}",

@@ -612,16 +612,16 @@ void launch_tile_amax(const double *W, int b, const int *tiles, int ntiles, doub
     // one grid row per listed tile, at most 65535 rows per launch
     for (int t0 = 0; t0 < ntiles; t0 += 65535) {
         const int nt = ntiles - t0 < 65535 ? ntiles - t0 : 65535;
-        k_tile_amax<<<dim3(64, nt), 256, 0, s>>>(W, b, tiles + t0, amax, alt ? alt + (int64_t)t0 * b * b : nullptr);
+        k_tile_amax<<<dim3(tile_ctas(nt), nt), 256, 0, s>>>(W, b, tiles + t0, amax, alt ? alt + (int64_t)t0 * b * b : nullptr);
     }
 }
 void launch_store_round(double *W, int b, const int *tiles, int ntiles, const uint8_t *prec, const double *amaxL,
                         double *amaxS, cudaStream_t s) {
-    if (ntiles > 0) k_store_round<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, prec, amaxL, amaxS);
+    if (ntiles > 0) k_store_round<<<dim3(tile_ctas(ntiles), ntiles), 256, 0, s>>>(W, b, tiles, prec, amaxL, amaxS);
 }
 void launch_make_copies(const double *W, int b, const CopyJob *jobs, int njobs, const double *amaxS, float *hi,
                         float *lo, __half *p16, uint8_t *p8, int *e16, int *e8, cudaStream_t s) {
-    if (njobs > 0) k_make_copies<<<dim3(64, njobs), 256, 0, s>>>(W, b, jobs, amaxS, hi, lo, p16, p8, e16, e8, CopyJob{});
+    if (njobs > 0) k_make_copies<<<dim3(tile_ctas(njobs), njobs), 256, 0, s>>>(W, b, jobs, amaxS, hi, lo, p16, p8, e16, e8, CopyJob{});
 }
 
 // ------------------------------------------------------------ out-of-core, one cache slot

@@ -728,7 +728,7 @@ static int sm_count() {            // per device, cached
 
 void launch_digits(const double *W, int b, const int *tiles, int ntiles, const double *amax, uint8_t *pool, int *exps,
                    cudaStream_t s, const double *alt) {
-    if (ntiles > 0) k_digits<<<dim3(64, ntiles), 256, 0, s>>>(W, b, tiles, amax, pool, exps, alt);
+    if (ntiles > 0) k_digits<<<dim3(tile_ctas(ntiles), ntiles), 256, 0, s>>>(W, b, tiles, amax, pool, exps, alt);
 }
 void launch_lower_only(double *T, int b, cudaStream_t s) { k_lower_only<<<64, 256, 0, s>>>(T, b); }
 __global__ void k_add_tile(double *dst, const double *src, int64_t count) {

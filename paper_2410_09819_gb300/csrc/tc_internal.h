@@ -185,6 +185,13 @@ struct ZItem {
 // One grouped out-of-core update launch: tiles C[t] -= sum_{n<k} X_{t,n} Y_n^T, the operands
 // given by digit-pool slot (ZG_MAX tiles and ZK_MAX sources at most per launch).
 constexpr int ZG_MAX = 16, ZK_MAX = 256;
+// CTAs (x dimension) per listed tile for the per-tile conversion kernels (grid-stride loops):
+// about two full waves of 256-thread CTAs over the 152 SMs whatever the number of tiles, at
+// least 64 per tile
+inline int tile_ctas(int ntiles) {
+    const int c = ntiles > 0 ? 2432 / ntiles : 64;
+    return c < 64 ? 64 : (c > 1024 ? 1024 : c);
+}
 constexpr int Z_BN = 16;     // columns of one emulated-update work item (rows: 128)
 constexpr int Z64_BN = 64;   // columns of a work item of the mixed-precision update kernel (k_ozaki64.cu)
 // 3D maps over the digit-plane pool (K bytes, rows of a plane, plane index) for k_zgemm64:
