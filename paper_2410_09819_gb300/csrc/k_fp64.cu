@@ -347,33 +347,37 @@ __device__ __forceinline__ void warp_tri64(double (*S)[65], double *blk, bool fo
 // Forward substitution with one diagonal tile, one right-hand side r (in place): per 64-row
 // block, the product with the solved part (256 threads, 4 partial sums per row, fixed order)
 // and the warp solve of the diagonal block.
-__device__ __forceinline__ void fwd_diag_body(const double *L, int ld, int b, double *r) {
+// T: the right-hand side's storage type (double, or float for the FP32 correction solves of a
+// refined batched solve); the arithmetic is FP64 either way.
+template <typename T>
+__device__ __forceinline__ void fwd_diag_body(const double *L, int ld, int b, T *r) {
     __shared__ double red[4][64];
     __shared__ double blk[64];
     __shared__ double S[64][65];
-    double *z = r;                       // solved in place (block barriers order the accesses)
+    T *z = r;                            // solved in place (block barriers order the accesses)
     const int tid = threadIdx.x;
     const int rr = tid & 63, part = tid >> 6;
     for (int jb = 0; jb < b / 64; ++jb) {
         double acc = 0.0;
-        for (int l = part; l < jb * 64; l += 4) acc = fma(L[(int64_t)l * ld + jb * 64 + rr], z[l], acc);
+        for (int l = part; l < jb * 64; l += 4) acc = fma(L[(int64_t)l * ld + jb * 64 + rr], (double)z[l], acc);
         red[part][rr] = acc;
         for (int idx = tid; idx < 4096; idx += 256) {
             const int lr = idx & 63, lc = idx >> 6;
             S[lr][lc] = (lr >= lc) ? L[(int64_t)(jb * 64 + lc) * ld + jb * 64 + lr] : 0.0;
         }
         __syncthreads();
-        if (tid < 64) blk[tid] = z[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+        if (tid < 64) blk[tid] = (double)z[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
         __syncthreads();
         if (tid < 32) warp_tri64(S, blk, true);
         __syncthreads();
-        if (tid < 64) z[jb * 64 + tid] = blk[tid];
+        if (tid < 64) z[jb * 64 + tid] = (T)blk[tid];
         __syncthreads();
     }
 }
 
 // Back substitution with one diagonal tile: L_jj^T x = z, one right-hand side (in place).
-__device__ __forceinline__ void bwd_diag_body(const double *L, int ld, int b, double *x) {
+template <typename T>
+__device__ __forceinline__ void bwd_diag_body(const double *L, int ld, int b, T *x) {
     __shared__ double S[64][65];
     __shared__ double red[4][64];
     __shared__ double blk[64];
@@ -384,18 +388,18 @@ __device__ __forceinline__ void bwd_diag_body(const double *L, int ld, int b, do
         // read along l (column-major L: contiguous in l for a fixed column)
         double acc = 0.0;
         const double *Lc = L + (int64_t)(jb * 64 + rr) * ld;
-        for (int l = (jb + 1) * 64 + part; l < b; l += 4) acc = fma(Lc[l], x[l], acc);
+        for (int l = (jb + 1) * 64 + part; l < b; l += 4) acc = fma(Lc[l], (double)x[l], acc);
         red[part][rr] = acc;
         for (int idx = tid; idx < 4096; idx += 256) {
             const int lr = idx & 63, lc = idx >> 6;
             S[lr][lc] = (lr >= lc) ? L[(int64_t)(jb * 64 + lc) * ld + jb * 64 + lr] : 0.0;
         }
         __syncthreads();
-        if (tid < 64) blk[tid] = x[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+        if (tid < 64) blk[tid] = (double)x[jb * 64 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
         __syncthreads();
         if (tid < 32) warp_tri64(S, blk, false);
         __syncthreads();
-        if (tid < 64) x[jb * 64 + tid] = blk[tid];
+        if (tid < 64) x[jb * 64 + tid] = (T)blk[tid];
         __syncthreads();
     }
 }
@@ -754,6 +758,100 @@ __global__ void __launch_bounds__(256) k_bwd_update_g(const SUpd *__restrict__ u
     part_reduce_sub(reinterpret_cast<double(*)[17]>(&S[0][0]), acc, nrhs, R + U.dst, U.ldr, 0);
 }
 
+// FP32 forms of the grouped substitution (the correction solves of a refined batched solve): the
+// factor tiles are read in FP64 and rounded to FP32 on load, products and sums run on the FP32
+// pipe (GB300 retires 64x more FP32 than FP64 operations per clock); the diagonal blocks keep
+// FP64 arithmetic on the FP32 vectors.  Iterative refinement with FP64 residuals takes the
+// result to FP64 accuracy: a correction needs only a few correct digits.
+template <int NQ>
+__device__ __forceinline__ void part_reduce_sub_f(float (*red)[17], const float (&acc)[NQ], int nrhs, float *R,
+                                                  int64_t ldr) {
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    for (int p = 0; p < 4; ++p) {
+        __syncthreads();
+        if (part == p)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nrhs) red[rr][q] = (p == 0) ? acc[q] : red[rr][q] + acc[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < 64 * nrhs; e += 256) {
+        const int r = e % 64, q = e / 64;
+        R[q * ldr + r] -= red[r][q];
+    }
+}
+__global__ void __launch_bounds__(256) k_fwd_diag_gf(const SDiag *__restrict__ e, float *R, int b) {
+    const SDiag E = e[blockIdx.y];
+    fwd_diag_body(E.L, b, b, R + E.off + blockIdx.x * E.ldr);
+}
+__global__ void __launch_bounds__(256) k_bwd_diag_gf(const SDiag *__restrict__ e, float *R, int b) {
+    const SDiag E = e[blockIdx.y];
+    bwd_diag_body(E.L, b, b, R + E.off + blockIdx.x * E.ldr);
+}
+template <int NQ>
+__global__ void __launch_bounds__(256) k_fwd_update_gf(const SUpd *__restrict__ u, float *R, int b, int nrhs) {
+    const SUpd U = u[blockIdx.x];
+    __shared__ float zs[128][17];
+    __shared__ float red[64][17];
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    float acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
+    for (int c0 = 0; c0 < b; c0 += 128) {
+        __syncthreads();
+        for (int e = tid; e < 128 * nrhs; e += 256) {
+            const int c = e % 128, q = e / 128;
+            zs[c][q] = R[U.src + q * U.ldr + c0 + c];
+        }
+        __syncthreads();
+        for (int c = part; c < 128; c += 4) {
+            const float l = (float)U.L[(int64_t)(c0 + c) * b + U.r0 + rr];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nrhs) acc[q] = fmaf(l, zs[c][q], acc[q]);
+        }
+    }
+    part_reduce_sub_f(red, acc, nrhs, R + U.dst, U.ldr);
+}
+template <int NQ>
+__global__ void __launch_bounds__(256) k_bwd_update_gf(const SUpd *__restrict__ u, float *R, int b, int nrhs) {
+    const SUpd U = u[blockIdx.x];
+    __shared__ float xs[64][17];
+    __shared__ float S[64][65];
+    __shared__ float red[64][17];
+    const int tid = threadIdx.x, rr = tid & 63, part = tid >> 6;
+    float acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
+    for (int c0 = 0; c0 < b; c0 += 64) {
+        __syncthreads();
+        for (int idx = tid; idx < 4096; idx += 256) {
+            const int c = idx & 63, r = idx >> 6;
+            S[r][c] = (float)U.L[(int64_t)(U.r0 + r) * b + c0 + c];
+        }
+        for (int e = tid; e < 64 * nrhs; e += 256) {
+            const int c = e % 64, q = e / 64;
+            xs[c][q] = R[U.src + q * U.ldr + c0 + c];
+        }
+        __syncthreads();
+        for (int c = part; c < 64; c += 4) {
+            const float l = S[rr][c];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nrhs) acc[q] = fmaf(l, xs[c][q], acc[q]);
+        }
+    }
+    part_reduce_sub_f(red, acc, nrhs, R + U.dst, U.ldr);
+}
+__global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+__global__ void k_add_f32(double *__restrict__ x, const float *__restrict__ d, int64_t n, int assign) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = assign ? (double)d[i] : x[i] + (double)d[i];
+}
+
 template <int NQ>
 __global__ void __launch_bounds__(256)
 k_symv_g(const SRes *__restrict__ rs, int b, const double *X, const double *B, double *R, int nrhs, int absmode) {
@@ -862,6 +960,24 @@ void launch_bwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaS
 }
 void launch_bwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s) {
     if (nu > 0) NQ_DISPATCH(nrhs, k_bwd_update_g, nu, 256, 0, s, u, R, b, nrhs);
+}
+void launch_fwd_diag_gf(const SDiag *e, int ne, float *R, int b, int nrhs, cudaStream_t s) {
+    if (ne > 0) k_fwd_diag_gf<<<dim3(nrhs, ne), 256, 0, s>>>(e, R, b);
+}
+void launch_fwd_update_gf(const SUpd *u, int nu, float *R, int b, int nrhs, cudaStream_t s) {
+    if (nu > 0) NQ_DISPATCH(nrhs, k_fwd_update_gf, nu, 256, 0, s, u, R, b, nrhs);
+}
+void launch_bwd_diag_gf(const SDiag *e, int ne, float *R, int b, int nrhs, cudaStream_t s) {
+    if (ne > 0) k_bwd_diag_gf<<<dim3(nrhs, ne), 256, 0, s>>>(e, R, b);
+}
+void launch_bwd_update_gf(const SUpd *u, int nu, float *R, int b, int nrhs, cudaStream_t s) {
+    if (nu > 0) NQ_DISPATCH(nrhs, k_bwd_update_gf, nu, 256, 0, s, u, R, b, nrhs);
+}
+void launch_to_f32(const double *x, float *y, int64_t n, cudaStream_t s) {
+    if (n > 0) k_to_f32<<<608, 256, 0, s>>>(x, y, n);
+}
+void launch_add_f32(double *x, const float *d, int64_t n, int assign, cudaStream_t s) {
+    if (n > 0) k_add_f32<<<608, 256, 0, s>>>(x, d, n, assign);
 }
 void launch_symv_g(const SRes *r, int nr, int b, const double *X, const double *B, double *R, int nrhs, int absmode,
                    cudaStream_t s) {

@@ -1614,6 +1614,29 @@ static int upload_batch_solve(tc_handle h, const BatchSolvePlan &S, BatchSolveDe
     return TC_OK;
 }
 
+// The same sweeps in FP32 (Rf: FP32 vectors of the RHS layout): the correction solves of a
+// refined solve, whose FP64 residuals carry the accuracy.
+static int batch_subst_f32(tc_handle h, const BatchSolvePlan &S, const BatchSolveDev &D, float *R, int nrhs) {
+    const int b = h->b;
+    for (size_t j = 0; j < S.fd.size(); ++j) {
+        launch_fwd_diag_gf(D.diag + S.fd[j].first, S.fd[j].second, R, b, nrhs, h->s);
+        CK_LAUNCH();
+        if (S.fu[j].second) {
+            launch_fwd_update_gf(D.upd + S.fu[j].first, S.fu[j].second, R, b, nrhs, h->s);
+            CK_LAUNCH();
+        }
+    }
+    for (size_t j = 0; j < S.bd.size(); ++j) {
+        launch_bwd_diag_gf(D.diag + S.bd[j].first, S.bd[j].second, R, b, nrhs, h->s);
+        CK_LAUNCH();
+        if (S.bu[j].second) {
+            launch_bwd_update_gf(D.upd + S.bu[j].first, S.bu[j].second, R, b, nrhs, h->s);
+            CK_LAUNCH();
+        }
+    }
+    return TC_OK;
+}
+
 static int batch_subst(tc_handle h, const BatchSolvePlan &S, const BatchSolveDev &D, double *R, int nrhs, bool back) {
     const int b = h->b;
     for (size_t j = 0; j < S.fd.size(); ++j) {
@@ -1650,9 +1673,13 @@ int tile_chol_solve_batched(tc_handle h, int nrhs, const double *const *B, doubl
     BatchSolveDev D{};
     int rc = upload_batch_solve(h, S, D);
     if (rc) return rc;
-    if ((rc = ensure(h, h->vec, (size_t)3 * S.total * sizeof(double)))) return rc;
+    // refined solves run their substitutions in FP32 (Rf) and their residuals in FP64
+    const bool f32 = max_refine > 0;
+    if ((rc = ensure(h, h->vec, (size_t)3 * S.total * sizeof(double) + (f32 ? (size_t)S.total * sizeof(float) : 0))))
+        return rc;
     if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, (size_t)(3 * nrhs + 1) * count) * sizeof(double)))) return rc;
     double *Bd = static_cast<double *>(h->vec.p), *Xd = Bd + S.total, *Rd = Xd + S.total;
+    float *Rf = reinterpret_cast<float *>(Rd + S.total);
     double *sc = static_cast<double *>(h->scratch.p);
     CK(cudaMemsetAsync(Bd, 0, S.total * sizeof(double), h->s));
     for (int i = 0; i < count; ++i) {
@@ -1660,8 +1687,16 @@ int tile_chol_solve_batched(tc_handle h, int nrhs, const double *const *B, doubl
         CK(cudaMemcpy2DAsync(Bd + S.off[i], (size_t)M.nt * b * sizeof(double), B[i], M.n * sizeof(double),
                              M.n * sizeof(double), nrhs, cudaMemcpyDefault, h->s));
     }
-    CK(cudaMemcpyAsync(Xd, Bd, S.total * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-    if ((rc = batch_subst(h, S, D, Xd, nrhs, true))) return rc;
+    if (f32) {
+        launch_to_f32(Bd, Rf, S.total, h->s);
+        CK_LAUNCH();
+        if ((rc = batch_subst_f32(h, S, D, Rf, nrhs))) return rc;
+        launch_add_f32(Xd, Rf, S.total, 1, h->s);
+        CK_LAUNCH();
+    } else {
+        CK(cudaMemcpyAsync(Xd, Bd, S.total * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+        if ((rc = batch_subst(h, S, D, Xd, nrhs, true))) return rc;
+    }
     // ||A_i||_inf once per factorization: max row sum of |A_i| (X = nullptr reads ones)
     if (max_refine > 0 && h->normA_infs[0] < 0) {
         CK(cudaMemsetAsync(sc, 0, (size_t)count * nrhs * sizeof(double), h->s));
@@ -1702,8 +1737,10 @@ int tile_chol_solve_batched(tc_handle h, int nrhs, const double *const *B, doubl
         }
         if (worst <= target_berr || it >= max_refine) break;
         // one refinement step for every matrix (already-accurate ones stay accurate)
-        if ((rc = batch_subst(h, S, D, Rd, nrhs, true))) return rc;
-        launch_axpy_flat(Xd, Rd, S.total, h->s);
+        launch_to_f32(Rd, Rf, S.total, h->s);
+        CK_LAUNCH();
+        if ((rc = batch_subst_f32(h, S, D, Rf, nrhs))) return rc;
+        launch_add_f32(Xd, Rf, S.total, 0, h->s);
         CK_LAUNCH();
     }
     for (int i = 0; i < count; ++i) {

@@ -158,6 +158,13 @@ void launch_axpy_cols(double *X, int64_t ldx, const double *D, int64_t ldd, int6
 void launch_dot_self(const double *v, int64_t n, double *out, cudaStream_t s);
 void launch_dot(const double *u, const double *v, int64_t n, double *out, cudaStream_t s);
 void launch_fwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaStream_t s);
+// FP32 forms (correction solves of a refined batched solve; factor tiles read in FP64)
+void launch_fwd_diag_gf(const SDiag *e, int ne, float *R, int b, int nrhs, cudaStream_t s);
+void launch_fwd_update_gf(const SUpd *u, int nu, float *R, int b, int nrhs, cudaStream_t s);
+void launch_bwd_diag_gf(const SDiag *e, int ne, float *R, int b, int nrhs, cudaStream_t s);
+void launch_bwd_update_gf(const SUpd *u, int nu, float *R, int b, int nrhs, cudaStream_t s);
+void launch_to_f32(const double *x, float *y, int64_t n, cudaStream_t s);
+void launch_add_f32(double *x, const float *d, int64_t n, int assign, cudaStream_t s);   // x (+)= d
 void launch_fwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s);
 void launch_bwd_diag_g(const SDiag *e, int ne, double *R, int b, int nrhs, cudaStream_t s);
 void launch_bwd_update_g(const SUpd *u, int nu, double *R, int b, int nrhs, cudaStream_t s);
