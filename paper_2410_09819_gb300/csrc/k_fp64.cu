@@ -1156,7 +1156,7 @@ k_trsm_tile(const __grid_constant__ TGroup g, const double *L, int ld, int b, co
 // the group's first nonzero row on, the product with the already solved rows (kept in shared
 // memory) is followed by the 64 x 64 diagonal solve.
 constexpr int TRINV_COLS = 4;
-__global__ void __launch_bounds__(256) k_trinv(const double *__restrict__ L, int b, double *__restrict__ Y) {
+__device__ __forceinline__ void trinv_body(const double *__restrict__ L, int b, double *__restrict__ Y) {
     extern __shared__ double tsm[];
     double *Ys = tsm;                               // b x 4: the group's columns, row-major by row
     double(*Ld)[65] = reinterpret_cast<double(*)[65]>(tsm + (size_t)b * TRINV_COLS);
@@ -1195,6 +1195,14 @@ __global__ void __launch_bounds__(256) k_trinv(const double *__restrict__ L, int
             Y[(int64_t)(c0 + cc) * b + rr] = Ys[rr * TRINV_COLS + cc];
         }
     }
+}
+__global__ void __launch_bounds__(256) k_trinv(const double *__restrict__ L, int b, double *__restrict__ Y) {
+    trinv_body(L, b, Y);
+}
+// the same for several tiles at once (grid.y = entry): the diagonal tiles of a batch's column
+__global__ void __launch_bounds__(256) k_trinv_batched(const TEntry *__restrict__ e, int b) {
+    const TEntry E = e[blockIdx.y];
+    trinv_body(E.L, b, E.Y);
 }
 
 // sum of log of the nv leading diagonal entries of one tile, fixed order, into *out
@@ -1317,6 +1325,17 @@ void launch_trinv(const double *L, int b, double *Y, cudaStream_t s) {
         mark_attrs_set(attr);
     }
     k_trinv<<<b / (2 * TRINV_COLS), 256, smem, s>>>(L, b, Y);
+}
+void launch_trinv_batched(const TEntry *e, int n, int b, cudaStream_t s) {
+    if (n <= 0) return;
+    const size_t smem = ((size_t)b * TRINV_COLS + 64 * 65 + 64 * TRINV_COLS) * sizeof(double);
+    static std::atomic<unsigned long long> attr{0};
+    if (attrs_pending(attr)) {     // sized for the largest tile it serves (b <= 2048)
+        cudaFuncSetAttribute(k_trinv_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(((size_t)2048 * TRINV_COLS + 64 * 65 + 64 * TRINV_COLS) * sizeof(double)));
+        mark_attrs_set(attr);
+    }
+    k_trinv_batched<<<dim3(b / (2 * TRINV_COLS), n), 256, smem, s>>>(e, b);
 }
 void launch_logdiag_tile(const double *D, int b, int nv, double *out, cudaStream_t s) {
     k_logdiag_tile<<<1, 256, 0, s>>>(D, b, nv, out);

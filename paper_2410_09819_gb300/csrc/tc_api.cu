@@ -37,6 +37,7 @@ struct ColPlan {
     int z0 = 0, nz = 0;          // emulated-FP64 update items
     int y0 = 0, ny = 0;          // emulated FP32-output update items (10 digit planes)
     int v0 = 0, nv = 0;          // TRSM as an emulated product with L_kk^{-1} (assign mode)
+    int ti0 = 0, nti = 0;        //   ... the diagonal tiles inverted for it (tinv / dinv entries)
     int nvp[4] = {0, 0, 0, 0};   //   ... of which per output precision (items in that order)
     int dg0 = 0, ndg = 0;        // tiles whose digit planes are made after the column's TRSMs
     int it0 = 0, nit = 0;        // FP64 update items
@@ -53,6 +54,8 @@ struct Plan {
     std::vector<PEntry> pentries;
     std::vector<LEntry> lentries;
     std::vector<ZItem> zitems, zitems32, zinv, zinvc, zref;
+    std::vector<TEntry> tinv;    // L_kk^{-1} of every matrix's diagonal tile, per column
+    std::vector<int> dinv;       //   ... the digit slot each inverse goes to (the diagonal tile's)
     bool inv_trsm = false, inv_refine = false;
     // columns of the update work items (zitems, zitems32): 128 x Z64_BN blocks for the
     // mixed-precision kernel when any matrix has a mixed map, else 128 x Z_BN
@@ -144,8 +147,10 @@ Plan build_plan(tc_handle h, double *W, int *status) {
     // of a mixed-precision factorization); an all-FP64 factorization adds one refinement step
     // with the residual C_mk - X0 L_kk^T, which brings the backward error back to the level of
     // substitution (the explicit inverse alone loses a factor ~kappa(L_kk)).
-    P.inv_trsm = h->cfg.fp64_mode == 2 && h->mats.size() == 1;
-    P.inv_refine = P.inv_trsm && !h->mats[0].mixed;
+    // a batch uses the inverse-based TRSM when its maps are mixed (products at each stored
+    // precision's plane count, no refinement step); an all-FP64 batch keeps the FP64 strips
+    P.inv_trsm = h->cfg.fp64_mode == 2 && (h->mats.size() == 1 || (zw == Z64_BN && b <= 2048));
+    P.inv_refine = P.inv_trsm && h->mats.size() == 1 && !h->mats[0].mixed;
     // L_kk^{-1} at invbuf, X0 of tile (k + i, k) at invbuf + i b^2 (sized by factor_matrices)
     double *inv_scratch = static_cast<double *>(h->invbuf.p);
     auto T = [&](const MatDesc &M, int i, int j) { return W + (M.tile0 + tidx(i, j)) * bb; };
@@ -227,14 +232,24 @@ Plan build_plan(tc_handle h, double *W, int *status) {
         C.ndg = (int)P.dtiles.size() - C.dg0;
         // TRSM of a mixed-precision column as C_mk L_kk^{-T} on the emulated engine (one matrix)
         C.v0 = (int)P.zinv.size();
+        C.ti0 = (int)P.tinv.size();
         if (P.inv_trsm) {
             // digit slots: C_mk (and later X0, R) in the tile's own slot, L_kk^{-1} in the slot of
             // the diagonal tile (k, k), L_kk in that of (k+1, k+1) (diagonal tiles are never
-            // update operands, and (k+1, k+1) is not factored yet)
-            const MatDesc &M = h->mats[0];
-            const int sinv = (int)(M.tile0 + tidx(k, k)), sl = (int)(M.tile0 + tidx(k + 1, k + 1));
+            // update operands, and (k+1, k+1) is not factored yet).  Inverse e of the column
+            // (one per matrix with tiles below its diagonal tile) at invbuf + e b^2.
+            for (int mi = 0; mi < nmat; ++mi) {
+                const MatDesc &M = h->mats[mi];
+                if (M.nt <= k + 1) continue;
+                const int e = (int)P.tinv.size() - C.ti0;
+                P.tinv.push_back({T(M, k, k), inv_scratch + (int64_t)e * bb});
+                P.dinv.push_back((int)(M.tile0 + tidx(k, k)));
+            }
             // tiles in precision order: one product launch per output precision
             for (int p = 0; p < 4; ++p)
+            for (int mi = 0; mi < nmat; ++mi) {
+            const MatDesc &M = h->mats[mi];
+            const int sinv = (int)(M.tile0 + tidx(k, k)), sl = (int)(M.tile0 + tidx(k + 1, k + 1));
             for (int m = k + 1; m < M.nt; ++m) {
                 if ((M.mixed ? (int)M.map[(size_t)m * M.nt + k] : TC_FP64) != p) continue;
                 const size_t before = P.zinv.size();
@@ -251,8 +266,10 @@ Plan build_plan(tc_handle h, double *W, int *status) {
                 }, P.inv_refine ? Z_BN : zw);
                 C.nvp[p] += (int)(P.zinv.size() - before);
             }
+            }
         }
         C.nv = (int)P.zinv.size() - C.v0;
+        C.nti = (int)P.tinv.size() - C.ti0;
         // 2. blocked POTRF of the diagonal tiles: per 64-panel, the block, its panel and the
         //    trailing update, each one launch over all matrices
         for (int jb = 0; jb < b / 64; ++jb) {
@@ -491,6 +508,8 @@ struct PlanDev {
     const TStrip *strips;
     const PEntry *pentries;
     const LEntry *lentries;
+    const TEntry *tinv = nullptr;       // inverse-based TRSM: the diagonal tiles to invert, per column
+    const int *dinv = nullptr;          //   ... and the digit slots of their inverses
     const ZItem *zitems = nullptr, *zitems32 = nullptr, *zinv = nullptr, *zinvc = nullptr, *zref = nullptr;
     double *zamax2 = nullptr;
     double *zamax3 = nullptr;    // refinement: amax of L_kk, X0 and R (3 x Ttot)
@@ -510,7 +529,9 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
     const size_t sr = P.reds.size() * sizeof(DRed), ss = P.strips.size() * sizeof(TStrip);
     const size_t sp = P.pentries.size() * sizeof(PEntry), sl = P.lentries.size() * sizeof(LEntry);
     const size_t oj = 0, oi = align_up(oj + sj), orr = align_up(oi + si), os = align_up(orr + sr);
-    const size_t op = align_up(os + ss), ol = align_up(op + sp), total = align_up(ol + sl);
+    const size_t st = P.tinv.size() * sizeof(TEntry), sdv = P.dinv.size() * sizeof(int);
+    const size_t op = align_up(os + ss), ol = align_up(op + sp), ot = align_up(ol + sl), odv = align_up(ot + st);
+    const size_t total = align_up(odv + sdv);
     int rc = ensure(h, h->tables, total);
     if (rc) return rc;
     std::vector<char> host(total);
@@ -520,6 +541,8 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
     if (ss) memcpy(host.data() + os, P.strips.data(), ss);
     if (sp) memcpy(host.data() + op, P.pentries.data(), sp);
     if (sl) memcpy(host.data() + ol, P.lentries.data(), sl);
+    if (st) memcpy(host.data() + ot, P.tinv.data(), st);
+    if (sdv) memcpy(host.data() + odv, P.dinv.data(), sdv);
     CK(cudaMemcpy(h->tables.p, host.data(), total, cudaMemcpyHostToDevice));
     char *base = static_cast<char *>(h->tables.p);
     D.jobs = reinterpret_cast<const DJob *>(base + oj);
@@ -528,6 +551,8 @@ int prepare_factor(tc_handle h, const Plan &P, const MxpPlan *M, PlanDev &D) {
     D.strips = reinterpret_cast<const TStrip *>(base + os);
     D.pentries = reinterpret_cast<const PEntry *>(base + op);
     D.lentries = reinterpret_cast<const LEntry *>(base + ol);
+    D.tinv = reinterpret_cast<const TEntry *>(base + ot);
+    D.dinv = reinterpret_cast<const int *>(base + odv);
     if ((rc = ensure(h, h->partials, (size_t)std::max(1, P.max_parts) * 4096 * sizeof(double)))) return rc;
     h->pairs_dev = nullptr;
     if (!P.zitems.empty() || !P.zitems32.empty() || !P.zinv.empty() || !P.dtiles.empty()) {
@@ -701,22 +726,29 @@ int execute_factor(tc_handle h, const Plan &P, const MxpPlan *M, const PlanDev &
             // with the refinement step, for an all-FP64 factorization)
             const int sp = spans ? span_begin(h, CAT_TRSM) : -1;
             const MatDesc &Md = h->mats[0];
-            const int gkk = (int)(Md.tile0 + tidx(k, k));
             double *inv = static_cast<double *>(h->invbuf.p);
             uint8_t *pool = static_cast<uint8_t *>(h->dpool.p);
-            const double *Lkk0 = W + (Md.tile0 + tidx(k, k)) * bb;
             if (b <= 2048) {
-                launch_trinv(Lkk0, b, inv, h->s);                     // inv = L_kk^{-1}
-            } else {                                                   // (its shared-memory column panel would not fit)
+                // inverse e of the column at inv + e b^2 (one per matrix), then its amax and
+                // digit planes into the diagonal tile's slot
+                launch_trinv_batched(D.tinv + C.ti0, C.nti, b, h->s);
+                CK_LAUNCH();
+                launch_tile_amax(W, b, D.dinv + C.ti0, C.nti, D.zamax2, h->s, inv);
+                CK_LAUNCH();
+                launch_digits(W, b, D.dinv + C.ti0, C.nti, D.zamax2, pool, D.zexps, h->s, inv);
+                CK_LAUNCH();
+            } else {                       // one matrix: its shared-memory column panel would not fit
+                const int gkk = (int)(Md.tile0 + tidx(k, k));
+                const double *Lkk0 = W + (Md.tile0 + tidx(k, k)) * bb;
                 launch_set_identity(inv, b, h->s);
                 CK_LAUNCH();
                 launch_trsm_tile(inv, Lkk0, b, b, nullptr, h->s);     // inv = L_kk^{-T}
+                CK_LAUNCH();
+                launch_amax_ptr(inv, bb, D.zamax2 + gkk, h->s);
+                CK_LAUNCH();
+                launch_digits_src(inv, b, 1, gkk, D.zamax2 + gkk, pool, D.zexps, h->s);
+                CK_LAUNCH();
             }
-            CK_LAUNCH();
-            launch_amax_ptr(inv, bb, D.zamax2 + gkk, h->s);
-            CK_LAUNCH();
-            launch_digits_src(inv, b, b <= 2048 ? 0 : 1, gkk, D.zamax2 + gkk, pool, D.zexps, h->s);
-            CK_LAUNCH();
             launch_tile_amax(W, b, D.dtiles + C.dg0, C.ndg, D.zamax2, h->s);
             CK_LAUNCH();
             launch_digits(W, b, D.dtiles + C.dg0, C.ndg, D.zamax2, pool, D.zexps, h->s);
@@ -871,9 +903,10 @@ int factor_matrices(tc_handle h, tc_stats *stats, bool use_graph, const std::vec
     if (rc) return rc;
     status = static_cast<int *>(h->status.p);
     if ((rc = ensure(h, h->scratch, std::max<size_t>(4096, h->mats.size()) * sizeof(double)))) return rc;
-    if (h->cfg.fp64_mode == 2 && h->mats.size() == 1) {
+    if (h->cfg.fp64_mode == 2 && (h->mats.size() == 1 || mixed)) {
+        // L_kk^{-1} of every matrix of a column (and, for one all-FP64 matrix, X0 of each tile)
         const size_t bb = (size_t)h->b * h->b;
-        const size_t tiles = mixed ? 1 : 1 + (size_t)h->mats[0].nt;
+        const size_t tiles = h->mats.size() > 1 ? h->mats.size() : (mixed ? 1 : 1 + (size_t)h->mats[0].nt);
         if ((rc = ensure(h, h->invbuf, tiles * bb * sizeof(double)))) return rc;
     }
     Plan P = build_plan(h, W, status);

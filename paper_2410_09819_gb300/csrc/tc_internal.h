@@ -68,6 +68,11 @@ struct SUpd {           // off-diagonal update of a 64-row chunk: dst -= op(L) s
     int64_t src, dst, ldr;
     int r0;             // chunk's first row inside the destination tile row
 };
+struct TEntry {         // triangular inverse of one diagonal tile: Y = L^{-1} (b x b, column-major)
+    const double *L;
+    double *Y;
+};
+void launch_trinv_batched(const TEntry *e, int n, int b, cudaStream_t s);
 struct SRes {           // residual / |A| x of one 64-row chunk of one matrix
     const double *A;    // the matrix's tiles
     int64_t n;
