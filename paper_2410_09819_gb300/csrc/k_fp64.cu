@@ -592,6 +592,99 @@ k_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t
     }
 }
 
+// One right-hand side: R = B - A x (ABS false) or R = |A| x (ABS true; x = ones when X is
+// null), A symmetric and held as lower tiles (column-major, the diagonal tiles full).  One
+// CTA per 64 rows [r0, r0 + 64) of tile row i; every element of its 64 x n row panel is
+// loaded once, straight from global memory into registers, for one multiply-add.
+//   * tiles A_ij, j <= i: columns of the stored tile.  Warp w takes the columns c = w (mod 8),
+//     each lane two adjacent rows (one 16-byte load per column; a warp reads 512 contiguous
+//     bytes), with two accumulators per row so that consecutive columns do not chain.
+//   * tiles right of the diagonal, A_ij = A_ji^T (j > i): row r of A_ij is column r of the
+//     stored A_ji, contiguous in memory.  Warp w takes the rows r0 + 8w ... r0 + 8w + 7, its
+//     lanes two adjacent columns per 64, with x's pair loaded once for the eight rows.
+// Partial sums meet in a fixed order (lanes by shuffle, warps in shared memory), so the
+// result does not depend on scheduling.  Rows and columns >= n (padding) contribute nothing
+// and R's padding is 0.  The multiply-adds, not the bytes, bound it: a GB300 SM retires two
+// FP64 multiply-adds per clock, n^2 per call.
+template <bool ABS>
+__global__ void __launch_bounds__(256)
+k_symv1(const double *__restrict__ A, int nt, int b, int64_t n, const double *__restrict__ X,
+        const double *__restrict__ B, double *__restrict__ R) {
+    __shared__ double red[8][64];
+    __shared__ double tr[64];
+    const int chunks = b / 64;
+    const int i = blockIdx.x / chunks, r0 = (blockIdx.x % chunks) * 64;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t bb = (int64_t)b * b;
+    // tiles left of and on the diagonal
+    double a0 = 0.0, a1 = 0.0, e0 = 0.0, e1 = 0.0;
+    for (int j = 0; j <= i; ++j) {
+        const double *T = A + ((int64_t)i * (i + 1) / 2 + j) * bb + r0 + 2 * lane;
+        const double *x = X ? X + (int64_t)j * b : nullptr;
+        const int cmax = (int)min((int64_t)b, n - (int64_t)j * b);
+        int c = warp;
+#pragma unroll 2
+        for (; c + 8 < cmax; c += 16) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(T + (int64_t)c * b));
+            const double2 w = __ldg(reinterpret_cast<const double2 *>(T + (int64_t)(c + 8) * b));
+            const double xv = x ? __ldg(x + c) : 1.0, xw = x ? __ldg(x + c + 8) : 1.0;
+            a0 = fma(ABS ? fabs(v.x) : v.x, xv, a0);
+            a1 = fma(ABS ? fabs(v.y) : v.y, xv, a1);
+            e0 = fma(ABS ? fabs(w.x) : w.x, xw, e0);
+            e1 = fma(ABS ? fabs(w.y) : w.y, xw, e1);
+        }
+        if (c < cmax) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(T + (int64_t)c * b));
+            const double xv = x ? __ldg(x + c) : 1.0;
+            a0 = fma(ABS ? fabs(v.x) : v.x, xv, a0);
+            a1 = fma(ABS ? fabs(v.y) : v.y, xv, a1);
+        }
+    }
+    red[warp][2 * lane] = a0 + e0;
+    red[warp][2 * lane + 1] = a1 + e1;
+    // tiles right of the diagonal, through the stored tiles (j, i)
+    double acc[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) acc[p] = 0.0;
+    for (int j = i + 1; j < nt; ++j) {
+        const double *T = A + ((int64_t)j * (j + 1) / 2 + i) * bb + (int64_t)(r0 + 8 * warp) * b + 2 * lane;
+        const double *x = X ? X + (int64_t)j * b + 2 * lane : nullptr;
+        const int cmax = (int)min((int64_t)b, n - (int64_t)j * b);
+        for (int m = 0; m < b; m += 64) {
+            double2 xv = x ? __ldg(reinterpret_cast<const double2 *>(x + m)) : make_double2(1.0, 1.0);
+            const int c = m + 2 * lane;
+            if (c >= cmax) xv.x = 0.0;
+            if (c + 1 >= cmax) xv.y = 0.0;
+            const bool lo = c < cmax, hi = c + 1 < cmax;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                double2 v = __ldg(reinterpret_cast<const double2 *>(T + (int64_t)p * b + m));
+                if (!lo) v.x = 0.0;
+                if (!hi) v.y = 0.0;
+                acc[p] = fma(ABS ? fabs(v.x) : v.x, xv.x, acc[p]);
+                acc[p] = fma(ABS ? fabs(v.y) : v.y, xv.y, acc[p]);
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        double v = acc[p];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) tr[8 * warp + p] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const int r = threadIdx.x;
+        double s = tr[r];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += red[w][r];
+        const int64_t g = (int64_t)i * b + r0 + r;
+        double out = 0.0;
+        if (g < n) out = ABS ? s : B[g] - s;
+        R[g] = out;
+    }
+}
+
 // out[c] = max_r |V[c*ld + r]|, r < n (out must start at 0; max of non-negative doubles is
 // monotone in their bit patterns, so atomicMax on the bits is exact and order-free).
 __global__ void k_colmax_abs(const double *V, int64_t ld, int64_t n, double *out) {
@@ -1062,6 +1155,14 @@ void launch_bwd_update(const double *W, int nt, int b, int j, double *R, int64_t
 void launch_symv_resid(const double *A, int nt, int b, int64_t n, const double *X, int64_t ldx,
                        const double *B, int64_t ldb, double *R, int64_t ldr, int nrhs, int absmode,
                        cudaStream_t s) {
+    const auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    if (nrhs == 1 && al16(A) && al16(X) && b % 64 == 0) {      // 16-byte loads of A and x
+        if (absmode)
+            k_symv1<true><<<nt * (b / 64), 256, 0, s>>>(A, nt, b, n, X, nullptr, R);
+        else
+            k_symv1<false><<<nt * (b / 64), 256, 0, s>>>(A, nt, b, n, X, B, R);
+        return;
+    }
     NQ_DISPATCH(nrhs, k_symv_resid, nt * (b / 64), 256, 0, s, A, nt, b, n, X, ldx, B, ldb, R, ldr, nrhs, absmode);
 }
 void launch_colmax_abs(const double *V, int64_t ld, int64_t n, int ncols, double *out, cudaStream_t s) {

@@ -208,3 +208,41 @@ def test_loglik_from_solution_matches_refined_and_oracle(H):
     quad = lambda ll, l: -2.0 * (ll + 0.5 * n * math.log(2 * math.pi) + 0.5 * l)  # noqa: E731
     q64 = quad(oracle.loglik(Lo, y), oracle.logdet(Lo))
     assert abs(quad(ll_dev, ld) - q64) <= 1e-10 * abs(q64)
+
+
+@pytest.mark.parametrize("n", [1000, 1024])
+def test_one_rhs_residual_matches_multi_rhs_and_numpy(H, n):
+    """One refinement step from a mixed-precision factor: the single-RHS residual kernel and the
+    multi-RHS one give the same corrected solution (they differ only in rounding order), and the
+    backward error the solve reports is the one numpy computes for the returned solution (which
+    also checks the norm ||A||_inf from the |A| x pass).  n = 1000 leaves a ragged last tile."""
+    import torch
+    b = 128
+    pts = inputs.uniform_points(n, 31, morton=True)
+    A = oracle.matern(pts, 1.0, 0.02, 0.5, 1e-4)
+    nt = -(-n // b)
+    At = to_dev(pack_padded(A, b))
+    pm = np.empty(nt * nt, dtype=np.uint8)
+    tc.tile_chol_precision_map(H.h, n, b, At, 1e-5, 1, 4, pm)
+    assert tc.tile_chol_factor(H.h, n, b, At, pm) == 0
+    B = inputs.gaussian(n, 2, seed=21)
+    berr_np = lambda X, Bc: np.max(np.abs(Bc - A @ X).max(0) / (np.abs(A).sum(1).max() * np.abs(X).max(0)  # noqa: E731
+                                                              + np.abs(Bc).max(0)))
+    # two right-hand sides: the multi-RHS residual kernel
+    B2 = to_dev(B.T.copy())
+    X2 = torch.empty_like(B2)
+    s2 = tc.tc_stats()
+    tc.tile_chol_solve(H.h, 2, B2, n, X2, n, 1, 0.0, s2)
+    X2h = X2.cpu().numpy().reshape(2, n).T
+    # the first of them alone: the single-RHS kernel
+    B1 = to_dev(B[:, 0].copy())
+    X1 = torch.empty_like(B1)
+    s1 = tc.tc_stats()
+    tc.tile_chol_solve(H.h, 1, B1, n, X1, n, 1, 0.0, s1)
+    X1h = X1.cpu().numpy()
+    assert s1.refine_iters == 1 and s2.refine_iters == 1
+    # a wrong tile in either residual would move the correction by ~eps_high |X|
+    assert np.max(np.abs(X1h - X2h[:, 0])) <= 1e-10 * np.abs(X2h[:, 0]).max()
+    e1 = berr_np(X1h[:, None], B[:, :1])
+    assert e1 > 1e-15                       # one step from a 1e-5 factor: not yet at rounding level
+    assert abs(s1.berr - e1) <= 1e-3 * e1
