@@ -455,16 +455,23 @@ def run_ours(args, ws, rank, local):
         yh = y.cpu().pin_memory()
         xh = torch.empty_like(yh).pin_memory()
         maph = torch.zeros(nt * nt, dtype=torch.uint8, pin_memory=True) if w.mixed else None
+
+        def e2e_step():
+            # the user's calls on host buffers: map and factor from one copy of A over the link
+            if w.mixed:
+                tc.tile_chol_factor_mapped(H.h, n, b, Ah, w.eps_high, w.band, w.prec_set, maph, None)
+            else:
+                tc.tile_chol_factor(H.h, n, b, Ah, None, None)
+            tc.tile_chol_solve(H.h, 1, yh, n, xh, n, 2, 1e-14, None)
+            return tc.tile_chol_loglik_solved(H.h, yh, xh)
+
+        e2e_step()                     # warm-up: the handle's device copy of A is allocated once
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        if w.mixed:
-            tc.tile_chol_precision_map(H.h, n, b, Ah, w.eps_high, w.band, w.prec_set, maph)
-        tc.tile_chol_factor(H.h, n, b, Ah, maph, None)
-        tc.tile_chol_solve(H.h, 1, yh, n, xh, n, 2, 1e-14, None)
-        ll_h = tc.tile_chol_loglik_solved(H.h, yh, xh)
+        ll_h = e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
         te = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
@@ -472,7 +479,7 @@ def run_ours(args, ws, rank, local):
             tt = torch.tensor([te], device=dev, dtype=torch.float64)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             te = float(tt.item())
-        h2d = Ah.numel() * 8 * (2 if w.mixed else 1) + 2 * n * 8
+        h2d = Ah.numel() * 8 + 3 * n * 8          # A once; y for the solve, y and x for Eq. 1
         d2h = n * 8 + 8
         e2e = {"value": ws * flops / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "loglik_matches_device": bool(abs(ll_h - ll) <= 1e-9 * abs(ll))}

@@ -231,6 +231,22 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles,
                      const uint8_t *map, tc_stats *stats);
 
 /*
+ * tile_chol_precision_map (Section IV-C) followed by tile_chol_factor (Algorithm 1) with
+ * that map, on one device copy of A: a host A_tiles is copied once into the handle's device
+ * copy (which the factor and tile_chol_solve's refinement then read), instead of once for
+ * the map's tile norms and again for the factor.  A device A_tiles is used in place and
+ * must stay valid as for tile_chol_factor.  The map and the factor are the ones the two
+ * separate calls give.
+ * map_out: host or device, Nt*Nt bytes (written, as tile_chol_precision_map).
+ * stats: the factorization's, as tile_chol_factor (NULL allowed).
+ * Returns as tile_chol_factor; TC_ERR_ARG for a NULL A_tiles or map_out, eps_high <= 0,
+ * band < 0 or prec_set outside 1..4; TC_ERR_OOM when the device copy does not fit.
+ */
+int tile_chol_factor_mapped(tc_handle h, int64_t n, int b, const double *A_tiles,
+                            double eps_high, int band, int prec_set, uint8_t *map_out,
+                            tc_stats *stats);
+
+/*
  * Out-of-core factorization (Sections III-C and IV-B, Algorithms 2 and 3): A_tiles is HOST
  * memory (best page-locked) holding A in the tile layout; on return it holds the factor L
  * (in place, as the paper's write-back does; upper triangles of diagonal tiles are left as

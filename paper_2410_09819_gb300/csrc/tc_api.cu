@@ -1211,6 +1211,30 @@ int tile_chol_factor(tc_handle h, int64_t n, int b, const double *A_tiles, const
     return info;
 }
 
+// The precision map of Section IV-C and the factorization of Algorithm 1 on one device copy of
+// A: a host matrix crosses the link once (into the handle's copy, which the factor then
+// references), not once for the map's norms and again for the factor.
+int tile_chol_factor_mapped(tc_handle h, int64_t n, int b, const double *A_tiles, double eps_high, int band,
+                            int prec_set, uint8_t *map_out, tc_stats *stats) {
+    int rc = check_nb(h, n, b);
+    if (rc) return rc;
+    if (!A_tiles || !map_out) return set_err(h, TC_ERR_ARG, "A_tiles and map_out must not be NULL");
+    if (!(eps_high > 0) || band < 0 || prec_set < 1 || prec_set > 4)
+        return set_err(h, TC_ERR_ARG, "eps_high > 0, band >= 0 and prec_set in 1..4 are required");
+    CK(cudaSetDevice(h->device));
+    const double *Ad = A_tiles;
+    if (!on_device(A_tiles)) {
+        const int nt = (int)((n + b - 1) / b);
+        const size_t bytes = (size_t)tidx(nt, 0) * b * b * sizeof(double);
+        h->factored = false;                       // the handle's copy of A is replaced
+        if ((rc = ensure(h, h->Acopy, bytes))) return rc;
+        CK(cudaMemcpyAsync(h->Acopy.p, A_tiles, bytes, cudaMemcpyHostToDevice, h->s));
+        Ad = static_cast<const double *>(h->Acopy.p);
+    }
+    if ((rc = tile_chol_precision_map(h, n, b, Ad, eps_high, band, prec_set, map_out, nullptr))) return rc;
+    return tile_chol_factor(h, n, b, Ad, map_out, stats);
+}
+
 int tile_chol_logdet(tc_handle h, double *logdet_out) {
     if (!h || !logdet_out) return TC_ERR_ARG;
     if (!h->factored) return set_err(h, TC_ERR_STATE, "no successful factorization");

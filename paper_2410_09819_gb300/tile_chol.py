@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
         "tile_chol_precision_map": (ci, [H, i64, ci, vp, cd, ci, ci, vp, vp]),
         "tile_chol_factor": (ci, [H, i64, ci, vp, vp, ctypes.POINTER(tc_stats)]),
         "tile_chol_factor_ooc": (ci, [H, i64, ci, vp, vp, ctypes.POINTER(tc_stats)]),
+        "tile_chol_factor_mapped": (ci, [H, i64, ci, vp, cd, ci, ci, vp, ctypes.POINTER(tc_stats)]),
         "tile_chol_solve": (ci, [H, ci, vp, i64, vp, i64, ci, cd, ctypes.POINTER(tc_stats)]),
         "tile_chol_logdet": (ci, [H, ctypes.POINTER(cd)]),
         "tile_chol_loglik": (ci, [H, vp, ctypes.POINTER(cd)]),
@@ -211,6 +212,16 @@ def tile_chol_factor(h, n, b, A_tiles, map=None, stats: tc_stats | None = None) 
     _need_tiles(n, b, A_tiles, map)
     return _check(h, lib().tile_chol_factor(h, n, b, _ptr(A_tiles), _ptr(map),
                                             ctypes.byref(stats) if stats is not None else None),
+                  allow_positive=True)
+
+
+def tile_chol_factor_mapped(h, n, b, A_tiles, eps_high, band, prec_set, map_out,
+                            stats: tc_stats | None = None) -> int:
+    """Precision map and factor on one device copy of A (a host A crosses the link once).
+    Returns 0, or the 1-based column of a non-positive pivot."""
+    _need_tiles(n, b, A_tiles, map_out)
+    return _check(h, lib().tile_chol_factor_mapped(h, n, b, _ptr(A_tiles), eps_high, band, prec_set, _ptr(map_out),
+                                                   ctypes.byref(stats) if stats is not None else None),
                   allow_positive=True)
 
 

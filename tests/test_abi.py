@@ -59,6 +59,7 @@ def test_null_handle_is_rejected_without_touching_a_gpu(lib):
     assert L.tc_last_error(None) == b"null handle"
     assert L.tc_set_wait_limit(None, 5, 0) == -1
     assert L.tile_chol_loglik_solved(None, None, None, None) == -1
+    assert L.tile_chol_factor_mapped(None, 10, 64, None, 1e-9, 0, 4, None, None) == -1
 
 
 def test_config_struct_matches_the_header():

@@ -246,3 +246,42 @@ def test_one_rhs_residual_matches_multi_rhs_and_numpy(H, n):
     e1 = berr_np(X1h[:, None], B[:, :1])
     assert e1 > 1e-15                       # one step from a 1e-5 factor: not yet at rounding level
     assert abs(s1.berr - e1) <= 1e-3 * e1
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_factor_mapped_equals_map_then_factor(H, where):
+    """tile_chol_factor_mapped (one device copy of A) gives the map, factor and log-determinant
+    of tile_chol_precision_map followed by tile_chol_factor, and the refined solve after it
+    reads the right A (n = 1000: a ragged last tile)."""
+    import torch
+    n, b = 1000, 128
+    pts = inputs.uniform_points(n, 31, morton=True)
+    A = oracle.matern(pts, 1.0, 0.02, 1.5, 1e-4)
+    nt = -(-n // b)
+    Ah = pack_padded(A, b)
+    At = to_dev(Ah)
+    pm = np.empty(nt * nt, dtype=np.uint8)
+    tc.tile_chol_precision_map(H.h, n, b, At, 1e-6, 1, 4, pm)
+    assert tc.tile_chol_factor(H.h, n, b, At, pm) == 0
+    L1 = torch.empty_like(At)
+    tc.tile_chol_get_factor(H.h, L1)
+    ld1 = tc.tile_chol_logdet(H.h)
+    src = np.ascontiguousarray(Ah) if where == "host" else to_dev(Ah)
+    pm2 = np.zeros(nt * nt, dtype=np.uint8) if where == "host" else torch.zeros(nt * nt, dtype=torch.uint8, device="cuda")
+    st = tc.tc_stats()
+    assert tc.tile_chol_factor_mapped(H.h, n, b, src, 1e-6, 1, 4, pm2, st) == 0
+    pm2h = pm2 if where == "host" else pm2.cpu().numpy()
+    assert (pm2h == pm).all()
+    assert (pm != tc.TC_FP64).any()
+    L2 = torch.empty_like(At)
+    tc.tile_chol_get_factor(H.h, L2)
+    assert torch.equal(L1, L2)
+    assert tc.tile_chol_logdet(H.h) == ld1
+    assert st.flops == pytest.approx(n ** 3 / 3)
+    B = inputs.gaussian(n, 1, seed=5)[:, 0].copy()
+    Bd = to_dev(B)
+    X = torch.empty_like(Bd)
+    tc.tile_chol_solve(H.h, 1, Bd, n, X, n, 10, 1e-14, None)
+    Xh = X.cpu().numpy()
+    berr = np.abs(B - A @ Xh).max() / (np.abs(A).sum(1).max() * np.abs(Xh).max() + np.abs(B).max())
+    assert berr <= 1e-13
